@@ -1,0 +1,229 @@
+"""Plain CPU oracle for the QMC hot path (ctypes over ``liboracle.so``).
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and the
+cpu_baseline / reference leg of ``bench.py`` may import this package; the
+product package never does.  The arithmetic lives in ``qmc_oracle.c`` (plain
+C, fp64 integrands, one bit / digit / sample at a time); this module only
+marshals numpy arrays and, for speed of the test suite, runs independent
+integrals or row ranges on several host threads (ctypes releases the GIL).
+
+Parity unpinned: the exact output bits of ``nested_scramble`` (the paper
+names Owen scrambling but prints no algorithm; see ``qmc_oracle.c``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qmc_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+SOURCE_SOBOL, SOURCE_LATTICE = 0, 1
+SCRAMBLE_NONE, SCRAMBLE_XOR, SCRAMBLE_NESTED = 0, 1, 2
+F_BILINEAR2D, F_GENZ_PRODUCT_PEAK, F_GENZ_OSCILLATORY, F_GAUSSMIX4_6D = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile qmc_oracle.c with gcc (no FMA contraction, so x86 and Arm agree)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        u32, u64, i32 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+        P = ctypes.c_void_p
+        dbl = ctypes.c_double
+        sig = {
+            "qo_map_u32_to_unifloat": (ctypes.c_float, [u32]),
+            "qo_map_array": (None, [P, u64, P]),
+            "qo_bit_reverse": (u32, [u32]),
+            "qo_radical_inverse_u32": (u32, [u32, u64]),
+            "qo_primitive_polynomials": (u32, [u32, P, u32]),
+            "qo_sobol_matrices": (i32, [u32, P, P]),
+            "qo_sobol_u32": (u32, [P, u32]),
+            "qo_nested_scramble": (u32, [u32, u32]),
+            "qo_sobol_points": (None, [P, u32, u64, u64, u32, P, P, P]),
+            "qo_lattice_u32": (u32, [u32, u32, u32, u32]),
+            "qo_lattice_points": (None, [P, P, u32, u64, u64, u32, P, P]),
+            "qo_integrate_one": (i32, [u32, u32, u32, u32, P, P, P, u32, P, P, P, P, P]),
+            "qo_integrand": (dbl, [u32, u32, P, P, P]),
+            "qo_gaussmix_f64": (dbl, [P, P]),
+            "qo_exact_genz_product_peak": (dbl, [u32, P]),
+            "qo_exact_genz_oscillatory": (dbl, [u32, P]),
+            "qo_exact_gaussmix": (dbl, [P, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _threads(threads):
+    return threads or (os.cpu_count() or 1)
+
+
+def map_u32_to_unifloat(u) -> np.ndarray:
+    u = np.ascontiguousarray(u, dtype=np.uint32)
+    out = np.empty(u.shape, np.float32)
+    lib().qo_map_array(_p(u), u.size, _p(out))
+    return out
+
+
+def bit_reverse(v: int) -> int:
+    return lib().qo_bit_reverse(v)
+
+
+def radical_inverse_u32(b: int, i: int) -> int:
+    return lib().qo_radical_inverse_u32(b, i)
+
+
+def primitive_polynomials(max_degree: int = 7) -> list[int]:
+    buf = np.zeros(4096, np.uint32)
+    n = lib().qo_primitive_polynomials(max_degree, _p(buf), buf.size)
+    return [int(v) for v in buf[:n]]
+
+
+def sobol_matrices(s: int, raw_init: np.ndarray) -> np.ndarray:
+    raw = np.ascontiguousarray(raw_init, dtype=np.uint32).reshape(-1)
+    if raw.size < 7 * s:
+        raise ValueError("raw_init needs 7 words per dimension")
+    C = np.zeros((s, 32), np.uint32)
+    if lib().qo_sobol_matrices(s, _p(raw), _p(C)) != 0:
+        raise ValueError("too many dimensions for polynomials of degree <= 7")
+    return C
+
+
+def nested_scramble(y: int, seed: int) -> int:
+    return lib().qo_nested_scramble(y, seed)
+
+
+def _chunked(count, threads, fn):
+    threads = _threads(threads)
+    step = max(1, -(-count // threads))
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(fn, range(0, count, step), [step] * len(range(0, count, step))))
+
+
+def sobol_points(C, begin, count, mode=SCRAMBLE_NONE, seeds=None, threads=None):
+    """(u32 [count][s], f32 [count][s]) of points begin .. begin+count-1."""
+    C = np.ascontiguousarray(C, dtype=np.uint32)
+    s = C.shape[0]
+    seeds = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint32)
+    u = np.empty((count, s), np.uint32)
+    f = np.empty((count, s), np.float32)
+
+    def run(r0, n):
+        n = min(n, count - r0)
+        lib().qo_sobol_points(_p(C), s, begin + r0, n, mode, _p(seeds),
+                              u[r0:].ctypes.data, f[r0:].ctypes.data)
+
+    _chunked(count, threads, run)
+    return u, f
+
+
+def lattice_points(g, shift, begin, count, backward=False, threads=None):
+    g = np.ascontiguousarray(g, dtype=np.uint32)
+    s = g.shape[0]
+    shift = None if shift is None else np.ascontiguousarray(shift, dtype=np.uint32)
+    u = np.empty((count, s), np.uint32)
+    f = np.empty((count, s), np.float32)
+
+    def run(r0, n):
+        n = min(n, count - r0)
+        lib().qo_lattice_points(_p(g), _p(shift), s, begin + r0, n, int(backward),
+                                u[r0:].ctypes.data, f[r0:].ctypes.data)
+
+    _chunked(count, threads, run)
+    return u, f
+
+
+def integrate(source, integrand, s, counts, theta, *, C=None, g=None, scramble=0, seeds=None,
+              with_grad=False, threads=None):
+    """Per-integral QMC estimates (fp64).
+
+    counts [n]; theta [n][P] (fp32); seeds None, [s] shared or [n][s].
+    Returns dict(est [n], mass [n], grad [n][16], grad_mass [n][16]).
+    """
+    counts = np.ascontiguousarray(counts, dtype=np.uint32).reshape(-1)
+    n = counts.size
+    theta = np.ascontiguousarray(theta, dtype=np.float32).reshape(n, -1)
+    C = None if C is None else np.ascontiguousarray(C, dtype=np.uint32)
+    g = None if g is None else np.ascontiguousarray(g, dtype=np.uint32)
+    if seeds is not None:
+        seeds = np.asarray(seeds, dtype=np.uint32)
+        if seeds.ndim == 1:  # one seed vector shared by every integral
+            seeds = np.tile(seeds.reshape(1, s), (n, 1))
+        seeds = np.ascontiguousarray(seeds.reshape(n, s))
+    est = np.zeros(n)
+    mass = np.zeros(n)
+    grad = np.zeros((n, 16)) if with_grad else None
+    gmass = np.zeros((n, 16)) if with_grad else None
+
+    def one(p):
+        rc = lib().qo_integrate_one(
+            source, integrand, s, scramble, _p(C), _p(g),
+            None if seeds is None else seeds[p].ctypes.data, int(counts[p]), theta[p].ctypes.data,
+            est[p:].ctypes.data, mass[p:].ctypes.data,
+            None if grad is None else grad[p].ctypes.data,
+            None if gmass is None else gmass[p].ctypes.data)
+        if rc != 0:
+            raise ValueError("oracle rejected the problem")
+
+    # largest integrals first so the pool stays busy
+    order = np.argsort(-counts.astype(np.int64), kind="stable")
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(one, order.tolist()))
+    return {"est": est, "mass": mass, "grad": grad, "grad_mass": gmass}
+
+
+def integrand(kind, x, theta, s=None):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    theta = np.ascontiguousarray(theta, dtype=np.float32)
+    grad = np.zeros(16)
+    v = lib().qo_integrand(kind, s or x.size, _p(x), _p(theta), _p(grad))
+    return v, grad
+
+
+def gaussmix_f64(x, th) -> float:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    th = np.ascontiguousarray(th, dtype=np.float64)
+    return lib().qo_gaussmix_f64(_p(x), _p(th))
+
+
+def exact_genz_product_peak(theta, s) -> float:
+    theta = np.ascontiguousarray(theta, dtype=np.float32)
+    return lib().qo_exact_genz_product_peak(s, _p(theta))
+
+
+def exact_genz_oscillatory(theta, s) -> float:
+    theta = np.ascontiguousarray(theta, dtype=np.float32)
+    return lib().qo_exact_genz_oscillatory(s, _p(theta))
+
+
+def exact_gaussmix(theta, with_grad=False):
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    grad = np.zeros(16)
+    v = lib().qo_exact_gaussmix(_p(th), _p(grad) if with_grad else None)
+    return (v, grad) if with_grad else v

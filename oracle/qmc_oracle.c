@@ -1,0 +1,488 @@
+/*
+ * qmc_oracle.c -- plain, slow CPU oracle for the QMC hot path of
+ * Keller, Waechter, Binder, "Quasi-Monte Carlo Algorithms (not only) for
+ * Graphics Software" (arXiv 2307.15584).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference leg of bench.py may load this library.  The CUDA
+ * product path never calls it, and the two share no code, header, table or
+ * constant generator: each writes its arithmetic from the paper (and from the
+ * readings the library documents where the paper is silent).
+ *
+ * Every routine computes its result the literal way -- one index bit, one
+ * digit, one sample at a time, in the order the paper states -- and all
+ * integrand arithmetic is fp64.  Nothing is blocked, fused or reordered.
+ *
+ * Pins (tests/test_oracle_*.py check these against things other than this
+ * file): the float mapping against an integer-truncation closed form and the
+ * paper's special cases; dimension 0 against the radical inverse in exact
+ * rational arithmetic; dimensions 0-1 against the (0,m,2)-net property by
+ * brute-force counting; the polynomial enumeration against the counts
+ * phi(2^d-1)/d; dimension 1 against the Pascal matrix mod 2; the lattice
+ * against its closed form; integrands against closed-form integrals and
+ * numerical quadrature; gradients against finite differences.
+ *
+ * Parity unpinned: the exact output bits of qo_nested_scramble.  The paper
+ * names Owen scrambling but prints no algorithm; the hash below is this
+ * library's own definition.  Its structure (nestedness, bijectivity, exact
+ * per-point uniformity over seeds, preservation of the net property) is
+ * pinned; its particular constants are not pinned to anything in the paper.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#define QO_EXPORT __attribute__((visibility("default")))
+
+enum { QO_SOURCE_SOBOL = 0, QO_SOURCE_LATTICE = 1 };
+enum { QO_SCRAMBLE_NONE = 0, QO_SCRAMBLE_XOR = 1, QO_SCRAMBLE_NESTED = 2 };
+enum {
+    QO_F_BILINEAR2D = 0,
+    QO_F_GENZ_PRODUCT_PEAK = 1,
+    QO_F_GENZ_OSCILLATORY = 2,
+    QO_F_GAUSSMIX4_6D = 3
+};
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.1: floating point conversion.                                      */
+/* ------------------------------------------------------------------------ */
+
+/* The best fp32 representation of u / 2^32 inside [0,1): the largest float
+ * that is not above the exact value (0 for u = 0).  Sec. 2.1 asks for a value
+ * in the right-open unit interval, so rounding may never go up. */
+QO_EXPORT float qo_map_u32_to_unifloat(uint32_t u)
+{
+    if (u == 0) return 0.0f;
+    double exact = (double)u / 4294967296.0; /* exact: u has <= 32 significant bits */
+    float f = (float)exact;                  /* nearest float, may lie above */
+    if ((double)f > exact) f = nextafterf(f, 0.0f);
+    return f;
+}
+
+QO_EXPORT void qo_map_array(const uint32_t* u, uint64_t n, float* out)
+{
+    for (uint64_t k = 0; k < n; ++k) out[k] = qo_map_u32_to_unifloat(u[k]);
+}
+
+/* Mirror the 32 bits of v: bit b moves to bit 31-b. */
+QO_EXPORT uint32_t qo_bit_reverse(uint32_t v)
+{
+    uint32_t r = 0;
+    for (int b = 0; b < 32; ++b)
+        if ((v >> b) & 1u) r |= 1u << (31 - b);
+    return r;
+}
+
+/* Sec. 2.2: radical inverse phi_b(i) = sum_k a_k(i) b^(-k-1), returned as the
+ * integer floor(phi_b(i) * 2^32).  Digits are peeled off one at a time. */
+QO_EXPORT uint32_t qo_radical_inverse_u32(uint32_t b, uint64_t i)
+{
+    /* numerator / denominator of phi_b(i) as exact integers */
+    unsigned __int128 num = 0, den = 1;
+    while (i > 0) {
+        num = num * b + (i % b);
+        den *= b;
+        i /= b;
+    }
+    return (uint32_t)((num << 32) / den);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.3, Eq. (ts): Sobol' generator matrices over GF(2).                 */
+/* ------------------------------------------------------------------------ */
+
+/* Multiplicative order of x modulo the GF(2) polynomial p of degree d with
+ * p(0) = 1 (bit k of p is the coefficient of x^k), found by multiplying by x
+ * until the residue returns to 1; 0 when it does not within 2^d steps. */
+static uint32_t order_of_x(uint32_t p, uint32_t d)
+{
+    uint32_t r = 1;
+    for (uint32_t k = 1; k <= (1u << d); ++k) {
+        r <<= 1;                    /* multiply by x */
+        if ((r >> d) & 1u) r ^= p;  /* reduce modulo p */
+        if (r == 1u) return k;
+    }
+    return 0;
+}
+
+/* All primitive polynomials of degree 1..max_degree, by increasing degree and
+ * then increasing integer encoding.  A polynomial of degree d with p(0) = 1
+ * is primitive exactly when x has order 2^d - 1 modulo p.  Writes at most cap
+ * encodings and returns how many exist. */
+QO_EXPORT uint32_t qo_primitive_polynomials(uint32_t max_degree, uint32_t* out, uint32_t cap)
+{
+    uint32_t n = 0;
+    for (uint32_t d = 1; d <= max_degree; ++d)
+        for (uint32_t p = (1u << d) | 1u; p < (2u << d); p += 2)
+            if (order_of_x(p, d) == (1u << d) - 1u) {
+                if (n < cap) out[n] = p;
+                ++n;
+            }
+    return n;
+}
+
+static uint32_t degree_of(uint32_t p)
+{
+    uint32_t d = 0;
+    while (p >> (d + 1)) ++d;
+    return d;
+}
+
+/* Generator matrices of the s-dimensional Sobol' sequence, as 32 columns per
+ * dimension: C[32*j + k] is the image of index bit k, bit 31 being the first
+ * digit b^-1 of Eq. (ts).
+ *   dimension 0: the identity (van der Corput, phi_2);
+ *   dimension j >= 1: the j-th primitive polynomial of the enumeration above,
+ *   initial direction numbers m_k = (raw[7*j + k - 1] mod 2^k) | 1 for k <= deg,
+ *   then m_k = m_{k-d} ^ (m_{k-d} << d) ^ XOR_{l=1}^{d-1} a_l (m_{k-l} << l)
+ *   for k = d+1..32 (a_l the coefficient of x^(d-l)), column k-1 = m_k << (32-k).
+ * Returns 0, or -1 when s exceeds 1 + the number of polynomials of degree <= 7. */
+QO_EXPORT int qo_sobol_matrices(uint32_t s, const uint32_t* raw, uint32_t* C)
+{
+    uint32_t polys[64];
+    uint32_t npoly = qo_primitive_polynomials(7, polys, 64);
+    if (s > npoly + 1) return -1;
+    for (uint32_t j = 0; j < s; ++j) {
+        if (j == 0) {
+            for (uint32_t k = 0; k < 32; ++k) C[k] = 1u << (31 - k);
+            continue;
+        }
+        uint32_t p = polys[j - 1];
+        uint32_t d = degree_of(p);
+        uint64_t m[33];
+        for (uint32_t k = 1; k <= d; ++k)
+            m[k] = (raw[7 * j + (k - 1)] % (1ull << k)) | 1ull;
+        for (uint32_t k = d + 1; k <= 32; ++k) {
+            uint64_t v = m[k - d] ^ (m[k - d] << d);
+            for (uint32_t l = 1; l < d; ++l)
+                if ((p >> (d - l)) & 1u) v ^= m[k - l] << l;
+            m[k] = v;
+        }
+        for (uint32_t k = 1; k <= 32; ++k)
+            C[32 * j + (k - 1)] = (uint32_t)(m[k] << (32 - k));
+    }
+    return 0;
+}
+
+/* Eq. (ts) over F_2 and Alg. 3 with a zero scramble: the XOR of the columns
+ * selected by the set bits of the index. */
+QO_EXPORT uint32_t qo_sobol_u32(const uint32_t* Cj, uint32_t i)
+{
+    uint32_t y = 0;
+    for (uint32_t k = 0; k < 32; ++k)
+        if ((i >> k) & 1u) y ^= Cj[k];
+    return y;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.1 / 2.3 / 2.5.2: randomisation kept in integers.                   */
+/* ------------------------------------------------------------------------ */
+
+/* Hash-based nested (Owen-type) scramble of the 32 digits of y.  The digits
+ * are mirrored so that the first digit b^-1 sits in bit 0; each step below
+ * changes bit b only as a function of bits below b (an add, a multiply by an
+ * odd number, or an XOR with a multiple by an even number), so digit d of the
+ * result is digit d of the input flipped by a function of the digits before
+ * it.  Arithmetic is mod 2^32, carried in 64 bits and masked. */
+QO_EXPORT uint32_t qo_nested_scramble(uint32_t y, uint32_t seed)
+{
+    const uint64_t M = 0xFFFFFFFFull;
+    uint64_t v = qo_bit_reverse(y);
+    uint64_t odd = ((((uint64_t)seed << 16) | ((uint64_t)seed >> 16)) & M) | 1ull;
+    v = (v + seed) & M;
+    v = (v ^ (v * 0xD37A65C4ull)) & M;
+    v = (v * odd) & M;
+    v = (v ^ (v * 0x2AAE6212ull)) & M;
+    v = (v ^ (v * 0x2BB2601Eull)) & M;
+    return qo_bit_reverse((uint32_t)v);
+}
+
+static uint32_t randomise_sobol(uint32_t y, uint32_t mode, uint32_t seed)
+{
+    if (mode == QO_SCRAMBLE_XOR) return y ^ seed;  /* Sec. 2.3: random digital shift */
+    if (mode == QO_SCRAMBLE_NESTED) return qo_nested_scramble(y, seed);
+    return y;
+}
+
+/* Materialised Sobol' points: row r holds point begin + r, dimension j at
+ * column j; both outputs optional. */
+QO_EXPORT void qo_sobol_points(const uint32_t* C, uint32_t s, uint64_t begin, uint64_t count,
+                               uint32_t mode, const uint32_t* seeds, uint32_t* out_u32,
+                               float* out_f32)
+{
+    for (uint64_t r = 0; r < count; ++r) {
+        uint32_t i = (uint32_t)(begin + r);
+        for (uint32_t j = 0; j < s; ++j) {
+            uint32_t y = qo_sobol_u32(C + 32 * j, i);
+            y = randomise_sobol(y, mode, seeds ? seeds[j] : 0u);
+            if (out_u32) out_u32[r * s + j] = y;
+            if (out_f32) out_f32[r * s + j] = qo_map_u32_to_unifloat(y);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.4, Eq. (R1LS) and Alg. 4: rank-1 lattice sequence in base 2.       */
+/* ------------------------------------------------------------------------ */
+
+/* Component j of point k, as an integer in units of 2^-32:
+ * (phi_2(k) * g_j + shift_j) mod 1, with g_j forced odd (Alg. 4 sets its
+ * least significant bit) and the Cranley-Patterson shift added mod 2^32.
+ * Backward enumeration uses phi_2(2^32 - 1 - k) as Alg. 4 does. */
+QO_EXPORT uint32_t qo_lattice_u32(uint32_t k, uint32_t g, uint32_t shift, uint32_t backward)
+{
+    uint32_t phi = qo_bit_reverse(backward ? 0xFFFFFFFFu - k : k);
+    uint64_t prod = (uint64_t)phi * (uint64_t)(g | 1u);
+    return (uint32_t)((prod + shift) & 0xFFFFFFFFull);
+}
+
+QO_EXPORT void qo_lattice_points(const uint32_t* g, const uint32_t* shift, uint32_t s,
+                                 uint64_t begin, uint64_t count, uint32_t backward,
+                                 uint32_t* out_u32, float* out_f32)
+{
+    for (uint64_t r = 0; r < count; ++r) {
+        uint32_t k = (uint32_t)(begin + r);
+        for (uint32_t j = 0; j < s; ++j) {
+            uint32_t x = qo_lattice_u32(k, g[j], shift ? shift[j] : 0u, backward);
+            if (out_u32) out_u32[r * s + j] = x;
+            if (out_f32) out_f32[r * s + j] = qo_map_u32_to_unifloat(x);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.6: test integrands with analytic integrals, in fp64.               */
+/* Parameters are fp32 values promoted exactly to double.                    */
+/* ------------------------------------------------------------------------ */
+
+/* f(x, y) = (1 + (x - 1/2)/2) (1 + (y - 1/2)/2); its integral over [0,1)^2 is 1. */
+static double f_bilinear(const double* x)
+{
+    return (1.0 + 0.5 * (x[0] - 0.5)) * (1.0 + 0.5 * (x[1] - 0.5));
+}
+
+/* Genz product peak: prod_j 1 / (a_j^-2 + (x_j - u_j)^2); theta = a[s], u[s]. */
+static double f_genz_product_peak(const double* x, uint32_t s, const float* theta)
+{
+    double f = 1.0;
+    for (uint32_t j = 0; j < s; ++j) {
+        double a = theta[j], u = theta[s + j];
+        double d = x[j] - u;
+        f *= 1.0 / (1.0 / (a * a) + d * d);
+    }
+    return f;
+}
+
+/* Genz oscillatory: cos(2 pi u_1 + sum_j a_j x_j); theta = a[s], u[s]. */
+static double f_genz_oscillatory(const double* x, uint32_t s, const float* theta)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    double arg = two_pi * (double)theta[s];
+    for (uint32_t j = 0; j < s; ++j) arg += (double)theta[j] * x[j];
+    return cos(arg);
+}
+
+/* Mixture of four separable Gaussians in six dimensions.  Component c uses
+ * theta[4c..4c+3] = (w_c, mu_c, nu_c, sigma_c): mean mu_c in dimensions
+ * 0, 2, 4, mean nu_c in dimensions 1, 3, 5, width sigma_c in all six:
+ *   f = sum_c w_c exp(-sum_d (x_d - m_{c,d})^2 / (2 sigma_c^2)).
+ * When grad is given, it receives df/dtheta (16 values). */
+static double f_gaussmix(const double* x, const float* theta, double* grad)
+{
+    double f = 0.0;
+    for (uint32_t c = 0; c < 4; ++c) {
+        double w = theta[4 * c + 0], mu = theta[4 * c + 1];
+        double nu = theta[4 * c + 2], sg = theta[4 * c + 3];
+        double q = 0.0, se = 0.0, so = 0.0;
+        for (uint32_t d = 0; d < 6; ++d) {
+            double m = (d % 2 == 0) ? mu : nu;
+            double diff = x[d] - m;
+            q += diff * diff;
+            if (d % 2 == 0) se += diff; else so += diff;
+        }
+        double G = exp(-q / (2.0 * sg * sg));
+        f += w * G;
+        if (grad) {
+            grad[4 * c + 0] = G;
+            grad[4 * c + 1] = w * G * se / (sg * sg);
+            grad[4 * c + 2] = w * G * so / (sg * sg);
+            grad[4 * c + 3] = w * G * q / (sg * sg * sg);
+        }
+    }
+    return f;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.5: one integral, samples reduced in index order.                   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { double s, c; } neumaier;
+
+/* Neumaier's compensated addition (the paper names Kahan's algorithm). */
+static void neu_add(neumaier* a, double v)
+{
+    double t = a->s + v;
+    if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;
+    else a->c += (v - t) + a->s;
+    a->s = t;
+}
+
+/* QMC estimate (1/n) sum_{i<n} f(x_i; theta) of one integral.
+ *   source 0 (Sobol'): x_i = Sobol' point i of C[s][32] randomised by
+ *     `scramble` with seeds[s];
+ *   source 1 (lattice): x_i = lattice point i of g[s] shifted by seeds[s]
+ *     (the Cranley-Patterson rotation), backward when scramble & 1.
+ * Coordinates are the fp32 values of the float mapping, promoted to fp64.
+ * Outputs (each may be NULL except est): est = estimate; mass = (1/n) sum |f|;
+ * grad[16] = (1/n) sum df/dtheta and grad_mass[16] = (1/n) sum |df/dtheta|
+ * (Gaussian mixture only).  n = 0 gives zeros.  Returns 0, or -1 on bad
+ * arguments. */
+QO_EXPORT int qo_integrate_one(uint32_t source, uint32_t integrand, uint32_t s,
+                               uint32_t scramble, const uint32_t* C, const uint32_t* g,
+                               const uint32_t* seeds, uint32_t n, const float* theta,
+                               double* est, double* mass, double* grad, double* grad_mass)
+{
+    if (s == 0 || s > 32) return -1;
+    if (integrand == QO_F_BILINEAR2D && s != 2) return -1;
+    if (integrand == QO_F_GAUSSMIX4_6D && s != 6) return -1;
+    if (integrand > QO_F_GAUSSMIX4_6D || source > QO_SOURCE_LATTICE) return -1;
+
+    neumaier sum = {0, 0}, abs_sum = {0, 0};
+    neumaier gsum[16], gabs[16];
+    for (int k = 0; k < 16; ++k) gsum[k] = gabs[k] = (neumaier){0, 0};
+
+    double x[32], df[16];
+    for (uint32_t i = 0; i < n; ++i) {
+        for (uint32_t j = 0; j < s; ++j) {
+            uint32_t v;
+            if (source == QO_SOURCE_SOBOL)
+                v = randomise_sobol(qo_sobol_u32(C + 32 * j, i), scramble, seeds ? seeds[j] : 0u);
+            else
+                v = qo_lattice_u32(i, g[j], seeds ? seeds[j] : 0u, scramble & 1u);
+            x[j] = (double)qo_map_u32_to_unifloat(v);
+        }
+        double f;
+        switch (integrand) {
+        case QO_F_BILINEAR2D: f = f_bilinear(x); break;
+        case QO_F_GENZ_PRODUCT_PEAK: f = f_genz_product_peak(x, s, theta); break;
+        case QO_F_GENZ_OSCILLATORY: f = f_genz_oscillatory(x, s, theta); break;
+        default: f = f_gaussmix(x, theta, grad ? df : NULL); break;
+        }
+        neu_add(&sum, f);
+        neu_add(&abs_sum, fabs(f));
+        if (grad && integrand == QO_F_GAUSSMIX4_6D)
+            for (int k = 0; k < 16; ++k) {
+                neu_add(&gsum[k], df[k]);
+                neu_add(&gabs[k], fabs(df[k]));
+            }
+    }
+    double inv = n ? 1.0 / (double)n : 0.0;
+    *est = n ? (sum.s + sum.c) / (double)n : 0.0;
+    if (mass) *mass = (abs_sum.s + abs_sum.c) * inv;
+    if (grad)
+        for (int k = 0; k < 16; ++k) {
+            grad[k] = n ? (gsum[k].s + gsum[k].c) / (double)n : 0.0;
+            if (grad_mass) grad_mass[k] = (gabs[k].s + gabs[k].c) * inv;
+        }
+    return 0;
+}
+
+/* Integrand value (and Gaussian-mixture gradient) at one fp64 point; used by
+ * the finite-difference pins. */
+QO_EXPORT double qo_integrand(uint32_t integrand, uint32_t s, const double* x,
+                              const float* theta, double* grad)
+{
+    switch (integrand) {
+    case QO_F_BILINEAR2D: return f_bilinear(x);
+    case QO_F_GENZ_PRODUCT_PEAK: return f_genz_product_peak(x, s, theta);
+    case QO_F_GENZ_OSCILLATORY: return f_genz_oscillatory(x, s, theta);
+    default: return f_gaussmix(x, theta, grad);
+    }
+}
+
+/* Gaussian-mixture integrand with fp64 parameters (for central differences in
+ * theta, whose perturbed values are not fp32). */
+QO_EXPORT double qo_gaussmix_f64(const double* x, const double* th)
+{
+    double f = 0.0;
+    for (uint32_t c = 0; c < 4; ++c) {
+        double q = 0.0;
+        for (uint32_t d = 0; d < 6; ++d) {
+            double diff = x[d] - ((d % 2 == 0) ? th[4 * c + 1] : th[4 * c + 2]);
+            q += diff * diff;
+        }
+        f += th[4 * c + 0] * exp(-q / (2.0 * th[4 * c + 3] * th[4 * c + 3]));
+    }
+    return f;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Closed-form integrals over [0,1)^s (Sec. 2.6: test functions with        */
+/* analytic integrals).                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Product peak: prod_j a_j [atan(a_j (1 - u_j)) + atan(a_j u_j)]. */
+QO_EXPORT double qo_exact_genz_product_peak(uint32_t s, const float* theta)
+{
+    double I = 1.0;
+    for (uint32_t j = 0; j < s; ++j) {
+        double a = theta[j], u = theta[s + j];
+        I *= a * (atan(a * (1.0 - u)) + atan(a * u));
+    }
+    return I;
+}
+
+/* Oscillatory: Re[ e^{i 2 pi u_1} prod_j (e^{i a_j} - 1) / (i a_j) ]. */
+QO_EXPORT double qo_exact_genz_oscillatory(uint32_t s, const float* theta)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    double re = cos(two_pi * (double)theta[s]), im = sin(two_pi * (double)theta[s]);
+    for (uint32_t j = 0; j < s; ++j) {
+        double a = theta[j];
+        double fr, fi;  /* (e^{ia} - 1)/(ia) = sin(a)/a + i (1 - cos a)/a */
+        if (a == 0.0) { fr = 1.0; fi = 0.0; }
+        else { fr = sin(a) / a; fi = (1.0 - cos(a)) / a; }
+        double nr = re * fr - im * fi, ni = re * fi + im * fr;
+        re = nr; im = ni;
+    }
+    return re;
+}
+
+/* int_0^1 exp(-(x - m)^2 / (2 sg^2)) dx = sg sqrt(pi/2) [erf((1-m)/(sg sqrt 2)) + erf(m/(sg sqrt 2))] */
+static double gauss_1d(double m, double sg)
+{
+    const double r2 = 1.4142135623730950488016887242097;
+    const double sqrt_half_pi = 1.2533141373155002512078826424055;
+    return sg * sqrt_half_pi * (erf((1.0 - m) / (sg * r2)) + erf(m / (sg * r2)));
+}
+
+/* d/dm and d/dsg of gauss_1d */
+static double gauss_1d_dm(double m, double sg)
+{
+    return exp(-m * m / (2 * sg * sg)) - exp(-(1 - m) * (1 - m) / (2 * sg * sg));
+}
+static double gauss_1d_ds(double m, double sg)
+{
+    return (gauss_1d(m, sg) - (1 - m) * exp(-(1 - m) * (1 - m) / (2 * sg * sg)) -
+            m * exp(-m * m / (2 * sg * sg))) / sg;
+}
+
+/* sum_c w_c G(mu_c, sigma_c)^3 G(nu_c, sigma_c)^3; grad (may be NULL) gets dI/dtheta. */
+QO_EXPORT double qo_exact_gaussmix(const double* th, double* grad)
+{
+    double I = 0.0;
+    for (uint32_t c = 0; c < 4; ++c) {
+        double w = th[4 * c], mu = th[4 * c + 1], nu = th[4 * c + 2], sg = th[4 * c + 3];
+        double Gm = gauss_1d(mu, sg), Gn = gauss_1d(nu, sg);
+        double P = Gm * Gm * Gm * Gn * Gn * Gn;
+        I += w * P;
+        if (grad) {
+            grad[4 * c + 0] = P;
+            grad[4 * c + 1] = w * 3 * Gm * Gm * gauss_1d_dm(mu, sg) * Gn * Gn * Gn;
+            grad[4 * c + 2] = w * 3 * Gn * Gn * gauss_1d_dm(nu, sg) * Gm * Gm * Gm;
+            grad[4 * c + 3] = w * (3 * Gm * Gm * gauss_1d_ds(mu, sg) * Gn * Gn * Gn +
+                                   3 * Gn * Gn * gauss_1d_ds(nu, sg) * Gm * Gm * Gm);
+        }
+    }
+    return I;
+}
