@@ -1,0 +1,246 @@
+/*
+ * qmc.h -- C-ABI of libqmc_gb300.so: low-discrepancy point generation and
+ * massively parallel quasi-Monte Carlo integro-approximation on one GB300
+ * (sm_103a), after Keller, Waechter, Binder, "Quasi-Monte Carlo Algorithms
+ * (not only) for Graphics Software" (arXiv 2307.15584).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; h_* are
+ *     host pointers owned by the caller.  The library allocates no device
+ *     memory; kernels that need scratch use the caller's workspace.
+ *   - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL is
+ *     the legacy default stream).  The returned status covers argument
+ *     validation and the launch; a fault inside a kernel surfaces at the next
+ *     synchronisation, and in-kernel capacity checks set bits that
+ *     qmc_read_device_error() returns.
+ *   - Invalid arguments are rejected before anything is enqueued.  No C++
+ *     exception crosses this boundary.
+ *   - Point layouts are row-major [count][s]: row r holds point index_begin + r.
+ *   - Indices are 32-bit: index_begin + count must not exceed 2^32 (Sec. 2.5
+ *     warns that indices wrapping around in 32 bits cause subtle errors, so
+ *     the range is checked instead of wrapped).
+ */
+#ifndef QMC_GB300_H
+#define QMC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define QMC_API __attribute__((visibility("default")))
+#else
+#define QMC_API
+#endif
+
+/* cudaStream_t without including the CUDA headers. */
+typedef struct CUstream_st* qmc_stream_t;
+
+typedef enum qmc_status {
+    QMC_OK = 0,
+    QMC_ERR_INVALID_ARG = 1, /* null pointer, zero/oversized dimension, bad enum */
+    QMC_ERR_RANGE = 2,       /* index range beyond 2^32, counts beyond limits */
+    QMC_ERR_ALIGN = 3,       /* a device buffer is not aligned to its element type */
+    QMC_ERR_CUDA = 4,        /* the CUDA runtime reported an error at launch */
+    QMC_ERR_TIMEOUT = 5,     /* reserved: a bounded device wait gave up */
+    QMC_ERR_UNSUPPORTED = 6, /* a valid combination this build does not implement */
+    QMC_ERR_WORKSPACE = 7    /* workspace missing, misaligned or too small */
+} qmc_status;
+
+/* Randomisation of Sobol' points, kept in integers (Sec. 2.1, Sec. 2.3). */
+typedef enum qmc_scramble {
+    QMC_SCRAMBLE_NONE = 0,   /* plain Eq. (ts) */
+    QMC_SCRAMBLE_XOR = 1,    /* random digital shift: y ^ seed (Sec. 2.3) */
+    QMC_SCRAMBLE_NESTED = 2  /* hash-based nested (Owen-type) scramble, per-dimension seed */
+} qmc_scramble;
+
+/* Flags of rank-1 lattice points. */
+#define QMC_LATTICE_BACKWARD 1u /* enumerate phi_2(2^32-1-k) as Alg. 4 does: the origin comes last */
+
+typedef enum qmc_source {
+    QMC_SOURCE_SOBOL = 0,   /* digital (t,s)-sequence in base 2, Eq. (ts) */
+    QMC_SOURCE_LATTICE = 1  /* rank-1 lattice sequence in base 2, Eq. (R1LS) */
+} qmc_source;
+
+/* Integrands with closed-form integrals (Sec. 2.6 recommends such test
+ * functions).  theta layouts are per integral, fp32:
+ *   BILINEAR2D          s = 2, no parameters: (1 + (x-1/2)/2)(1 + (y-1/2)/2)
+ *   GENZ_PRODUCT_PEAK   1 <= s <= 16, theta = a[s], u[s]: prod_j 1/(a_j^-2 + (x_j-u_j)^2)
+ *   GENZ_OSCILLATORY    1 <= s <= 16, theta = a[s], u[s]: cos(2 pi u_1 + sum_j a_j x_j)
+ *   GAUSSMIX4_6D        s = 6, theta[16] = 4 x (w, mu, nu, sigma):
+ *                       sum_c w_c exp(-sum_d (x_d - m_{c,d})^2 / (2 sigma_c^2)),
+ *                       m_{c,d} = mu_c for even d, nu_c for odd d. */
+typedef enum qmc_integrand {
+    QMC_F_BILINEAR2D = 0,
+    QMC_F_GENZ_PRODUCT_PEAK = 1,
+    QMC_F_GENZ_OSCILLATORY = 2,
+    QMC_F_GAUSSMIX4_6D = 3
+} qmc_integrand;
+
+/* One batch of integrals that share a point source and an integrand
+ * (Sec. 2.5: many problems in parallel, no intermediate communication).
+ * Integral p takes indices 0 .. counts[p]-1 of the source, randomised with
+ * its own seeds when seeds_per_integral is set (Sec. 2.5.2, randomised QMC
+ * per processing element). */
+typedef struct qmc_problem {
+    uint32_t source;             /* qmc_source */
+    uint32_t integrand;          /* qmc_integrand */
+    uint32_t s;                  /* dimension of the points = of the integrand */
+    uint32_t randomize;          /* SOBOL: qmc_scramble; LATTICE: 0 or QMC_LATTICE_BACKWARD */
+    const uint32_t* d_matrices;  /* SOBOL: [s][32] generator columns (see qmc_sobol_points) */
+    const uint32_t* d_g;         /* LATTICE: [s] generator words, low bit forced to 1 */
+    const uint32_t* d_seeds;     /* SOBOL: scramble seeds; LATTICE: Cranley-Patterson shifts
+                                    (units of 2^-32).  [s], or [n_integrals][s] when
+                                    seeds_per_integral = 1.  NULL: no randomisation/shift. */
+    uint32_t seeds_per_integral; /* 0 or 1 */
+    uint32_t chunk;              /* samples per work item: a power of two in [32, 8192];
+                                    0 = the tuned value for this problem class, else 4096 */
+    uint32_t block;              /* threads per CTA (multiple of 32, <= 1024); 0 = tuned/256 */
+    uint32_t max_count;          /* upper bound of every count; sizes the workspace when the
+                                    host does not pass counts to qmc_integrate_workspace_bytes */
+    uint32_t with_gradient;      /* 1: size the workspace for qmc_integrate_backward and
+                                    qmc_integrate_fwd_bwd (17 partial sums per work item) */
+} qmc_problem;
+
+/* ABI revision of this header (bumped on any incompatible change). */
+QMC_API uint32_t qmc_abi_version(void);
+
+/* Human-readable name of a status code (static storage). */
+QMC_API const char* qmc_status_string(qmc_status status);
+
+/*
+ * Sobol' generator matrices (Sec. 2.3, Eq. (ts); host only, no CUDA call).
+ *   s            number of dimensions, 1 <= s <= 37 (1 + the 36 primitive
+ *                polynomials of degree <= 7)
+ *   h_raw_init   [s][7] random words; dimension j >= 1 takes its initial
+ *                direction numbers m_k = (h_raw_init[j][k-1] mod 2^k) | 1 for
+ *                k <= degree (row 0 is ignored)
+ *   h_matrices   out: [s][32]; column k of dimension j is the image of index
+ *                bit k, its bit 31 being the first digit 2^-1
+ * Dimension 0 is the identity (the van der Corput sequence, phi_2);
+ * dimension j >= 1 uses the j-th primitive polynomial over GF(2), enumerated
+ * by degree and then by integer encoding (x+1 first, giving the Pascal matrix
+ * mod 2), with the Sobol' recurrence
+ *   m_k = m_{k-d} ^ (m_{k-d} << d) ^ XOR_{l=1}^{d-1} a_l (m_{k-l} << l),
+ * a_l the coefficient of x^(d-l), and column k-1 = m_k << (32-k).
+ */
+QMC_API qmc_status qmc_sobol_matrices(uint32_t s, const uint32_t* h_raw_init, uint32_t* h_matrices);
+
+/*
+ * Materialised Sobol' points (Alg. 3, Eq. (ts), Sec. 2.1 float conversion).
+ *   d_matrices   [s][32] generator columns (layout of qmc_sobol_matrices)
+ *   s            1 <= s <= 1024
+ *   index_begin, count   indices index_begin .. index_begin+count-1; their
+ *                end must not exceed 2^32 (QMC_ERR_RANGE)
+ *   scramble     qmc_scramble; d_seeds [s] required unless NONE
+ *   d_out_u32    [count][s] integer points (units of 2^-32), or NULL
+ *   d_out_f32    [count][s] map_u32_to_unifloat of the same values (every
+ *                component in [0,1)), or NULL; at least one output required
+ * Outputs must be 4-byte aligned (QMC_ERR_ALIGN); the 128-bit store path runs
+ * when both are 16-byte aligned and index_begin is a multiple of the warp's
+ * row group, a scalar path otherwise.  count = 0 is a no-op.
+ */
+QMC_API qmc_status qmc_sobol_points(const uint32_t* d_matrices, uint32_t s, uint64_t index_begin,
+                            uint64_t count, uint32_t scramble, const uint32_t* d_seeds,
+                            uint32_t* d_out_u32, float* d_out_f32, qmc_stream_t stream);
+
+/*
+ * Materialised rank-1 lattice points (Eq. (R1LS), Alg. 4):
+ *   x_j(k) = (phi_2(k) g_j + shift_j) mod 1, computed as a 32-bit multiply-add.
+ *   d_g          [s] generator words; the low bit is forced to 1 (Alg. 4), so
+ *                every dimension is stratified at powers of two (Sec. 2.4.1)
+ *   d_shift      [s] Cranley-Patterson shifts in units of 2^-32, or NULL
+ *   flags        0 or QMC_LATTICE_BACKWARD (phi_2(2^32-1-k), Alg. 4)
+ * Other arguments, layouts and errors as for qmc_sobol_points.
+ */
+QMC_API qmc_status qmc_lattice_points(const uint32_t* d_g, const uint32_t* d_shift, uint32_t s,
+                              uint64_t index_begin, uint64_t count, uint32_t flags,
+                              uint32_t* d_out_u32, float* d_out_f32, qmc_stream_t stream);
+
+/*
+ * Bytes of workspace qmc_integrate / qmc_integrate_backward /
+ * qmc_integrate_fwd_bwd / qmc_integrate_points need for n_integrals
+ * integrals.  With h_counts (host copy of the counts) the size is exact; with
+ * NULL it is the worst case for counts <= p->max_count.  When p->chunk is 0
+ * the size covers every chunk the tuner may choose.  The work-item capacity
+ * of a call is derived from the workspace_bytes it is given; a call whose
+ * items do not fit integrates nothing, writes NaN results and sets bit 0 of
+ * the device error word.  Returns 0 for an invalid problem.
+ */
+QMC_API size_t qmc_integrate_workspace_bytes(const qmc_problem* p, uint32_t n_integrals,
+                                     const uint32_t* h_counts);
+
+/*
+ * Batched QMC integration (Sec. 2.5, parallel integro-approximation):
+ *   d_estimate[p] = (1/counts[p]) sum_{i < counts[p]} f(x_i; theta_p), 0 when
+ *   counts[p] = 0.
+ * Points are generated, evaluated in fp32 and summed with compensated (Neumaier)
+ * fp32 sums inside one persistent kernel; work items are (integral, chunk of
+ * p->chunk samples) and each writes its compensated partial to a fixed slot,
+ * so the result does not depend on scheduling.  A last kernel adds each
+ * integral's partials in index order in fp64 (Sec. 2.5.1: controlled order of
+ * additions) and divides by the count.
+ *   d_counts     [n_integrals] sample counts, each <= 2^32 - 1
+ *   d_theta      [n_integrals][P] fp32 parameters (layout of qmc_integrand), or
+ *                NULL for BILINEAR2D
+ *   d_estimate   out: [n_integrals] fp64
+ *   d_workspace  >= qmc_integrate_workspace_bytes(), 256-byte aligned
+ */
+QMC_API qmc_status qmc_integrate(const qmc_problem* p, uint32_t n_integrals, const uint32_t* d_counts,
+                         const float* d_theta, double* d_estimate, void* d_workspace,
+                         size_t workspace_bytes, qmc_stream_t stream);
+
+/*
+ * Adjoint of qmc_integrate with respect to theta (GAUSSMIX4_6D only):
+ *   d_grad_theta[p][k] = d_grad_estimate[p] (1/counts[p]) sum_i df(x_i; theta_p)/dtheta_k.
+ * The points are regenerated, never stored; sums as in qmc_integrate.
+ *   d_grad_estimate [n_integrals] fp64 upstream gradient dL/d estimate
+ *   d_grad_theta    out: [n_integrals][16] fp32
+ */
+QMC_API qmc_status qmc_integrate_backward(const qmc_problem* p, uint32_t n_integrals,
+                                  const uint32_t* d_counts, const float* d_theta,
+                                  const double* d_grad_estimate, float* d_grad_theta,
+                                  void* d_workspace, size_t workspace_bytes, qmc_stream_t stream);
+
+/*
+ * Fused forward + backward for the squared-error loss (GAUSSMIX4_6D only):
+ * one pass over the points computes I_p and J_p = (1/n_p) sum_i df/dtheta, then
+ *   d_estimate[p]   = I_p
+ *   d_loss[0]       = sum_p (I_p - target_p)^2        (fp64, fixed order)
+ *   d_grad_theta[p] = 2 (I_p - target_p) J_p           (fp32)
+ *   d_target     [n_integrals] fp64
+ */
+QMC_API qmc_status qmc_integrate_fwd_bwd(const qmc_problem* p, uint32_t n_integrals,
+                                 const uint32_t* d_counts, const float* d_theta,
+                                 const double* d_target, double* d_estimate,
+                                 float* d_grad_theta, double* d_loss, void* d_workspace,
+                                 size_t workspace_bytes, qmc_stream_t stream);
+
+/*
+ * Unfused comparison path: integrate points that were materialised in HBM
+ * by qmc_sobol_points / qmc_lattice_points (d_points [rows][s] fp32).
+ * Integral p reads rows offset_p .. offset_p + counts[p] - 1, where
+ * offset_p = sum_{q<p} counts[q], or rows 0 .. counts[p]-1 when
+ * points_shared = 1.  Sums and workspace as for qmc_integrate (the problem's
+ * source fields are ignored; p->integrand, p->s, p->chunk, p->block apply).
+ */
+QMC_API qmc_status qmc_integrate_points(const qmc_problem* p, uint32_t n_integrals,
+                                const uint32_t* d_counts, const float* d_points,
+                                uint32_t points_shared, const float* d_theta,
+                                double* d_estimate, void* d_workspace, size_t workspace_bytes,
+                                qmc_stream_t stream);
+
+/* In-kernel error bits of the last integration that used this workspace
+ * (0 = none; bit 0: more work items than the workspace holds).  Synchronises
+ * `stream`. */
+QMC_API qmc_status qmc_read_device_error(const void* d_workspace, uint32_t* h_error_bits,
+                                 qmc_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QMC_GB300_H */

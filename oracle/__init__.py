@@ -84,10 +84,17 @@ def _threads(threads):
     return threads or (os.cpu_count() or 1)
 
 
-def map_u32_to_unifloat(u) -> np.ndarray:
+def map_u32_to_unifloat(u, threads=None) -> np.ndarray:
     u = np.ascontiguousarray(u, dtype=np.uint32)
     out = np.empty(u.shape, np.float32)
-    lib().qo_map_array(_p(u), u.size, _p(out))
+    uf, of = u.reshape(-1), out.reshape(-1)
+
+    def run(r0, n):
+        n = min(n, uf.size - r0)
+        lib().qo_map_array(uf[r0:].ctypes.data, n, of[r0:].ctypes.data)
+
+    if uf.size:
+        _chunked(uf.size, threads if uf.size > (1 << 20) else 1, run)
     return out
 
 

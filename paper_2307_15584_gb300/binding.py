@@ -1,0 +1,214 @@
+"""ctypes binding of libqmc_gb300.so (include/qmc.h): argument marshalling only.
+
+Every function named ``qmc_*`` here calls the C entry point of the same name
+with device pointers taken from torch tensors and the current torch CUDA
+stream.  Nothing is computed in Python and there is no CPU fallback: importing
+this module raises when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import c_double, c_size_t, c_uint32, c_uint64, c_void_p
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqmc_gb300.so")
+if not os.path.exists(LIB_PATH):
+    raise RuntimeError(
+        f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`; "
+        "the QMC path has no CPU fallback")
+_lib = ctypes.CDLL(LIB_PATH)
+
+# enums of include/qmc.h
+QMC_OK = 0
+STATUS_NAMES = {0: "QMC_OK", 1: "QMC_ERR_INVALID_ARG", 2: "QMC_ERR_RANGE", 3: "QMC_ERR_ALIGN",
+                4: "QMC_ERR_CUDA", 5: "QMC_ERR_TIMEOUT", 6: "QMC_ERR_UNSUPPORTED", 7: "QMC_ERR_WORKSPACE"}
+SCRAMBLE_NONE, SCRAMBLE_XOR, SCRAMBLE_NESTED = 0, 1, 2
+LATTICE_BACKWARD = 1
+SOURCE_SOBOL, SOURCE_LATTICE = 0, 1
+F_BILINEAR2D, F_GENZ_PRODUCT_PEAK, F_GENZ_OSCILLATORY, F_GAUSSMIX4_6D = 0, 1, 2, 3
+
+EXPORTED = ["qmc_abi_version", "qmc_status_string", "qmc_sobol_matrices", "qmc_sobol_points",
+            "qmc_lattice_points", "qmc_integrate_workspace_bytes", "qmc_integrate",
+            "qmc_integrate_backward", "qmc_integrate_fwd_bwd", "qmc_integrate_points",
+            "qmc_read_device_error"]
+
+
+class QMCError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.qmc_status_string(status).decode()
+        super().__init__(f"{where}: {msg}")
+
+
+class qmc_problem(ctypes.Structure):
+    _fields_ = [("source", c_uint32), ("integrand", c_uint32), ("s", c_uint32), ("randomize", c_uint32),
+                ("d_matrices", c_void_p), ("d_g", c_void_p), ("d_seeds", c_void_p),
+                ("seeds_per_integral", c_uint32), ("chunk", c_uint32), ("block", c_uint32),
+                ("max_count", c_uint32), ("with_gradient", c_uint32)]
+
+
+_P = c_void_p
+_sigs = {
+    "qmc_abi_version": (c_uint32, []),
+    "qmc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "qmc_sobol_matrices": (ctypes.c_int, [c_uint32, _P, _P]),
+    "qmc_sobol_points": (ctypes.c_int, [_P, c_uint32, c_uint64, c_uint64, c_uint32, _P, _P, _P, _P]),
+    "qmc_lattice_points": (ctypes.c_int, [_P, _P, c_uint32, c_uint64, c_uint64, c_uint32, _P, _P, _P]),
+    "qmc_integrate_workspace_bytes": (c_size_t, [ctypes.POINTER(qmc_problem), c_uint32, _P]),
+    "qmc_integrate": (ctypes.c_int, [ctypes.POINTER(qmc_problem), c_uint32, _P, _P, _P, _P, c_size_t, _P]),
+    "qmc_integrate_backward": (ctypes.c_int, [ctypes.POINTER(qmc_problem), c_uint32, _P, _P, _P, _P, _P,
+                                              c_size_t, _P]),
+    "qmc_integrate_fwd_bwd": (ctypes.c_int, [ctypes.POINTER(qmc_problem), c_uint32, _P, _P, _P, _P, _P, _P,
+                                             _P, c_size_t, _P]),
+    "qmc_integrate_points": (ctypes.c_int, [ctypes.POINTER(qmc_problem), c_uint32, _P, _P, c_uint32, _P, _P,
+                                            _P, c_size_t, _P]),
+    "qmc_read_device_error": (ctypes.c_int, [_P, ctypes.POINTER(c_uint32), _P]),
+}
+for _name, (_res, _args) in _sigs.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+def _check(status: int, where: str) -> None:
+    if status != QMC_OK:
+        raise QMCError(status, where)
+
+
+def _dev(t):
+    """Device pointer of a CUDA tensor (None passes NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def u32_tensor(a, device="cuda") -> torch.Tensor:
+    """uint32 numpy data as an int32 tensor holding the same bits."""
+    a = np.ascontiguousarray(a, dtype=np.uint32)
+    return torch.from_numpy(a.view(np.int32)).to(device)
+
+
+def as_u32(t: torch.Tensor) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+# ----------------------------------------------------------------- C entry points
+def qmc_abi_version() -> int:
+    return _lib.qmc_abi_version()
+
+
+def qmc_status_string(status: int) -> str:
+    return _lib.qmc_status_string(status).decode()
+
+
+def qmc_sobol_matrices(s: int, raw_init) -> np.ndarray:
+    raw = np.ascontiguousarray(raw_init, dtype=np.uint32)
+    out = np.zeros((s, 32), np.uint32)
+    _check(_lib.qmc_sobol_matrices(s, raw.ctypes.data if raw.size else None, out.ctypes.data),
+           "qmc_sobol_matrices")
+    return out
+
+
+def qmc_sobol_points(matrices, s, index_begin, count, scramble, seeds, out_u32, out_f32, stream=None):
+    _check(_lib.qmc_sobol_points(_dev(matrices), s, index_begin, count, scramble, _dev(seeds), _dev(out_u32),
+                                 _dev(out_f32), _stream(stream)), "qmc_sobol_points")
+
+
+def qmc_lattice_points(g, shift, s, index_begin, count, flags, out_u32, out_f32, stream=None):
+    _check(_lib.qmc_lattice_points(_dev(g), _dev(shift), s, index_begin, count, flags, _dev(out_u32),
+                                   _dev(out_f32), _stream(stream)), "qmc_lattice_points")
+
+
+def qmc_integrate_workspace_bytes(problem: qmc_problem, n_integrals: int, h_counts=None) -> int:
+    hc = None if h_counts is None else np.ascontiguousarray(h_counts, dtype=np.uint32)
+    return _lib.qmc_integrate_workspace_bytes(ctypes.byref(problem), n_integrals,
+                                              None if hc is None else hc.ctypes.data)
+
+
+def qmc_integrate(problem, n_integrals, counts, theta, estimate, workspace, workspace_bytes=None, stream=None):
+    wb = workspace.numel() * workspace.element_size() if workspace_bytes is None else workspace_bytes
+    _check(_lib.qmc_integrate(ctypes.byref(problem), n_integrals, _dev(counts), _dev(theta), _dev(estimate),
+                              _dev(workspace), wb, _stream(stream)), "qmc_integrate")
+
+
+def qmc_integrate_backward(problem, n_integrals, counts, theta, grad_estimate, grad_theta, workspace,
+                           workspace_bytes=None, stream=None):
+    wb = workspace.numel() * workspace.element_size() if workspace_bytes is None else workspace_bytes
+    _check(_lib.qmc_integrate_backward(ctypes.byref(problem), n_integrals, _dev(counts), _dev(theta),
+                                       _dev(grad_estimate), _dev(grad_theta), _dev(workspace), wb,
+                                       _stream(stream)), "qmc_integrate_backward")
+
+
+def qmc_integrate_fwd_bwd(problem, n_integrals, counts, theta, target, estimate, grad_theta, loss, workspace,
+                          workspace_bytes=None, stream=None):
+    wb = workspace.numel() * workspace.element_size() if workspace_bytes is None else workspace_bytes
+    _check(_lib.qmc_integrate_fwd_bwd(ctypes.byref(problem), n_integrals, _dev(counts), _dev(theta),
+                                      _dev(target), _dev(estimate), _dev(grad_theta), _dev(loss),
+                                      _dev(workspace), wb, _stream(stream)), "qmc_integrate_fwd_bwd")
+
+
+def qmc_integrate_points(problem, n_integrals, counts, points, points_shared, theta, estimate, workspace,
+                         workspace_bytes=None, stream=None):
+    wb = workspace.numel() * workspace.element_size() if workspace_bytes is None else workspace_bytes
+    _check(_lib.qmc_integrate_points(ctypes.byref(problem), n_integrals, _dev(counts), _dev(points),
+                                     int(points_shared), _dev(theta), _dev(estimate), _dev(workspace), wb,
+                                     _stream(stream)), "qmc_integrate_points")
+
+
+def qmc_read_device_error(workspace, stream=None) -> int:
+    bits = c_uint32(0)
+    _check(_lib.qmc_read_device_error(_dev(workspace), ctypes.byref(bits), _stream(stream)),
+           "qmc_read_device_error")
+    return bits.value
+
+
+# ----------------------------------------------------------------- conveniences
+def make_problem(source, integrand, s, randomize=0, matrices=None, g=None, seeds=None,
+                 seeds_per_integral=False, chunk=0, block=0, max_count=0, with_gradient=False) -> qmc_problem:
+    """A qmc_problem holding device pointers of the given tensors (keep them alive)."""
+    return qmc_problem(source, integrand, s, randomize, _dev(matrices), _dev(g), _dev(seeds),
+                       int(bool(seeds_per_integral)), chunk, block, max_count, int(bool(with_gradient)))
+
+
+def alloc_workspace(problem: qmc_problem, n_integrals: int, h_counts=None, device="cuda") -> torch.Tensor:
+    nbytes = qmc_integrate_workspace_bytes(problem, n_integrals, h_counts)
+    if nbytes == 0:
+        raise QMCError(1, "qmc_integrate_workspace_bytes")
+    # torch's caching allocator returns 512-byte aligned blocks
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def sobol_points(matrices, count, index_begin=0, scramble=SCRAMBLE_NONE, seeds=None, want_u32=True,
+                 want_f32=True, stream=None):
+    s = matrices.shape[0]
+    dev = matrices.device
+    u = torch.empty((count, s), dtype=torch.int32, device=dev) if want_u32 else None
+    f = torch.empty((count, s), dtype=torch.float32, device=dev) if want_f32 else None
+    qmc_sobol_points(matrices, s, index_begin, count, scramble, seeds, u, f, stream)
+    return u, f
+
+
+def lattice_points(g, count, index_begin=0, shift=None, backward=False, want_u32=True, want_f32=True,
+                   stream=None):
+    s = g.shape[0]
+    dev = g.device
+    u = torch.empty((count, s), dtype=torch.int32, device=dev) if want_u32 else None
+    f = torch.empty((count, s), dtype=torch.float32, device=dev) if want_f32 else None
+    qmc_lattice_points(g, shift, s, index_begin, count, LATTICE_BACKWARD if backward else 0, u, f, stream)
+    return u, f

@@ -1,0 +1,400 @@
+// api.cu -- the C-ABI of include/qmc.h: argument validation, the host-side
+// construction of Sobol' generator matrices, and kernel dispatch.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/qmc.h"
+#include "qmc_integrate.h"
+#include "qmc_internal.h"
+
+namespace qmc {
+
+const DeviceInfo& device_info() {
+  static std::mutex mu;
+  static std::vector<DeviceInfo> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  for (const DeviceInfo& d : cache)
+    if (d.device == dev) return d;
+  DeviceInfo d{};
+  d.device = dev;
+  cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&d.cc_major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&d.cc_minor, cudaDevAttrComputeCapabilityMinor, dev);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  d.smem_per_block_optin = (size_t)optin;
+  if (d.sm_count <= 0) d.sm_count = 1;
+  cache.reserve(64);
+  cache.push_back(d);
+  return cache.back();
+}
+
+WsLayout workspace_layout(uint32_t n, uint64_t capacity_items, uint32_t values_per_item) {
+  auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+  const size_t nb = ((size_t)n + 1024) / 1024;
+  WsLayout L{};
+  size_t off = 0;
+  L.header = off;
+  off += up(sizeof(WsHeader));
+  L.item_off = off;
+  off += up(((size_t)n + 1) * 4);
+  L.row_off = off;
+  off += up(((size_t)n + 1) * 8);
+  L.block_items = off;
+  off += up(nb * 8);
+  L.block_rows = off;
+  off += up(nb * 8);
+  L.loss_terms = off;
+  off += up((size_t)n * 8);
+  L.partials = off;
+  off += up((size_t)capacity_items * values_per_item * 2 * sizeof(float));
+  L.total = off;
+  return L;
+}
+
+namespace {
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// --- Sobol' matrices (Sec. 2.3).  Polynomials over GF(2) are bit masks, bit k
+// holding the coefficient of x^k. ---------------------------------------------
+
+uint32_t gf2_mulmod(uint32_t a, uint32_t b, uint32_t p, uint32_t d) {
+  uint32_t r = 0;
+  while (b) {
+    if (b & 1u) r ^= a;
+    b >>= 1;
+    a <<= 1;
+    if ((a >> d) & 1u) a ^= p;
+  }
+  return r;
+}
+
+// x^e mod p by square-and-multiply.
+uint32_t gf2_pow_x(uint64_t e, uint32_t p, uint32_t d) {
+  uint32_t base = 2u;
+  if ((base >> d) & 1u) base ^= p;
+  uint32_t r = 1u;
+  while (e) {
+    if (e & 1u) r = gf2_mulmod(r, base, p, d);
+    base = gf2_mulmod(base, base, p, d);
+    e >>= 1;
+  }
+  return r;
+}
+
+// Primitive <=> x has order exactly 2^d - 1 modulo p: x^(2^d-1) = 1 and
+// x^((2^d-1)/q) != 1 for every prime q dividing 2^d - 1.
+bool is_primitive(uint32_t p, uint32_t d) {
+  const uint64_t order = (1ull << d) - 1;
+  if (gf2_pow_x(order, p, d) != 1u) return false;
+  uint64_t n = order;
+  for (uint64_t q = 2; n > 1; ++q) {  // distinct prime factors by trial division
+    if (n % q) continue;
+    if (gf2_pow_x(order / q, p, d) == 1u) return false;
+    while (n % q == 0) n /= q;
+  }
+  return true;
+}
+
+std::vector<uint32_t> primitive_polynomials_deg7() {
+  std::vector<uint32_t> out;
+  for (uint32_t d = 1; d <= 7; ++d)
+    for (uint32_t p = (1u << d) + 1u; p < (1u << (d + 1)); p += 2u)
+      if (is_primitive(p, d)) out.push_back(p);
+  return out;
+}
+
+}  // namespace
+}  // namespace qmc
+
+using namespace qmc;
+
+extern "C" {
+
+uint32_t qmc_abi_version(void) { return 1u; }
+
+const char* qmc_status_string(qmc_status st) {
+  switch (st) {
+    case QMC_OK: return "QMC_OK";
+    case QMC_ERR_INVALID_ARG: return "QMC_ERR_INVALID_ARG: invalid argument";
+    case QMC_ERR_RANGE: return "QMC_ERR_RANGE: index or count range exceeded";
+    case QMC_ERR_ALIGN: return "QMC_ERR_ALIGN: device buffer misaligned";
+    case QMC_ERR_CUDA: return "QMC_ERR_CUDA: CUDA runtime error";
+    case QMC_ERR_TIMEOUT: return "QMC_ERR_TIMEOUT: bounded device wait expired";
+    case QMC_ERR_UNSUPPORTED: return "QMC_ERR_UNSUPPORTED: combination not implemented";
+    case QMC_ERR_WORKSPACE: return "QMC_ERR_WORKSPACE: workspace missing, misaligned or too small";
+  }
+  return "unknown qmc_status";
+}
+
+qmc_status qmc_sobol_matrices(uint32_t s, const uint32_t* h_raw_init, uint32_t* h_matrices) {
+  static const std::vector<uint32_t> polys = primitive_polynomials_deg7();
+  if (s == 0 || s > polys.size() + 1 || !h_matrices) return QMC_ERR_INVALID_ARG;
+  if (s > 1 && !h_raw_init) return QMC_ERR_INVALID_ARG;
+  for (uint32_t j = 0; j < s; ++j) {
+    uint32_t* V = h_matrices + 32 * j;  // V[k-1] = direction integer v_k
+    if (j == 0) {
+      for (uint32_t k = 1; k <= 32; ++k) V[k - 1] = 0x80000000u >> (k - 1);
+      continue;
+    }
+    const uint32_t p = polys[j - 1];
+    uint32_t d = 0;
+    while (p >> (d + 1)) ++d;
+    for (uint32_t k = 1; k <= d; ++k) {
+      const uint32_t m = (uint32_t)(h_raw_init[7 * j + k - 1] & ((1ull << k) - 1)) | 1u;
+      V[k - 1] = m << (32 - k);
+    }
+    // Bratley-Fox form of the recurrence on direction integers:
+    // v_k = v_{k-d} ^ (v_{k-d} >> d) ^ XOR_{l=1}^{d-1} a_l v_{k-l}
+    for (uint32_t k = d + 1; k <= 32; ++k) {
+      uint32_t v = V[k - d - 1] ^ (V[k - d - 1] >> d);
+      for (uint32_t l = 1; l < d; ++l)
+        if ((p >> (d - l)) & 1u) v ^= V[k - l - 1];
+      V[k - 1] = v;
+    }
+  }
+  return QMC_OK;
+}
+
+static qmc_status check_points_args(uint32_t s, uint64_t index_begin, uint64_t count,
+                                    const void* out_u32, const void* out_f32) {
+  if (s == 0 || s > 1024) return QMC_ERR_INVALID_ARG;
+  if (!out_u32 && !out_f32) return QMC_ERR_INVALID_ARG;
+  if (index_begin > (1ull << 32) || count > (1ull << 32) - index_begin) return QMC_ERR_RANGE;
+  if (((uintptr_t)out_u32 & 3u) || ((uintptr_t)out_f32 & 3u)) return QMC_ERR_ALIGN;
+  return QMC_OK;
+}
+
+qmc_status qmc_sobol_points(const uint32_t* d_matrices, uint32_t s, uint64_t index_begin,
+                            uint64_t count, uint32_t scramble, const uint32_t* d_seeds,
+                            uint32_t* d_out_u32, float* d_out_f32, qmc_stream_t stream) {
+  if (!d_matrices) return QMC_ERR_INVALID_ARG;
+  if (scramble > QMC_SCRAMBLE_NESTED) return QMC_ERR_INVALID_ARG;
+  if (scramble != QMC_SCRAMBLE_NONE && !d_seeds) return QMC_ERR_INVALID_ARG;
+  qmc_status st = check_points_args(s, index_begin, count, d_out_u32, d_out_f32);
+  if (st != QMC_OK || count == 0) return st;
+  PointsArgs a{};
+  a.matrices = d_matrices;
+  a.seeds = d_seeds;
+  a.out_u32 = d_out_u32;
+  a.out_f32 = d_out_f32;
+  a.count = count;
+  a.s = s;
+  a.index_begin = (uint32_t)index_begin;
+  a.scramble = scramble;
+  return launch_sobol_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+qmc_status qmc_lattice_points(const uint32_t* d_g, const uint32_t* d_shift, uint32_t s,
+                              uint64_t index_begin, uint64_t count, uint32_t flags,
+                              uint32_t* d_out_u32, float* d_out_f32, qmc_stream_t stream) {
+  if (!d_g || (flags & ~QMC_LATTICE_BACKWARD)) return QMC_ERR_INVALID_ARG;
+  qmc_status st = check_points_args(s, index_begin, count, d_out_u32, d_out_f32);
+  if (st != QMC_OK || count == 0) return st;
+  PointsArgs a{};
+  a.matrices = d_g;
+  a.seeds = d_shift;
+  a.out_u32 = d_out_u32;
+  a.out_f32 = d_out_f32;
+  a.count = count;
+  a.s = s;
+  a.index_begin = (uint32_t)index_begin;
+  a.scramble = flags;
+  return launch_lattice_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+
+// --------------------------------------------------------------------------
+// Integration (Sec. 2.5)
+// --------------------------------------------------------------------------
+namespace {
+
+constexpr uint32_t kDefaultChunk = 4096;
+constexpr uint32_t kMinTunedChunk = 1024;
+constexpr uint32_t kDefaultBlock = 256;
+
+uint32_t ilog2(uint32_t v) {
+  uint32_t l = 0;
+  while ((1u << (l + 1)) <= v) ++l;
+  return l;
+}
+
+qmc_status validate_problem(const qmc_problem* p, bool need_source) {
+  if (!p) return QMC_ERR_INVALID_ARG;
+  if (p->integrand > QMC_F_GAUSSMIX4_6D || p->source > QMC_SOURCE_LATTICE) return QMC_ERR_INVALID_ARG;
+  const uint32_t s = p->s;
+  if (p->integrand == QMC_F_BILINEAR2D && s != 2) return QMC_ERR_INVALID_ARG;
+  if (p->integrand == QMC_F_GAUSSMIX4_6D && s != 6) return QMC_ERR_INVALID_ARG;
+  if ((p->integrand == QMC_F_GENZ_PRODUCT_PEAK || p->integrand == QMC_F_GENZ_OSCILLATORY) &&
+      (s == 0 || s > 16))
+    return QMC_ERR_INVALID_ARG;
+  if (p->seeds_per_integral > 1) return QMC_ERR_INVALID_ARG;
+  if (p->chunk != 0 && (p->chunk < 32 || p->chunk > 8192 || (p->chunk & (p->chunk - 1))))
+    return QMC_ERR_INVALID_ARG;
+  if (p->block != 0 && (p->block % 32 || p->block > 256)) return QMC_ERR_INVALID_ARG;
+  if (need_source) {
+    if (p->source == QMC_SOURCE_SOBOL) {
+      if (!p->d_matrices || p->randomize > QMC_SCRAMBLE_NESTED) return QMC_ERR_INVALID_ARG;
+      if (p->randomize != QMC_SCRAMBLE_NONE && !p->d_seeds) return QMC_ERR_INVALID_ARG;
+    } else {
+      if (!p->d_g || (p->randomize & ~QMC_LATTICE_BACKWARD)) return QMC_ERR_INVALID_ARG;
+    }
+  }
+  return QMC_OK;
+}
+
+uint32_t values_per_item(const qmc_problem* p, bool grad) {
+  return grad ? 17u : 1u;
+}
+
+uint32_t chunk_for(const qmc_problem* p) { return p->chunk ? p->chunk : kDefaultChunk; }
+
+struct Prepared {
+  IntegrateArgs a;
+  uint32_t block;
+};
+
+qmc_status prepare(const qmc_problem* p, uint32_t n, const uint32_t* d_counts, const float* d_theta,
+                   void* ws, size_t ws_bytes, bool grad, bool need_source, Prepared& out) {
+  qmc_status st = validate_problem(p, need_source);
+  if (st != QMC_OK) return st;
+  if (!d_counts) return QMC_ERR_INVALID_ARG;
+  if (p->integrand != QMC_F_BILINEAR2D && !d_theta) return QMC_ERR_INVALID_ARG;
+  if (p->integrand == QMC_F_GAUSSMIX4_6D && !aligned16(d_theta)) return QMC_ERR_ALIGN;
+  if (!ws || ((uintptr_t)ws & 255u)) return QMC_ERR_WORKSPACE;
+  const uint32_t vpi = values_per_item(p, grad);
+  const WsLayout L0 = workspace_layout(n, 0, vpi);
+  if (ws_bytes < L0.total) return QMC_ERR_WORKSPACE;
+  const uint64_t capacity = (ws_bytes - L0.partials) / ((size_t)vpi * 2 * sizeof(float));
+  const WsLayout L = workspace_layout(n, capacity, vpi);
+  char* base = static_cast<char*>(ws);
+  IntegrateArgs& a = out.a;
+  a = IntegrateArgs{};
+  a.source = p->source;
+  a.integrand = p->integrand;
+  a.s = p->s;
+  a.randomize = p->randomize;
+  a.matrices = p->d_matrices;
+  a.g = p->d_g;
+  a.seeds = p->d_seeds;
+  a.seeds_per_integral = p->seeds_per_integral;
+  a.chunk_log2 = ilog2(chunk_for(p));
+  a.n = n;
+  a.counts = d_counts;
+  a.theta = d_theta;
+  a.theta_stride = p->integrand == QMC_F_GAUSSMIX4_6D ? 16u
+                   : p->integrand == QMC_F_BILINEAR2D  ? 0u
+                                                       : 2u * p->s;
+  a.hdr = reinterpret_cast<WsHeader*>(base + L.header);
+  a.item_off = reinterpret_cast<uint32_t*>(base + L.item_off);
+  a.row_off = nullptr;
+  a.ws_block_items = reinterpret_cast<uint64_t*>(base + L.block_items);
+  a.ws_block_rows = reinterpret_cast<uint64_t*>(base + L.block_rows);
+  a.ws_loss_terms = reinterpret_cast<double*>(base + L.loss_terms);
+  a.partials = reinterpret_cast<float*>(base + L.partials);
+  a.capacity_items = capacity;
+  (void)L.row_off;
+  out.block = p->block ? p->block : kDefaultBlock;
+  return QMC_OK;
+}
+
+qmc_status finish(cudaError_t e) { return e == cudaSuccess ? QMC_OK : QMC_ERR_CUDA; }
+
+}  // namespace
+
+size_t qmc_integrate_workspace_bytes(const qmc_problem* p, uint32_t n_integrals,
+                                     const uint32_t* h_counts) {
+  if (validate_problem(p, false) != QMC_OK) return 0;
+  const bool grad = p->with_gradient != 0;
+  const uint32_t C = p->chunk ? p->chunk : kMinTunedChunk;
+  uint64_t items = 0;
+  if (h_counts) {
+    for (uint32_t i = 0; i < n_integrals; ++i) items += ((uint64_t)h_counts[i] + C - 1) / C;
+  } else {
+    items = (uint64_t)n_integrals * (((uint64_t)p->max_count + C - 1) / C);
+  }
+  if (items >= 0xFFFFFFFFull) return 0;
+  return workspace_layout(n_integrals, items, values_per_item(p, grad)).total;
+}
+
+qmc_status qmc_integrate(const qmc_problem* p, uint32_t n_integrals, const uint32_t* d_counts,
+                         const float* d_theta, double* d_estimate, void* d_workspace,
+                         size_t workspace_bytes, qmc_stream_t stream) {
+  if (!d_estimate) return QMC_ERR_INVALID_ARG;
+  Prepared pr;
+  qmc_status st = prepare(p, n_integrals, d_counts, d_theta, d_workspace, workspace_bytes, false, true, pr);
+  if (st != QMC_OK || n_integrals == 0) return st;
+  pr.a.estimate = d_estimate;
+  return finish(launch_integrate(pr.a, pr.block, false, (cudaStream_t)stream));
+}
+
+qmc_status qmc_integrate_backward(const qmc_problem* p, uint32_t n_integrals,
+                                  const uint32_t* d_counts, const float* d_theta,
+                                  const double* d_grad_estimate, float* d_grad_theta,
+                                  void* d_workspace, size_t workspace_bytes, qmc_stream_t stream) {
+  if (!d_grad_estimate || !d_grad_theta) return QMC_ERR_INVALID_ARG;
+  if (p && p->integrand != QMC_F_GAUSSMIX4_6D) return QMC_ERR_UNSUPPORTED;
+  Prepared pr;
+  qmc_status st = prepare(p, n_integrals, d_counts, d_theta, d_workspace, workspace_bytes, true, true, pr);
+  if (st != QMC_OK || n_integrals == 0) return st;
+  pr.a.grad_est = d_grad_estimate;
+  pr.a.grad_theta = d_grad_theta;
+  return finish(launch_integrate(pr.a, pr.block, true, (cudaStream_t)stream));
+}
+
+qmc_status qmc_integrate_fwd_bwd(const qmc_problem* p, uint32_t n_integrals,
+                                 const uint32_t* d_counts, const float* d_theta,
+                                 const double* d_target, double* d_estimate, float* d_grad_theta,
+                                 double* d_loss, void* d_workspace, size_t workspace_bytes,
+                                 qmc_stream_t stream) {
+  if (!d_target || !d_estimate || !d_grad_theta || !d_loss) return QMC_ERR_INVALID_ARG;
+  if (p && p->integrand != QMC_F_GAUSSMIX4_6D) return QMC_ERR_UNSUPPORTED;
+  Prepared pr;
+  qmc_status st = prepare(p, n_integrals, d_counts, d_theta, d_workspace, workspace_bytes, true, true, pr);
+  if (st != QMC_OK) return st;
+  if (n_integrals == 0) return cudaMemsetAsync(d_loss, 0, sizeof(double), (cudaStream_t)stream) == cudaSuccess
+                                   ? QMC_OK : QMC_ERR_CUDA;
+  pr.a.target = d_target;
+  pr.a.estimate = d_estimate;
+  pr.a.grad_theta = d_grad_theta;
+  pr.a.loss = d_loss;
+  return finish(launch_integrate(pr.a, pr.block, true, (cudaStream_t)stream));
+}
+
+qmc_status qmc_integrate_points(const qmc_problem* p, uint32_t n_integrals,
+                                const uint32_t* d_counts, const float* d_points,
+                                uint32_t points_shared, const float* d_theta,
+                                double* d_estimate, void* d_workspace, size_t workspace_bytes,
+                                qmc_stream_t stream) {
+  if (!d_points || !d_estimate || points_shared > 1) return QMC_ERR_INVALID_ARG;
+  Prepared pr;
+  qmc_status st = prepare(p, n_integrals, d_counts, d_theta, d_workspace, workspace_bytes, false, false, pr);
+  if (st != QMC_OK || n_integrals == 0) return st;
+  const WsLayout L = workspace_layout(n_integrals, 0, 1);
+  pr.a.points = d_points;
+  pr.a.points_shared = points_shared;
+  pr.a.row_off = reinterpret_cast<uint64_t*>(static_cast<char*>(d_workspace) + L.row_off);
+  pr.a.estimate = d_estimate;
+  return finish(launch_integrate(pr.a, pr.block, false, (cudaStream_t)stream));
+}
+
+qmc_status qmc_read_device_error(const void* d_workspace, uint32_t* h_error_bits,
+                                 qmc_stream_t stream) {
+  if (!d_workspace || !h_error_bits || ((uintptr_t)d_workspace & 255u)) return QMC_ERR_INVALID_ARG;
+  WsHeader h{};
+  if (cudaMemcpyAsync(&h, d_workspace, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+    return QMC_ERR_CUDA;
+  *h_error_bits = h.error_bits;
+  return QMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,696 @@
+// integrate.cu -- massively parallel QMC integro-approximation (Sec. 2.5).
+//
+// Launch sequence of one qmc_integrate* call (all on the caller's stream):
+//   1. scan_totals   per block of 1024 integrals: sum of work items
+//                    ceil(n_p / C) and of samples n_p (u64)
+//   2. scan_carry    one block: exclusive scan of the block totals, resets the
+//                    scheduler, checks the item count against the workspace
+//   3. scan_write    item_off[p] (u32) and, for the unfused path, row_off[p] (u64)
+//   4. integrate_main  persistent: each warp takes a work item (integral p,
+//                    chunk k) from an atomic counter, generates the chunk's
+//                    points in registers, evaluates f in fp32, accumulates
+//                    with Kahan sums, merges the 32 lanes in a fixed
+//                    butterfly and writes the compensated partial to slot
+//                    `item` -- so the result never depends on scheduling
+//   5. reduce_*      per integral, the partials in item order in fp64
+//                    (the only fp64 arithmetic of the path), divided by n_p
+//   6. loss_reduce   (fused fwd+bwd only) fixed-order fp64 sum of the loss terms
+//
+// Sample i of integral p lives in chunk k = i >> log2(C), iteration
+// r = (i >> 5) mod C/32 and lane i mod 32.  These bit fields are disjoint, so
+// the Sobol' digits split as y(i) = Y(kC) ^ T[r] ^ L[lane] (linearity of
+// Eq. (ts) over GF(2)): one shared-memory load and two XORs per coordinate.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "../../include/qmc.h"
+#include "qmc_device.cuh"
+#include "qmc_integrate.h"
+#include "qmc_internal.h"
+
+namespace qmc {
+
+namespace {
+
+constexpr uint32_t kScanBlock = 1024;  // integrals per scan block
+constexpr uint32_t kScanThreads = 256;
+
+// ---------------------------------------------------------------------------
+// 1-3: work-item offsets
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t block_sum_u64(uint64_t v, uint64_t* sh) {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  uint64_t t = 0;
+  for (uint32_t w = 0; w < blockDim.x / 32; ++w) t += sh[w];
+  __syncthreads();
+  return t;
+}
+
+// Exclusive scan of v over the block; returns the block total in `total`.
+__device__ __forceinline__ uint64_t block_exscan_u64(uint64_t v, uint64_t* sh, uint64_t& total) {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint64_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= (uint32_t)o) inc += t;
+  }
+  if (lane == 31) sh[warp] = inc;
+  __syncthreads();
+  uint64_t warp_off = 0;
+  total = 0;
+  for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
+    if (w < warp) warp_off += sh[w];
+    total += sh[w];
+  }
+  __syncthreads();
+  return warp_off + inc - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_totals(IntegrateArgs a) {
+  __shared__ uint64_t sh[32];
+  const uint64_t base = (uint64_t)blockIdx.x * kScanBlock;
+  uint64_t items = 0, rows = 0;
+  for (uint32_t t = threadIdx.x; t < kScanBlock; t += blockDim.x) {
+    const uint64_t p = base + t;
+    if (p < a.n) {
+      const uint64_t c = a.counts[p];
+      items += (c + (1ull << a.chunk_log2) - 1) >> a.chunk_log2;
+      rows += c;
+    }
+  }
+  items = block_sum_u64(items, sh);
+  rows = block_sum_u64(rows, sh);
+  if (threadIdx.x == 0) {
+    a.ws_block_items[blockIdx.x] = items;
+    a.ws_block_rows[blockIdx.x] = rows;
+  }
+}
+
+__global__ void __launch_bounds__(1024) scan_carry(IntegrateArgs a, uint32_t n_blocks) {
+  __shared__ uint64_t sh[32];
+  uint64_t carry_items = 0, carry_rows = 0;
+  for (uint32_t b0 = 0; b0 < n_blocks; b0 += blockDim.x) {
+    const uint32_t b = b0 + threadIdx.x;
+    const uint64_t vi = b < n_blocks ? a.ws_block_items[b] : 0;
+    const uint64_t vr = b < n_blocks ? a.ws_block_rows[b] : 0;
+    uint64_t ti, tr;
+    const uint64_t ei = block_exscan_u64(vi, sh, ti);
+    const uint64_t er = block_exscan_u64(vr, sh, tr);
+    if (b < n_blocks) {
+      a.ws_block_items[b] = carry_items + ei;
+      a.ws_block_rows[b] = carry_rows + er;
+    }
+    carry_items += ti;
+    carry_rows += tr;
+  }
+  if (threadIdx.x == 0) {
+    WsHeader* h = a.hdr;
+    h->next_item = 0;
+    h->error_bits = 0;
+    if (carry_items > a.capacity_items || carry_items >= 0xFFFFFFFFull) {
+      h->error_bits = kErrCapacity;
+      h->total_items = 0;  // integrate nothing rather than write past the workspace
+    } else {
+      h->total_items = (uint32_t)carry_items;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_write(IntegrateArgs a) {
+  __shared__ uint64_t sh[32];
+  constexpr uint32_t kPer = kScanBlock / kScanThreads;
+  const uint64_t base = (uint64_t)blockIdx.x * kScanBlock + (uint64_t)threadIdx.x * kPer;
+  uint64_t items[kPer], rows[kPer];
+  uint64_t ti = 0, tr = 0;
+#pragma unroll
+  for (uint32_t q = 0; q < kPer; ++q) {
+    const uint64_t p = base + q;
+    const uint64_t c = p < a.n ? a.counts[p] : 0;
+    items[q] = (c + (1ull << a.chunk_log2) - 1) >> a.chunk_log2;
+    rows[q] = c;
+    ti += items[q];
+    tr += rows[q];
+  }
+  uint64_t dummy;
+  uint64_t oi = block_exscan_u64(ti, sh, dummy) + a.ws_block_items[blockIdx.x];
+  uint64_t orow = block_exscan_u64(tr, sh, dummy) + a.ws_block_rows[blockIdx.x];
+  const bool ok = a.hdr->error_bits == 0;
+#pragma unroll
+  for (uint32_t q = 0; q < kPer; ++q) {
+    const uint64_t p = base + q;
+    if (p <= a.n) {  // entry n is the total
+      if (ok) a.item_off[p] = (uint32_t)oi;
+      if (a.row_off) a.row_off[p] = orow;
+    }
+    oi += items[q];
+    orow += rows[q];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Point sources.  Each produces the S coordinates of local sample il of the
+// current item (sample index start + il) as fp32 in [0,1).
+// ---------------------------------------------------------------------------
+template <int S, int SCR>  // SCR: 0 none, 1 XOR, 2 nested
+struct SobolSource {
+  const uint32_t* cols;  // shared: [s][32], mirrored when nested
+  const uint32_t* tab;   // shared: [C/32][S], y(32 r)
+  uint32_t s;
+  uint32_t lane_y[S];    // y(lane)
+  uint32_t yl[S];        // y(start) ^ y(lane) (^ seed for XOR)
+  NestedKey key[S];
+
+  static size_t smem_bytes(uint32_t s, uint32_t chunk_log2) {
+    return ((size_t)s * 32 + ((size_t)1 << (chunk_log2 - 5)) * S) * sizeof(uint32_t);
+  }
+
+  __device__ void kernel_setup(const IntegrateArgs& a, uint32_t* smem) {
+    s = a.s;
+    uint32_t* c = smem;
+    uint32_t* t = smem + s * 32;
+    for (uint32_t i = threadIdx.x; i < s * 32; i += blockDim.x) {
+      const uint32_t v = __ldg(a.matrices + i);
+      c[i] = SCR == 2 ? __brev(v) : v;
+    }
+    __syncthreads();
+    const uint32_t rows = 1u << (a.chunk_log2 - 5);
+    for (uint32_t i = threadIdx.x; i < rows * S; i += blockDim.x) {
+      const uint32_t r = i / S, j = i - r * S;
+      uint32_t y = 0;
+      if (j < s)
+        for (uint32_t b = 0; (r >> b) != 0; ++b)
+          if ((r >> b) & 1u) y ^= c[j * 32 + 5 + b];
+      t[i] = y;
+    }
+    __syncthreads();
+    cols = c;
+    tab = t;
+    const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      uint32_t y = 0;
+      if ((uint32_t)j < s)
+        for (uint32_t b = 0; b < 5; ++b)
+          if ((lane >> b) & 1u) y ^= c[j * 32 + b];
+      lane_y[j] = y;
+    }
+  }
+
+  __device__ void item_setup(const IntegrateArgs& a, uint32_t p, uint32_t start) {
+    const uint32_t khi = start >> a.chunk_log2;
+    const uint32_t* sd = a.seeds ? a.seeds + (a.seeds_per_integral ? (size_t)p * s : 0) : nullptr;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      uint32_t y = 0;
+      if ((uint32_t)j < s)
+        for (uint32_t b = 0; (khi >> b) != 0; ++b)
+          if ((khi >> b) & 1u) y ^= cols[j * 32 + a.chunk_log2 + b];
+      const uint32_t seed = (sd && (uint32_t)j < s) ? __ldg(sd + j) : 0u;
+      yl[j] = y ^ lane_y[j] ^ (SCR == 1 ? seed : 0u);
+      key[j] = nested_key(seed);
+    }
+  }
+
+  __device__ __forceinline__ void point(uint32_t r, uint32_t /*il*/, bool /*valid*/, float* x) const {
+    const uint32_t* row = tab + r * S;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      uint32_t y = row[j] ^ yl[j];
+      if (SCR == 2) y = __brev(nested_mix(y, key[j]));
+      x[j] = map_u32_to_unifloat(y);
+    }
+  }
+};
+
+template <int S, bool BACKWARD>
+struct LatticeSource {
+  uint32_t s;
+  uint32_t start;
+  uint32_t g[S];
+  uint32_t sh[S];
+
+  static size_t smem_bytes(uint32_t, uint32_t) { return 0; }
+
+  __device__ void kernel_setup(const IntegrateArgs& a, uint32_t*) {
+    s = a.s;
+#pragma unroll
+    for (int j = 0; j < S; ++j) g[j] = (uint32_t)j < s ? (__ldg(a.g + j) | 1u) : 1u;
+  }
+
+  __device__ void item_setup(const IntegrateArgs& a, uint32_t p, uint32_t st) {
+    start = st;
+    const uint32_t* sd = a.seeds ? a.seeds + (a.seeds_per_integral ? (size_t)p * s : 0) : nullptr;
+#pragma unroll
+    for (int j = 0; j < S; ++j) sh[j] = (sd && (uint32_t)j < s) ? __ldg(sd + j) : 0u;
+  }
+
+  __device__ __forceinline__ void point(uint32_t, uint32_t il, bool, float* x) const {
+    const uint32_t k = start + il;
+    const uint32_t phi = __brev(BACKWARD ? ~k : k);
+#pragma unroll
+    for (int j = 0; j < S; ++j) x[j] = map_u32_to_unifloat(phi * g[j] + sh[j]);
+  }
+};
+
+// Unfused comparison path: coordinates read back from HBM.
+template <int S>
+struct PointsSource {
+  const float* rows;
+  uint32_t s;
+
+  static size_t smem_bytes(uint32_t, uint32_t) { return 0; }
+
+  __device__ void kernel_setup(const IntegrateArgs& a, uint32_t*) { s = a.s; }
+
+  __device__ void item_setup(const IntegrateArgs& a, uint32_t p, uint32_t start) {
+    const uint64_t row0 = (a.points_shared ? 0ull : a.row_off[p]) + start;
+    rows = a.points + row0 * s;
+  }
+
+  __device__ __forceinline__ void point(uint32_t, uint32_t il, bool valid, float* x) const {
+    const float* r = rows + (size_t)il * s;
+#pragma unroll
+    for (int j = 0; j < S; ++j) x[j] = (valid && (uint32_t)j < s) ? __ldcs(r + j) : 0.5f;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Integrands (fp32).  Per-integral constants are built with error-free
+// transformations so that no rounding error is shared by all samples.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ex2_approx(float t) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(t));
+  return r;
+}
+
+// log2(e) split into two fp32 words (hi + lo to ~2^-48).
+constexpr float kLog2eHi = 1.44269502162933349609375f;
+constexpr float kLog2eLo = 1.925963033500011079e-08f;
+
+template <int FN>
+struct Integrand;
+
+template <>
+struct Integrand<QMC_F_BILINEAR2D> {
+  static constexpr int S = 2;
+  __device__ void setup(const float*, uint32_t) {}
+  __device__ __forceinline__ float eval(const float* x) const {
+    return __fmaf_rn(0.5f, x[0], 0.75f) * __fmaf_rn(0.5f, x[1], 0.75f);
+  }
+};
+
+template <>
+struct Integrand<QMC_F_GENZ_PRODUCT_PEAK> {
+  static constexpr int S = 16;
+  uint32_t s;
+  float ch[16], cl[16], u[16];  // a^-2 = ch + cl
+  __device__ void setup(const float* th, uint32_t s_) {
+    s = s_;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float a = (uint32_t)j < s ? __ldg(th + j) : 1.0f;
+      u[j] = (uint32_t)j < s ? __ldg(th + s + j) : 0.0f;
+      float e;
+      const float a2 = two_prod(a, a, e);
+      ch[j] = ff_recip(a2, e, cl[j]);
+    }
+  }
+  __device__ __forceinline__ float eval(const float* x) const {
+    float prod = 1.0f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if ((uint32_t)j < s) {
+        const float d = __fsub_rn(x[j], u[j]);
+        prod = __fmul_rn(prod, __fadd_rn(__fmaf_rn(d, d, ch[j]), cl[j]));
+      }
+    }
+    return __frcp_rn(prod);
+  }
+};
+
+template <>
+struct Integrand<QMC_F_GENZ_OSCILLATORY> {
+  static constexpr int S = 16;
+  uint32_t s;
+  float a[16];
+  float c0, s0;  // cos, sin of 2 pi u_1
+  __device__ void setup(const float* th, uint32_t s_) {
+    s = s_;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) a[j] = (uint32_t)j < s ? __ldg(th + j) : 0.0f;
+    sincospif(2.0f * __ldg(th + s), &s0, &c0);
+  }
+  // cos(2 pi u_1 + B) = cos(2 pi u_1) cos B - sin(2 pi u_1) sin B, B = sum_j a_j x_j
+  __device__ __forceinline__ float eval(const float* x) const {
+    float B = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if ((uint32_t)j < s) B = __fmaf_rn(a[j], x[j], B);
+    float sb, cb;
+    sincosf(B, &sb, &cb);
+    return __fmaf_rn(c0, cb, -__fmul_rn(s0, sb));
+  }
+};
+
+template <>
+struct Integrand<QMC_F_GAUSSMIX4_6D> {
+  static constexpr int S = 6;
+  float w[4], mu[4], nu[4], kh[4], kl[4];  // kh + kl = log2(e) / (2 sigma^2)
+  float is2[4], is3[4];                    // 1/sigma^2, 1/sigma^3 (gradient only)
+  __device__ void setup(const float* th, uint32_t) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(th) + c);
+      w[c] = t.x;
+      mu[c] = t.y;
+      nu[c] = t.z;
+      const float sg = t.w;
+      float e;
+      const float s2 = two_prod(sg, sg, e);  // sigma^2 = s2 + e exactly
+      float rl;
+      const float rh = ff_recip(2.0f * s2, 2.0f * e, rl);  // 1/(2 sigma^2)
+      float pe;
+      const float p = two_prod(rh, kLog2eHi, pe);
+      kh[c] = p;
+      kl[c] = pe + rh * kLog2eLo + rl * kLog2eHi;
+      is2[c] = __frcp_rn(s2);
+      is3[c] = is2[c] * __frcp_rn(sg);
+    }
+  }
+  __device__ __forceinline__ float eval(const float* x) const {
+    float f = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float q = 0.0f;
+#pragma unroll
+      for (int d = 0; d < 6; ++d) {
+        const float diff = __fsub_rn(x[d], (d & 1) ? nu[c] : mu[c]);
+        q = __fmaf_rn(diff, diff, q);
+      }
+      const float t = -__fmaf_rn(q, kh[c], __fmul_rn(q, kl[c]));
+      f = __fmaf_rn(w[c], ex2_approx(t), f);
+    }
+    return f;
+  }
+  // f and df/dtheta (theta order w, mu, nu, sigma per component)
+  __device__ __forceinline__ float eval_grad(const float* x, float* g) const {
+    float f = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float q = 0.0f, se = 0.0f, so = 0.0f;
+#pragma unroll
+      for (int d = 0; d < 6; ++d) {
+        const float diff = __fsub_rn(x[d], (d & 1) ? nu[c] : mu[c]);
+        q = __fmaf_rn(diff, diff, q);
+        if (d & 1) so = __fadd_rn(so, diff); else se = __fadd_rn(se, diff);
+      }
+      const float t = -__fmaf_rn(q, kh[c], __fmul_rn(q, kl[c]));
+      const float G = ex2_approx(t);
+      const float wG = __fmul_rn(w[c], G);
+      const float wg2 = __fmul_rn(wG, is2[c]);
+      f = __fadd_rn(f, wG);
+      g[4 * c + 0] = G;
+      g[4 * c + 1] = __fmul_rn(wg2, se);
+      g[4 * c + 2] = __fmul_rn(wg2, so);
+      g[4 * c + 3] = __fmul_rn(__fmul_rn(wG, is3[c]), q);
+    }
+    return f;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Kahan accumulation (true value = s - c) and the per-item store.
+// ---------------------------------------------------------------------------
+struct Kahan {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = __fsub_rn(v, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ Comp comp() const { return {s, -c}; }
+};
+
+// Warp-cooperative search: the integral p with item_off[p] <= item < item_off[p+1]
+// (32 probes per round, so about log32(n) dependent loads).
+__device__ __forceinline__ uint32_t find_integral(const uint32_t* off, uint32_t n, uint32_t item) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t lo = 0, hi = n;  // off[lo] <= item < off[hi]
+  while (hi - lo > 1) {
+    const uint32_t step = (hi - lo + 31) >> 5;
+    const uint64_t pos = (uint64_t)lo + (uint64_t)(lane + 1) * step;
+    const bool le = pos < hi && __ldg(off + pos) <= item;
+    const uint32_t m = __popc(__ballot_sync(0xffffffffu, le));
+    const uint64_t nhi = (uint64_t)lo + (uint64_t)(m + 1) * step;
+    lo += m * step;
+    if (nhi < hi) hi = (uint32_t)nhi;
+  }
+  return lo;
+}
+
+template <class Src, int FN, bool GRAD>
+__global__ void __launch_bounds__(256) integrate_main(IntegrateArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  using F = Integrand<FN>;
+  constexpr int S = F::S;
+  constexpr int NV = GRAD ? 17 : 1;
+  Src src;
+  src.kernel_setup(a, smem);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t total = a.hdr->total_items;
+  const uint32_t C = 1u << a.chunk_log2;
+  const uint32_t pstride = a.theta_stride;
+
+  uint32_t next = 0;
+  if (lane == 0) next = atomicAdd(&a.hdr->next_item, 1u);
+  next = __shfl_sync(0xffffffffu, next, 0);
+  while (next < total) {
+    const uint32_t item = next;
+    if (lane == 0) next = atomicAdd(&a.hdr->next_item, 1u);  // prefetch the next item
+    const uint32_t p = find_integral(a.item_off, a.n, item);
+    const uint32_t start = (item - __ldg(a.item_off + p)) << a.chunk_log2;
+    const uint32_t n_p = __ldg(a.counts + p);
+    const uint32_t len = min(C, n_p - start);
+    F f;
+    f.setup(a.theta ? a.theta + (size_t)p * pstride : nullptr, a.s);
+    src.item_setup(a, p, start);
+
+    Kahan acc[NV];
+    const uint32_t R = (len + 31u) >> 5;
+    for (uint32_t r = 0; r < R; ++r) {
+      const uint32_t il = (r << 5) + lane;
+      const bool valid = il < len;
+      float x[S];
+      src.point(r, il, valid, x);
+      if constexpr (GRAD) {
+        float g[16];
+        const float v = f.eval_grad(x, g);
+        if (valid) {
+          acc[0].add(v);
+#pragma unroll
+          for (int k = 0; k < 16; ++k) acc[1 + k].add(g[k]);
+        }
+      } else {
+        const float v = f.eval(x);
+        if (valid) acc[0].add(v);
+      }
+    }
+    float* out = a.partials + (size_t)item * (2 * NV);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const Comp c = warp_comp_sum(acc[v].comp());
+      if (lane == (uint32_t)(v & 31)) {
+        out[2 * v] = c.sum;
+        out[2 * v + 1] = c.err;
+      }
+    }
+    next = __shfl_sync(0xffffffffu, next, 0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 5-6: fp64 reductions, one warp per integral, partials in item order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void neumaier64(double& s, double& c, double v) {
+  const double t = s + v;
+  c += (fabs(s) >= fabs(v)) ? (s - t) + v : (v - t) + s;
+  s = t;
+}
+
+__global__ void __launch_bounds__(256) reduce_forward(IntegrateArgs a) {
+  const uint64_t p = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31u;
+  if (p >= a.n) return;
+  if (a.hdr->error_bits) {  // offsets were not written: report NaN, touch no partial
+    if (lane == 0) a.estimate[p] = __longlong_as_double(0x7FF8000000000000ll);
+    return;
+  }
+  const uint32_t b = a.item_off[p], e = a.item_off[p + 1];
+  double s = 0.0, c = 0.0;
+  for (uint32_t it = b + lane; it < e; it += 32) {
+    neumaier64(s, c, (double)a.partials[2 * (size_t)it]);
+    neumaier64(s, c, (double)a.partials[2 * (size_t)it + 1]);
+  }
+  // fixed-order tree over lanes (lane 0 ends with the sum of all)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double os = __shfl_down_sync(0xffffffffu, s, o);
+    const double oc = __shfl_down_sync(0xffffffffu, c, o);
+    neumaier64(s, c, os);
+    c += oc;
+  }
+  if (lane == 0) {
+    const uint32_t n_p = a.counts[p];
+    a.estimate[p] = n_p ? (s + c) / (double)n_p : 0.0;
+  }
+}
+
+// GRAD partials: 17 values per item (f, 16 derivatives).  Lane v < 17 adds
+// value v over the integral's items in item order.
+__global__ void __launch_bounds__(256) reduce_grad(IntegrateArgs a) {
+  const uint64_t p = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31u;
+  if (p >= a.n) return;
+  if (a.hdr->error_bits) {  // offsets were not written: report NaN, touch no partial
+    const double nan = __longlong_as_double(0x7FF8000000000000ll);
+    if (lane == 0 && a.target) {
+      a.estimate[p] = nan;
+      a.ws_loss_terms[p] = nan;
+    }
+    if (lane >= 1 && lane < 17) a.grad_theta[p * 16 + (lane - 1)] = __int_as_float(0x7FC00000);
+    return;
+  }
+  const uint32_t b = a.item_off[p], e = a.item_off[p + 1];
+  double s = 0.0, c = 0.0;
+  if (lane < 17)
+    for (uint32_t it = b; it < e; ++it) {
+      const float* q = a.partials + (size_t)it * 34 + 2 * lane;
+      neumaier64(s, c, (double)q[0]);
+      neumaier64(s, c, (double)q[1]);
+    }
+  const uint32_t n_p = a.counts[p];
+  const double mean = n_p ? (s + c) / (double)n_p : 0.0;  // lane 0: I_p; lane 1+k: J_pk
+  const double I = __shfl_sync(0xffffffffu, mean, 0);
+  double scale;
+  if (a.target) {  // fused squared-error loss
+    const double diff = I - a.target[p];
+    scale = 2.0 * diff;
+    if (lane == 0) {
+      a.estimate[p] = I;
+      a.ws_loss_terms[p] = diff * diff;
+    }
+  } else {
+    scale = a.grad_est[p];
+  }
+  if (lane >= 1 && lane < 17) a.grad_theta[p * 16 + (lane - 1)] = (float)(scale * mean);
+}
+
+__global__ void __launch_bounds__(1024) loss_reduce(IntegrateArgs a) {
+  __shared__ double sh_s[32], sh_c[32];
+  double s = 0.0, c = 0.0;
+  for (uint64_t p = threadIdx.x; p < a.n; p += blockDim.x) neumaier64(s, c, a.ws_loss_terms[p]);
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double os = __shfl_down_sync(0xffffffffu, s, o);
+    const double oc = __shfl_down_sync(0xffffffffu, c, o);
+    neumaier64(s, c, os);
+    c += oc;
+  }
+  if (lane == 0) {
+    sh_s[warp] = s;
+    sh_c[warp] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double S = 0.0, Cc = 0.0;
+    for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
+      neumaier64(S, Cc, sh_s[w]);
+      Cc += sh_c[w];
+    }
+    a.loss[0] = S + Cc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+template <class Src, int FN, bool GRAD>
+cudaError_t launch_main_t(const IntegrateArgs& a, uint32_t block, cudaStream_t stream) {
+  auto kernel = integrate_main<Src, FN, GRAD>;
+  const size_t smem = Src::smem_bytes(a.s, a.chunk_log2);
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, (int)block, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const DeviceInfo& dev = device_info();
+  kernel<<<(unsigned)(dev.sm_count * per_sm), block, smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
+template <int FN, bool GRAD>
+cudaError_t launch_main_fn(const IntegrateArgs& a, uint32_t block, cudaStream_t stream) {
+  constexpr int S = Integrand<FN>::S;
+  if (a.points) return launch_main_t<PointsSource<S>, FN, GRAD>(a, block, stream);
+  if (a.source == QMC_SOURCE_LATTICE)
+    return (a.randomize & QMC_LATTICE_BACKWARD) ? launch_main_t<LatticeSource<S, true>, FN, GRAD>(a, block, stream)
+                                                : launch_main_t<LatticeSource<S, false>, FN, GRAD>(a, block, stream);
+  const uint32_t scr = a.seeds ? a.randomize : 0u;
+  if (scr == QMC_SCRAMBLE_NESTED) return launch_main_t<SobolSource<S, 2>, FN, GRAD>(a, block, stream);
+  if (scr == QMC_SCRAMBLE_XOR) return launch_main_t<SobolSource<S, 1>, FN, GRAD>(a, block, stream);
+  return launch_main_t<SobolSource<S, 0>, FN, GRAD>(a, block, stream);
+}
+
+}  // namespace
+
+size_t integrate_smem_bytes(uint32_t source, uint32_t integrand, uint32_t s, uint32_t chunk_log2,
+                            bool points) {
+  if (points || source == QMC_SOURCE_LATTICE) return 0;
+  switch (integrand) {
+    case QMC_F_BILINEAR2D: return SobolSource<2, 0>::smem_bytes(s, chunk_log2);
+    case QMC_F_GAUSSMIX4_6D: return SobolSource<6, 0>::smem_bytes(s, chunk_log2);
+    default: return SobolSource<16, 0>::smem_bytes(s, chunk_log2);
+  }
+}
+
+cudaError_t launch_integrate(const IntegrateArgs& a, uint32_t block, bool grad, cudaStream_t stream) {
+  const uint32_t n_blocks = (uint32_t)(((uint64_t)a.n + kScanBlock) / kScanBlock);  // covers entry n
+  scan_totals<<<n_blocks, kScanThreads, 0, stream>>>(a);
+  scan_carry<<<1, 1024, 0, stream>>>(a, n_blocks);
+  scan_write<<<n_blocks, kScanThreads, 0, stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  switch (a.integrand) {
+    case QMC_F_BILINEAR2D: e = launch_main_fn<QMC_F_BILINEAR2D, false>(a, block, stream); break;
+    case QMC_F_GENZ_PRODUCT_PEAK: e = launch_main_fn<QMC_F_GENZ_PRODUCT_PEAK, false>(a, block, stream); break;
+    case QMC_F_GENZ_OSCILLATORY: e = launch_main_fn<QMC_F_GENZ_OSCILLATORY, false>(a, block, stream); break;
+    default:
+      e = grad ? launch_main_fn<QMC_F_GAUSSMIX4_6D, true>(a, block, stream)
+               : launch_main_fn<QMC_F_GAUSSMIX4_6D, false>(a, block, stream);
+  }
+  if (e != cudaSuccess) return e;
+  const uint64_t threads = (uint64_t)a.n * 32;
+  const unsigned rblocks = (unsigned)((threads + 255) / 256);
+  if (grad) {
+    reduce_grad<<<rblocks, 256, 0, stream>>>(a);
+    if (a.target) loss_reduce<<<1, 1024, 0, stream>>>(a);
+  } else {
+    reduce_forward<<<rblocks, 256, 0, stream>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace qmc

@@ -1,0 +1,334 @@
+// points.cu -- materialised low-discrepancy points (HBM-write bound).
+//
+//   sobol_points_*    Alg. 3 / Eq. (ts): y_j(i) = XOR of the generator columns
+//                     selected by the bits of i, randomised in integers
+//                     (Sec. 2.3), mapped to [0,1) (Sec. 2.1).
+//   lattice_points_*  Eq. (R1LS) / Alg. 4: x_j(k) = phi_2(k) g_j + shift_j mod 2^32.
+//
+// Fast path layout.  Output rows are [count][s] u32/f32.  A warp writes a
+// "group" of Q = 128 / gcd(s,128) consecutive points per step: Q*s = 128*K
+// elements, i.e. K 16-byte chunks per lane, so every store is a coalesced
+// 128-bit store.  Lane l owns chunks l, l+32, .. of the group; element e of
+// a group is point p_e = e / s, dimension j_e = e % s, the same in every group.
+//
+// Linearity over GF(2) makes the per-element cost O(1): for a group starting
+// at index G*Q (index_begin is a multiple of Q), index bits split into three
+// disjoint fields,
+//   i = (G_hi << (u + q)) | (G_in << q) | p_e,   G_in < 2^u, p_e < Q,
+// and y_j(i) = Hout_j(G_hi) ^ Hin_j[G_in] ^ lo_e.  lo_e is fixed per lane,
+// Hin is a shared-memory table of 2^u rows, Hout is recomputed once every
+// 2^u groups.  For the lattice, phi_2 of disjoint bit fields adds without
+// carries, so x = phi_2(G*Q) g_j + lo_e with one bit reversal per group.
+#include <cstdint>
+
+#include "qmc_device.cuh"
+#include "qmc_internal.h"
+
+namespace qmc {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void store4(uint32_t* out_u32, float* out_f32, uint64_t off,
+                                       const uint32_t (&v)[4]) {
+  if (out_u32) __stcs(reinterpret_cast<uint4*>(out_u32 + off), make_uint4(v[0], v[1], v[2], v[3]));
+  if (out_f32)
+    __stcs(reinterpret_cast<float4*>(out_f32 + off),
+           make_float4(map_u32_to_unifloat(v[0]), map_u32_to_unifloat(v[1]),
+                       map_u32_to_unifloat(v[2]), map_u32_to_unifloat(v[3])));
+}
+
+__device__ __forceinline__ void store1(uint32_t* out_u32, float* out_f32, uint64_t off,
+                                       uint32_t v) {
+  if (out_u32) out_u32[off] = v;
+  if (out_f32) out_f32[off] = map_u32_to_unifloat(v);
+}
+
+// This warp's contiguous share [g0, g1) of n_groups groups.
+__device__ __forceinline__ void warp_range(uint64_t n_groups, uint64_t& g0, uint64_t& g1) {
+  const uint64_t w = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const uint64_t W = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  g0 = n_groups * w / W;
+  g1 = n_groups * (w + 1) / W;
+}
+
+// ---------------------------------------------------------------------------
+// K1 fast path.  MODE: 0 none, 1 XOR, 2 nested.  K: 16-byte chunks per lane.
+// Shared memory: cols[s][32] (mirrored for nested), hin[2^u][s].
+// ---------------------------------------------------------------------------
+template <int K, int MODE>
+__global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const uint32_t s = a.s;
+  uint32_t* cols = smem;
+  uint32_t* hin = smem + s * 32;
+  const uint32_t nin = 1u << a.u_log2;
+
+  for (uint32_t idx = threadIdx.x; idx < s * 32; idx += blockDim.x) {
+    const uint32_t c = __ldg(a.matrices + idx);
+    cols[idx] = (MODE == 2) ? __brev(c) : c;
+  }
+  __syncthreads();
+  for (uint32_t idx = threadIdx.x; idx < nin * s; idx += blockDim.x) {
+    const uint32_t g = idx / s, j = idx - g * s;
+    uint32_t y = 0;
+    for (uint32_t k = 0; (g >> k) != 0; ++k)
+      if ((g >> k) & 1u) y ^= cols[j * 32 + a.q_log2 + k];
+    hin[idx] = y;
+  }
+  __syncthreads();
+
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t Q = 1u << a.q_log2;
+  uint32_t jd[4 * K], lo[4 * K], hout[4 * K];
+  NestedKey key[4 * K];
+#pragma unroll
+  for (int c = 0; c < K; ++c)
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const uint32_t e = 4u * (lane + 32u * c) + t;
+      const uint32_t p = e / s, j = e - p * s;
+      uint32_t y = 0;
+      for (uint32_t k = 0; k < a.q_log2; ++k)
+        if ((p >> k) & 1u) y ^= cols[j * 32 + k];
+      if (MODE == 1) y ^= __ldg(a.seeds + j);
+      jd[4 * c + t] = j;
+      lo[4 * c + t] = y;
+      key[4 * c + t] = nested_key(MODE == 2 ? __ldg(a.seeds + j) : 0u);
+    }
+
+  const uint64_t n_groups = (a.count + Q - 1) >> a.q_log2;
+  uint64_t g0, g1;
+  warp_range(n_groups, g0, g1);
+  const uint32_t G_first = a.index_begin >> a.q_log2;
+  const uint32_t hi_shift = a.q_log2 + a.u_log2;
+
+  for (uint64_t g = g0; g < g1; ++g) {
+    const uint32_t G = G_first + (uint32_t)g;
+    const uint32_t G_in = G & (nin - 1u);
+    if (g == g0 || G_in == 0) {
+      const uint32_t G_hi = G >> a.u_log2;
+#pragma unroll
+      for (int e = 0; e < 4 * K; ++e) {
+        uint32_t y = 0;
+        for (uint32_t k = 0; (G_hi >> k) != 0; ++k)
+          if ((G_hi >> k) & 1u) y ^= cols[jd[e] * 32 + hi_shift + k];
+        hout[e] = y;
+      }
+    }
+    const uint64_t row0 = g << a.q_log2;
+    const uint64_t rows_left = a.count - row0;
+    const uint32_t* hrow = hin + G_in * s;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      uint32_t v[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        uint32_t y = hrow[jd[4 * c + t]] ^ hout[4 * c + t] ^ lo[4 * c + t];
+        if (MODE == 2) y = __brev(nested_mix(y, key[4 * c + t]));
+        v[t] = y;
+      }
+      const uint32_t e0 = 4u * (lane + 32u * c);
+      const uint64_t off = row0 * s + e0;
+      if ((uint64_t)((e0 + 3) / s) < rows_left) {
+        store4(a.out_u32, a.out_f32, off, v);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if ((uint64_t)((e0 + t) / s) < rows_left) store1(a.out_u32, a.out_f32, off + t, v[t]);
+      }
+    }
+  }
+}
+
+// K1 generic path: one element per thread, columns read through the cache.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) sobol_points_generic(PointsArgs a) {
+  const uint64_t total = a.count * a.s;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += stride) {
+    const uint64_t r = f / a.s;
+    const uint32_t j = (uint32_t)(f - r * a.s);
+    uint32_t i = a.index_begin + (uint32_t)r;
+    uint32_t y = 0;
+    for (; i != 0; i &= i - 1u) y ^= __ldg(a.matrices + j * 32 + (__ffs(i) - 1));
+    if (MODE == 1) y ^= __ldg(a.seeds + j);
+    if (MODE == 2) y = __brev(nested_mix(__brev(y), nested_key(__ldg(a.seeds + j))));
+    store1(a.out_u32, a.out_f32, f, y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2: rank-1 lattice.  BACKWARD follows Alg. 4: phi_2(~k) = ~phi_2(k), so
+// x = shift - g - phi_2(k) g (mod 2^32).
+// ---------------------------------------------------------------------------
+template <int K, bool BACKWARD>
+__global__ void __launch_bounds__(kThreads) lattice_points_fast(PointsArgs a) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t s = a.s;
+  const uint32_t Q = 1u << a.q_log2;
+  uint32_t gj[4 * K], lo[4 * K];
+#pragma unroll
+  for (int c = 0; c < K; ++c)
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const uint32_t e = 4u * (lane + 32u * c) + t;
+      const uint32_t p = e / s, j = e - p * s;
+      const uint32_t g = __ldg(a.matrices + j) | 1u;  // generator words
+      const uint32_t sh = a.seeds ? __ldg(a.seeds + j) : 0u;
+      const uint32_t phi_p = __brev(p);
+      gj[4 * c + t] = g;
+      lo[4 * c + t] = BACKWARD ? sh - g - phi_p * g : phi_p * g + sh;
+    }
+  const uint64_t n_groups = (a.count + Q - 1) >> a.q_log2;
+  uint64_t g0, g1;
+  warp_range(n_groups, g0, g1);
+  const uint32_t G_first = a.index_begin >> a.q_log2;
+  for (uint64_t g = g0; g < g1; ++g) {
+    const uint32_t phib = __brev((G_first + (uint32_t)g) << a.q_log2);
+    const uint64_t row0 = g << a.q_log2;
+    const uint64_t rows_left = a.count - row0;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      uint32_t v[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        v[t] = BACKWARD ? lo[4 * c + t] - phib * gj[4 * c + t] : phib * gj[4 * c + t] + lo[4 * c + t];
+      const uint32_t e0 = 4u * (lane + 32u * c);
+      const uint64_t off = row0 * s + e0;
+      if ((uint64_t)((e0 + 3) / s) < rows_left) {
+        store4(a.out_u32, a.out_f32, off, v);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if ((uint64_t)((e0 + t) / s) < rows_left) store1(a.out_u32, a.out_f32, off + t, v[t]);
+      }
+    }
+  }
+}
+
+template <bool BACKWARD>
+__global__ void __launch_bounds__(kThreads) lattice_points_generic(PointsArgs a) {
+  const uint64_t total = a.count * a.s;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += stride) {
+    const uint64_t r = f / a.s;
+    const uint32_t j = (uint32_t)(f - r * a.s);
+    const uint32_t k = a.index_begin + (uint32_t)r;
+    const uint32_t phi = __brev(BACKWARD ? ~k : k);
+    const uint32_t g = __ldg(a.matrices + j) | 1u;
+    const uint32_t sh = a.seeds ? __ldg(a.seeds + j) : 0u;
+    store1(a.out_u32, a.out_f32, f, phi * g + sh);
+  }
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Chunks per lane of the fast path, or 0 when the generic path must run.
+uint32_t fast_k(uint32_t s) {
+  uint32_t g = 128;
+  while (s % g) g >>= 1;  // gcd(s, 128): the largest power of two dividing both
+  const uint32_t K = s / g;
+  return K <= 4 ? K : 0;
+}
+
+uint32_t log2_exact(uint32_t v) {
+  uint32_t l = 0;
+  while ((1u << l) < v) ++l;
+  return l;
+}
+
+template <typename KernelT>
+cudaError_t launch_persistent(KernelT kernel, uint64_t warps_needed, size_t smem,
+                              cudaStream_t stream, const PointsArgs& a) {
+  const DeviceInfo& dev = device_info();
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  uint64_t blocks = (uint64_t)dev.sm_count * per_sm;
+  const uint64_t need = (warps_needed + kThreads / 32 - 1) / (kThreads / 32);
+  if (need < blocks) blocks = need;
+  if (blocks < 1) blocks = 1;
+  kernel<<<(unsigned)blocks, kThreads, smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename KernelT>
+cudaError_t launch_grid_stride(KernelT kernel, uint64_t elements, cudaStream_t stream,
+                               const PointsArgs& a) {
+  const DeviceInfo& dev = device_info();
+  uint64_t blocks = (elements + kThreads - 1) / kThreads;
+  const uint64_t cap = (uint64_t)dev.sm_count * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  kernel<<<(unsigned)blocks, kThreads, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_sobol_points(PointsArgs a, cudaStream_t stream) {
+  const uint32_t K = fast_k(a.s);
+  a.q_log2 = log2_exact(K ? 128u * K / a.s : 1u);
+  const bool fast = K != 0 && a.s <= 256 && (a.index_begin & ((1u << a.q_log2) - 1u)) == 0 &&
+                    aligned16(a.out_u32) && aligned16(a.out_f32);
+  if (!fast) {
+    switch (a.scramble) {
+      case 0: return launch_grid_stride(sobol_points_generic<0>, a.count * a.s, stream, a);
+      case 1: return launch_grid_stride(sobol_points_generic<1>, a.count * a.s, stream, a);
+      default: return launch_grid_stride(sobol_points_generic<2>, a.count * a.s, stream, a);
+    }
+  }
+  // inner table of at most 16 KiB and 256 rows
+  uint32_t u = 0;
+  while (u < 8 && (2u << u) * a.s * 4u <= 16384u) ++u;
+  a.u_log2 = u;
+  const size_t smem = ((size_t)a.s * 32 + ((size_t)1 << u) * a.s) * sizeof(uint32_t);
+  const uint64_t groups = (a.count + (1u << a.q_log2) - 1) >> a.q_log2;
+#define QMC_SOBOL_CASE(KK)                                                                    \
+  case KK:                                                                                    \
+    if (a.scramble == 0) return launch_persistent(sobol_points_fast<KK, 0>, groups, smem, stream, a); \
+    if (a.scramble == 1) return launch_persistent(sobol_points_fast<KK, 1>, groups, smem, stream, a); \
+    return launch_persistent(sobol_points_fast<KK, 2>, groups, smem, stream, a);
+  switch (K) {
+    QMC_SOBOL_CASE(1)
+    QMC_SOBOL_CASE(2)
+    QMC_SOBOL_CASE(3)
+    QMC_SOBOL_CASE(4)
+    default: return cudaErrorInvalidValue;
+  }
+#undef QMC_SOBOL_CASE
+}
+
+cudaError_t launch_lattice_points(PointsArgs a, cudaStream_t stream) {
+  const bool backward = (a.scramble & 1u) != 0;
+  const uint32_t K = fast_k(a.s);
+  a.q_log2 = log2_exact(K ? 128u * K / a.s : 1u);
+  const bool fast = K != 0 && (a.index_begin & ((1u << a.q_log2) - 1u)) == 0 && aligned16(a.out_u32) &&
+                    aligned16(a.out_f32);
+  if (!fast) {
+    return backward ? launch_grid_stride(lattice_points_generic<true>, a.count * a.s, stream, a)
+                    : launch_grid_stride(lattice_points_generic<false>, a.count * a.s, stream, a);
+  }
+  const uint64_t groups = (a.count + (1u << a.q_log2) - 1) >> a.q_log2;
+#define QMC_LATTICE_CASE(KK)                                                                 \
+  case KK:                                                                                   \
+    return backward ? launch_persistent(lattice_points_fast<KK, true>, groups, 0, stream, a) \
+                    : launch_persistent(lattice_points_fast<KK, false>, groups, 0, stream, a);
+  switch (K) {
+    QMC_LATTICE_CASE(1)
+    QMC_LATTICE_CASE(2)
+    QMC_LATTICE_CASE(3)
+    QMC_LATTICE_CASE(4)
+    default: return cudaErrorInvalidValue;
+  }
+#undef QMC_LATTICE_CASE
+}
+
+}  // namespace qmc

@@ -1,0 +1,115 @@
+// qmc_device.cuh -- device building blocks of the QMC hot path (sm_103a).
+//
+// Everything here is integer or fp32 register arithmetic; none of it touches
+// memory.  The definitions follow Keller, Waechter, Binder, "Quasi-Monte Carlo
+// Algorithms (not only) for Graphics Software": Sec. 2.1 (float conversion),
+// Sec. 2.3 (digital sequences, randomisation in integers), Sec. 2.4 (rank-1
+// lattices) and Sec. 2.5 (compensated, order-controlled reduction).
+#pragma once
+
+#include <cstdint>
+
+namespace qmc {
+
+// Sec. 2.1: the largest fp32 value not above u * 2^-32, so every component
+// stays in [0,1).  A uint->float conversion rounding toward zero keeps the 24
+// leading significant bits of u (all of them below 2^24, where the result is
+// exact and collision free); the scale by 2^-32 is exact because every
+// non-zero result is a normal number >= 2^-32.
+__device__ __forceinline__ float map_u32_to_unifloat(uint32_t u) {
+  return __uint2float_rz(u) * 0x1p-32f;
+}
+
+// Hash-based nested (Owen-type) scramble, applied in the mirrored digit domain
+// where the first digit 2^-1 sits in bit 0.  Each step changes bit b only as a
+// function of bits below b -- an add, a multiply by an odd number, an XOR
+// with a multiple by an even number -- so digit d of the scrambled value is
+// digit d of the input flipped by a function of the digits before it, and
+// the map is a bijection.  The seed enters as the addend and, rotated by 16
+// and made odd, as the multiplier.
+struct NestedKey {
+  uint32_t add;
+  uint32_t mul;
+};
+
+__device__ __forceinline__ NestedKey nested_key(uint32_t seed) {
+  return {seed, __funnelshift_l(seed, seed, 16) | 1u};
+}
+
+__device__ __forceinline__ uint32_t nested_mix(uint32_t v, NestedKey k) {
+  v += k.add;
+  v ^= v * 0xD37A65C4u;
+  v *= k.mul;
+  v ^= v * 0x2AAE6212u;
+  v ^= v * 0x2BB2601Eu;
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Compensated fp32 summation (Sec. 2.5.1 names Kahan's algorithm; this is
+// the Neumaier variant, whose error term is exact for either operand order).
+// ---------------------------------------------------------------------------
+struct Comp {
+  float sum;
+  float err;
+};
+
+// Knuth's TwoSum: t + e = a + b exactly (round-to-nearest, no branch).
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float t = __fadd_rn(a, b);
+  const float bv = __fsub_rn(t, a);
+  const float av = __fsub_rn(t, bv);
+  e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+  return t;
+}
+
+__device__ __forceinline__ void comp_add(Comp& c, float v) {
+  float e;
+  c.sum = two_sum(c.sum, v, e);
+  c.err = __fadd_rn(c.err, e);
+}
+
+// Merge two compensated states without losing the rounding error of the sums.
+__device__ __forceinline__ Comp comp_merge(Comp a, Comp b) {
+  float e;
+  Comp r;
+  r.sum = two_sum(a.sum, b.sum, e);
+  r.err = __fadd_rn(__fadd_rn(a.err, b.err), e);
+  return r;
+}
+
+// Fixed butterfly over the warp: every lane ends with the same merged state,
+// and the order of merges depends only on lane numbers (reproducible).
+__device__ __forceinline__ Comp warp_comp_sum(Comp c) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    Comp o;
+    o.sum = __shfl_xor_sync(0xffffffffu, c.sum, off);
+    o.err = __shfl_xor_sync(0xffffffffu, c.err, off);
+    // merge in lane order so both partners compute bit-identical results
+    c = ((threadIdx.x & off) == 0) ? comp_merge(c, o) : comp_merge(o, c);
+  }
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// Error-free fp32 products and a float-float reciprocal, used to keep
+// per-integral constants exact to ~2^-48 so that no systematic rounding error
+// is shared by all samples of an integral.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float two_prod(float a, float b, float& e) {
+  const float p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+  return p;
+}
+
+// 1 / (a_hi + a_lo) as hi + lo (one Newton correction of the rounded reciprocal).
+__device__ __forceinline__ float ff_recip(float a_hi, float a_lo, float& lo) {
+  const float r = __frcp_rn(a_hi);
+  // residual 1 - r (a_hi + a_lo), exact in its leading part thanks to the FMA
+  const float res = __fmaf_rn(-r, a_hi, 1.0f) - r * a_lo;
+  lo = r * res;
+  return r;
+}
+
+}  // namespace qmc

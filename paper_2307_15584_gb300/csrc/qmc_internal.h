@@ -1,0 +1,39 @@
+// qmc_internal.h -- host-side declarations shared by the translation units of
+// libqmc_gb300.so (never installed; the public interface is include/qmc.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace qmc {
+
+struct DeviceInfo {
+  int device;
+  int sm_count;
+  int cc_major, cc_minor;
+  size_t smem_per_block_optin;
+};
+
+// Properties of the current device (cached per device id).
+const DeviceInfo& device_info();
+
+// Arguments of the materialising kernels.
+struct PointsArgs {
+  const uint32_t* matrices;  // Sobol': [s][32] columns; lattice: [s] generator words
+  const uint32_t* seeds;     // Sobol': scramble seeds [s]; lattice: shifts [s] (nullable)
+  uint32_t* out_u32;         // [count][s] or null
+  float* out_f32;            // [count][s] or null
+  uint64_t count;
+  uint32_t s;
+  uint32_t index_begin;      // index_begin + count <= 2^32 was checked by the caller
+  uint32_t scramble;         // Sobol': 0 none, 1 XOR, 2 nested; lattice: bit 0 = backward
+  uint32_t q_log2;           // set by the launcher
+  uint32_t u_log2;           // set by the launcher
+};
+
+cudaError_t launch_sobol_points(PointsArgs a, cudaStream_t stream);
+cudaError_t launch_lattice_points(PointsArgs a, cudaStream_t stream);
+
+}  // namespace qmc

@@ -1,0 +1,129 @@
+"""The C-ABI library loads, exports every symbol include/qmc.h declares, and
+rejects invalid arguments on the host before touching CUDA.  CPU only: no
+call here reaches a kernel launch."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2307_15584_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2307_15584_gb300 import build
+
+    build.build()
+    from paper_2307_15584_gb300 import binding
+
+    return binding
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "qmc.h")).read()
+    return sorted(set(re.findall(r"QMC_API\s+[\w\s\*]+?\b(qmc_\w+)\s*\(", text)))
+
+
+def test_header_symbols_exported(B):
+    declared = _declared_symbols()
+    assert len(declared) >= 11
+    lib = ctypes.CDLL(B.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(B.EXPORTED) == sorted(declared)
+    assert B.qmc_abi_version() == 1
+    assert "INVALID" in B.qmc_status_string(1)
+
+
+def test_sobol_matrices_match_oracle(B, oracle):
+    """The library's host construction (Bratley-Fox form, primitivity by the
+    order test with prime factors) equals the oracle's (m-integer form, brute
+    order search) for every dimension it supports."""
+    raw = inputs.sobol_raw_init(37, seed=123)
+    got = B.qmc_sobol_matrices(37, raw)
+    np.testing.assert_array_equal(got, oracle.sobol_matrices(37, raw))
+    with pytest.raises(B.QMCError):
+        B.qmc_sobol_matrices(38, inputs.sobol_raw_init(38))
+    with pytest.raises(B.QMCError):
+        B.qmc_sobol_matrices(0, raw)
+
+
+FAKE = 0x10000  # an aligned non-null "device" address: never dereferenced (calls fail validation)
+
+
+def _status(fn, *args):
+    return fn(*args)
+
+
+def test_points_validation(B):
+    L = B._lib
+    S = None
+    # null matrices / no outputs / bad scramble / missing seeds
+    assert L.qmc_sobol_points(None, 4, 0, 16, 0, None, FAKE, None, S) == 1
+    assert L.qmc_sobol_points(FAKE, 4, 0, 16, 0, None, None, None, S) == 1
+    assert L.qmc_sobol_points(FAKE, 4, 0, 16, 3, FAKE, FAKE, None, S) == 1
+    assert L.qmc_sobol_points(FAKE, 4, 0, 16, 2, None, FAKE, None, S) == 1
+    assert L.qmc_sobol_points(FAKE, 0, 0, 16, 0, None, FAKE, None, S) == 1
+    assert L.qmc_sobol_points(FAKE, 1025, 0, 16, 0, None, FAKE, None, S) == 1
+    # index range beyond 2^32 (Sec. 2.5: no silent wrap-around)
+    assert L.qmc_sobol_points(FAKE, 4, (1 << 32) - 8, 9, 0, None, FAKE, None, S) == 2
+    assert L.qmc_sobol_points(FAKE, 4, 1 << 33, 1, 0, None, FAKE, None, S) == 2
+    # misaligned outputs
+    assert L.qmc_sobol_points(FAKE, 4, 0, 16, 0, None, FAKE + 2, None, S) == 3
+    assert L.qmc_lattice_points(FAKE, None, 4, 0, 16, 0, None, FAKE + 1, S) == 3
+    # lattice flags / generator
+    assert L.qmc_lattice_points(None, None, 4, 0, 16, 0, FAKE, None, S) == 1
+    assert L.qmc_lattice_points(FAKE, None, 4, 0, 16, 2, FAKE, None, S) == 1
+    # count = 0 is a no-op that needs no device
+    assert L.qmc_sobol_points(FAKE, 4, 0, 0, 0, None, FAKE, None, S) == 0
+    assert L.qmc_lattice_points(FAKE, None, 4, 1 << 32, 0, 0, FAKE, None, S) == 0
+
+
+def _problem(B, **kw):
+    d = dict(source=B.SOURCE_SOBOL, integrand=B.F_GAUSSMIX4_6D, s=6, randomize=B.SCRAMBLE_NESTED,
+             matrices=FAKE, seeds=FAKE, seeds_per_integral=True, max_count=65536)
+    d.update(kw)
+    return B.make_problem(**d)
+
+
+def test_workspace_sizing(B):
+    p = _problem(B)
+    counts = inputs.log_uniform_counts(1000)
+    exact = B.qmc_integrate_workspace_bytes(p, 1000, counts)
+    worst = B.qmc_integrate_workspace_bytes(p, 1000, None)
+    assert 0 < exact < worst
+    pg = _problem(B, with_gradient=True)
+    assert B.qmc_integrate_workspace_bytes(pg, 1000, counts) > exact
+    assert B.qmc_integrate_workspace_bytes(_problem(B, s=5), 10, None) == 0  # mixture needs s = 6
+    assert B.qmc_integrate_workspace_bytes(_problem(B, chunk=100), 10, None) == 0  # not a power of two
+
+
+def test_integrate_validation(B):
+    L = B._lib
+    ref = ctypes.byref
+    ws = 1 << 20  # fake 256-aligned address
+    p = _problem(B)
+    assert L.qmc_integrate(None, 4, FAKE, FAKE, FAKE, ws, 1 << 30, None) == 1
+    assert L.qmc_integrate(ref(p), 4, None, FAKE, FAKE, ws, 1 << 30, None) == 1
+    assert L.qmc_integrate(ref(p), 4, FAKE, None, FAKE, ws, 1 << 30, None) == 1  # mixture needs theta
+    assert L.qmc_integrate(ref(p), 4, FAKE, FAKE + 4, FAKE, ws, 1 << 30, None) == 3
+    assert L.qmc_integrate(ref(p), 4, FAKE, FAKE, FAKE, ws + 16, 1 << 30, None) == 7
+    assert L.qmc_integrate(ref(p), 4, FAKE, FAKE, FAKE, ws, 64, None) == 7
+    for bad in (dict(s=7), dict(integrand=9), dict(source=3), dict(randomize=5), dict(matrices=None),
+                dict(seeds=None), dict(block=48), dict(block=512), dict(chunk=16), dict(chunk=16384),
+                dict(integrand=B.F_BILINEAR2D, s=6), dict(integrand=B.F_GENZ_OSCILLATORY, s=17)):
+        assert L.qmc_integrate(ref(_problem(B, **bad)), 4, FAKE, FAKE, FAKE, ws, 1 << 30, None) == 1, bad
+    # backward / fused need the mixture and their outputs
+    pg = _problem(B, integrand=B.F_GENZ_PRODUCT_PEAK, s=16)
+    assert L.qmc_integrate_backward(ref(pg), 4, FAKE, FAKE, FAKE, FAKE, ws, 1 << 30, None) == 6
+    assert L.qmc_integrate_backward(ref(p), 4, FAKE, FAKE, None, FAKE, ws, 1 << 30, None) == 1
+    assert L.qmc_integrate_fwd_bwd(ref(p), 4, FAKE, FAKE, FAKE, FAKE, FAKE, None, ws, 1 << 30, None) == 1
+    assert L.qmc_integrate_points(ref(p), 4, FAKE, None, 0, FAKE, FAKE, ws, 1 << 30, None) == 1
+    assert L.qmc_integrate_points(ref(p), 4, FAKE, FAKE, 2, FAKE, FAKE, ws, 1 << 30, None) == 1
+    # n = 0 with valid arguments is a no-op
+    assert L.qmc_integrate(ref(p), 0, FAKE, FAKE, FAKE, ws, 1 << 30, None) == 0
+    assert L.qmc_read_device_error(None, ctypes.byref(ctypes.c_uint32()), None) == 1

@@ -1,0 +1,152 @@
+"""GPU parity of the materialised points (K1 Sobol', K2 lattice) against the
+oracle: bit-exact u32 and fp32 bit patterns, through the C-ABI."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2307_15584_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2307_15584_gb300 import binding
+
+    return binding
+
+
+def _f32_bits(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def _sobol_case(B, oracle, s, begin, count, mode, seed=7):
+    raw = inputs.sobol_raw_init(s, seed=seed)
+    C = B.qmc_sobol_matrices(min(s, 37), raw[: min(s, 37)])
+    if s > 37:  # more dimensions than polynomials: reuse columns (any matrices are valid input)
+        C = np.concatenate([C] * (s // 37 + 1))[:s]
+    seeds = inputs.scramble_seeds(s, seed=seed)
+    Cd, sd = B.u32_tensor(C), B.u32_tensor(seeds)
+    u, f = B.sobol_points(Cd, count, index_begin=begin, scramble=mode, seeds=sd if mode else None)
+    ou, of = oracle.sobol_points(C, begin, count, mode, seeds if mode else None)
+    np.testing.assert_array_equal(B.as_u32(u), ou)
+    np.testing.assert_array_equal(_f32_bits(f), of.view(np.uint32))
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("s", [1, 2, 3, 4, 5, 6, 12, 16, 24, 31, 32, 33, 64, 96])
+def test_sobol_points_bit_exact(B, oracle, s, mode):
+    """Fast path (s with K <= 4) and generic path, several groups and a ragged tail."""
+    count = 4096 * 3 + 37
+    _sobol_case(B, oracle, s, 0, count, mode)
+
+
+@pytest.mark.parametrize("begin", [1, 4, 5, 4096, 123457, (1 << 31) + 8, (1 << 32) - 3000])
+def test_sobol_points_offsets(B, oracle, begin):
+    for s, mode in ((32, 2), (2, 0), (6, 1)):
+        _sobol_case(B, oracle, s, begin, min(2999, (1 << 32) - begin), mode)
+
+
+def test_sobol_single_outputs_and_empty(B, oracle):
+    s, n = 32, 1000
+    C = B.qmc_sobol_matrices(s, inputs.sobol_raw_init(s))
+    seeds = inputs.scramble_seeds(s)
+    Cd, sd = B.u32_tensor(C), B.u32_tensor(seeds)
+    ou, of = oracle.sobol_points(C, 0, n, 2, seeds)
+    u, _ = B.sobol_points(Cd, n, scramble=2, seeds=sd, want_f32=False)
+    _, f = B.sobol_points(Cd, n, scramble=2, seeds=sd, want_u32=False)
+    np.testing.assert_array_equal(B.as_u32(u), ou)
+    np.testing.assert_array_equal(_f32_bits(f), of.view(np.uint32))
+    B.sobol_points(Cd, 0, scramble=2, seeds=sd)  # empty: no launch, no error
+    with pytest.raises(B.QMCError):
+        B.sobol_points(Cd, 16, index_begin=(1 << 32) - 8, scramble=2, seeds=sd)
+
+
+def test_config1_plain_2d_sobol_and_net(B, oracle):
+    """Config 1: 2-D Sobol', 2^16 points, unscrambled; bit-exact and a (0,16,2)-net."""
+    C = B.qmc_sobol_matrices(2, inputs.sobol_raw_init(2))
+    u, f = B.sobol_points(B.u32_tensor(C), 1 << 16)
+    ou, of = oracle.sobol_points(C, 0, 1 << 16)
+    gu = B.as_u32(u)
+    np.testing.assert_array_equal(gu, ou)
+    np.testing.assert_array_equal(_f32_bits(f), of.view(np.uint32))
+    for k1 in range(17):
+        code = ((gu[:, 0].astype(np.int64) >> (32 - k1)) << (16 - k1)) | (gu[:, 1].astype(np.int64) >> (16 + k1))
+        assert np.unique(code).size == 1 << 16, k1
+
+
+def test_config2_full_size_sampled(B, oracle):
+    """Config 2 at full size (s = 32, 2^24 points, nested scramble, u32 + fp32) in
+    the bench's launch configuration; rows checked: the first and last 4096, the
+    group boundaries of every warp range near them, and 2^14 random rows."""
+    s, N = 32, 1 << 24
+    C = B.qmc_sobol_matrices(s, inputs.sobol_raw_init(s))
+    seeds = inputs.scramble_seeds(s)
+    u, f = B.sobol_points(B.u32_tensor(C), N, scramble=2, seeds=B.u32_tensor(seeds))
+    rng = np.random.default_rng(5)
+    rows = np.unique(np.concatenate([np.arange(4096), np.arange(N - 4096, N),
+                                     rng.integers(0, N, size=1 << 14)]))
+    idx = torch.from_numpy(rows).cuda()
+    gu = B.as_u32(u.index_select(0, idx))
+    gf = _f32_bits(f.index_select(0, idx))
+    del u, f
+    for r0 in (0, N - 4096):
+        ou, of = oracle.sobol_points(C, r0, 4096, 2, seeds)
+        sel = np.searchsorted(rows, np.arange(r0, r0 + 4096))
+        np.testing.assert_array_equal(gu[sel], ou)
+        np.testing.assert_array_equal(gf[sel], of.view(np.uint32))
+    pos = {r: i for i, r in enumerate(rows.tolist())}
+    rand = rows[(rows >= 4096) & (rows < N - 4096)]
+    for r in rand[:: max(1, rand.size // 2048)].tolist():
+        ou, of = oracle.sobol_points(C, r, 1, 2, seeds, threads=1)
+        np.testing.assert_array_equal(gu[pos[r]], ou[0])
+        np.testing.assert_array_equal(gf[pos[r]], of[0].view(np.uint32))
+
+
+@pytest.mark.parametrize("backward", [False, True])
+@pytest.mark.parametrize("s", [1, 2, 3, 5, 16, 17, 32])
+def test_lattice_points_bit_exact(B, oracle, s, backward):
+    g = inputs.lattice_generator(s)
+    sh = inputs.lattice_shift(s)
+    for begin, count, shift in ((0, 4096 * 2 + 13, sh), (7, 3001, None), ((1 << 32) - 2000, 2000, sh)):
+        u, f = B.lattice_points(B.u32_tensor(g), count, index_begin=begin,
+                                shift=None if shift is None else B.u32_tensor(shift), backward=backward)
+        ou, of = oracle.lattice_points(g, shift, begin, count, backward)
+        np.testing.assert_array_equal(B.as_u32(u), ou)
+        np.testing.assert_array_equal(_f32_bits(f), of.view(np.uint32))
+
+
+def test_config3_lattice_full_size_sampled(B, oracle):
+    """Config 3 points: s = 16, 2^26 points, odd seeded g, integer CP shift."""
+    s, N = 16, 1 << 26
+    g, sh = inputs.lattice_generator(s), inputs.lattice_shift(s)
+    u, f = B.lattice_points(B.u32_tensor(g), N, shift=B.u32_tensor(sh))
+    rng = np.random.default_rng(6)
+    rows = np.unique(np.concatenate([np.arange(2048), np.arange(N - 2048, N), rng.integers(0, N, 4096)]))
+    idx = torch.from_numpy(rows).cuda()
+    gu, gf = B.as_u32(u.index_select(0, idx)), _f32_bits(f.index_select(0, idx))
+    del u, f
+    for i, r in enumerate(rows.tolist()):
+        if i % 7 and 2048 <= r < N - 2048:
+            continue
+        ou, of = oracle.lattice_points(g, sh, r, 1, threads=1)
+        np.testing.assert_array_equal(gu[i], ou[0])
+        np.testing.assert_array_equal(gf[i], of[0].view(np.uint32))
+
+
+def test_map_exhaustive_all_2pow32(B, oracle):
+    """Sec. 2.1: the GPU float mapping equals the oracle's for every one of the 2^32
+    inputs (the paper's own exhaustive check) and stays below 1; the oracle's
+    monotonicity is pinned on the CPU, so equality carries it over.  The 1-D
+    lattice with g = 1 enumerates phi_2(k), a permutation of all inputs."""
+    g = B.u32_tensor(np.array([1], np.uint32))
+    chunk = 1 << 28
+    top = 0.0
+    for c in range(1 << 4):
+        u, f = B.lattice_points(g, chunk, index_begin=c * chunk)
+        uu = B.as_u32(u).reshape(-1)
+        ff = f.cpu().numpy().reshape(-1)
+        del u, f
+        np.testing.assert_array_equal(ff.view(np.uint32), oracle.map_u32_to_unifloat(uu).view(np.uint32))
+        top = max(top, float(ff.max()))
+    assert top == float(np.float32(1.0) - np.float32(2.0**-24))
