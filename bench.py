@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true", help="headline only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    ap.add_argument("--log2-points", type=int, default=24, help="points per GPU (2^k); 24 is the workload")
     return ap.parse_args()
 
 
@@ -114,14 +115,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+KERNEL_SOURCES = {"sobol_points_fast<1,2>": ["points.cu", "qmc_device.cuh", "qmc_internal.h"]}
+
+
 def profile_traffic(kernel_key: str):
-    """dram bytes per launch from the committed ncu summary, if it matches the sources."""
+    """dram bytes per launch from the committed ncu summary, or None when the
+    kernel's sources changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     from paper_2307_15584_gb300.build import source_digest
 
-    digest = source_digest()
+    digest = source_digest(KERNEL_SOURCES[kernel_key])
     for line in open(path):
         parts = line.split()
         if len(parts) == 3 and parts[0] == kernel_key and parts[1] == digest:
@@ -130,7 +135,7 @@ def profile_traffic(kernel_key: str):
 
 
 # ------------------------------------------------------------------ oracle baseline
-def cpu_baseline(n_rows: int = 1 << 21):
+def cpu_baseline(n_rows: int = 1 << 23):
     import oracle
     from paper_2307_15584_gb300 import inputs
 
@@ -323,7 +328,7 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl", device_id=dev)
     stream = torch.cuda.current_stream()
 
-    begin, count = rank_window(rank, world)
+    begin, count = rank_window(rank, world, 1 << args.log2_points)
     C = B.qmc_sobol_matrices(S_DIMS, inputs.sobol_raw_init(S_DIMS))
     seeds = inputs.scramble_seeds(S_DIMS)
     Cd, sd = B.u32_tensor(C, dev), B.u32_tensor(seeds, dev)

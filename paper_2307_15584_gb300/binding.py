@@ -181,9 +181,12 @@ def qmc_read_device_error(workspace, stream=None) -> int:
 # ----------------------------------------------------------------- conveniences
 def make_problem(source, integrand, s, randomize=0, matrices=None, g=None, seeds=None,
                  seeds_per_integral=False, chunk=0, block=0, max_count=0, with_gradient=False) -> qmc_problem:
-    """A qmc_problem holding device pointers of the given tensors (keep them alive)."""
-    return qmc_problem(source, integrand, s, randomize, _dev(matrices), _dev(g), _dev(seeds),
-                       int(bool(seeds_per_integral)), chunk, block, max_count, int(bool(with_gradient)))
+    """A qmc_problem holding device pointers of the given tensors; the problem keeps
+    references to them so their memory stays valid while it is alive."""
+    p = qmc_problem(source, integrand, s, randomize, _dev(matrices), _dev(g), _dev(seeds),
+                    int(bool(seeds_per_integral)), chunk, block, max_count, int(bool(with_gradient)))
+    p._tensors = (matrices, g, seeds)
+    return p
 
 
 def alloc_workspace(problem: qmc_problem, n_integrals: int, h_counts=None, device="cuda") -> torch.Tensor:

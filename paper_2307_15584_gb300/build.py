@@ -27,13 +27,18 @@ def sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def source_digest() -> str:
-    """Short hash of every CUDA source and header (ties profile figures to a build)."""
+def source_digest(files: list[str] | None = None) -> str:
+    """Short hash of the given csrc files (default: every CUDA source and header);
+    ties a profile figure to the sources of the kernel it was taken from."""
     import hashlib
 
     h = hashlib.sha256()
-    deps = sorted(sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")))
-    for d in deps + [HEADER]:
+    if files:
+        deps = [os.path.join(CSRC, f) for f in files]
+    else:
+        deps = sorted(sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")))
+        deps.append(HEADER)
+    for d in deps:
         h.update(os.path.basename(d).encode())
         with open(d, "rb") as f:
             h.update(f.read())

@@ -166,8 +166,9 @@ qmc_status qmc_sobol_matrices(uint32_t s, const uint32_t* h_raw_init, uint32_t* 
 static qmc_status check_points_args(uint32_t s, uint64_t index_begin, uint64_t count,
                                     const void* out_u32, const void* out_f32) {
   if (s == 0 || s > 1024) return QMC_ERR_INVALID_ARG;
-  if (!out_u32 && !out_f32) return QMC_ERR_INVALID_ARG;
   if (index_begin > (1ull << 32) || count > (1ull << 32) - index_begin) return QMC_ERR_RANGE;
+  if (count == 0) return QMC_OK;  // nothing to write: outputs may be null (empty tensors)
+  if (!out_u32 && !out_f32) return QMC_ERR_INVALID_ARG;
   if (((uintptr_t)out_u32 & 3u) || ((uintptr_t)out_f32 & 3u)) return QMC_ERR_ALIGN;
   return QMC_OK;
 }

@@ -298,11 +298,19 @@ constexpr float kLog2eLo = 1.925963033500011079e-08f;
 template <int FN>
 struct Integrand;
 
+// Every integrand offers eval<EXACT>(x, err): f(x) in fp32 and, for adaptive
+// integrands, err = an estimate of the sample's rounding error scale.  EXACT
+// selects the float-float evaluation used when an item's error estimate is
+// over budget; non-adaptive integrands ignore it.
 template <>
 struct Integrand<QMC_F_BILINEAR2D> {
   static constexpr int S = 2;
+  static constexpr bool kAdaptive = false;
+  float wsum = 1.0f;
   __device__ void setup(const float*, uint32_t) {}
-  __device__ __forceinline__ float eval(const float* x) const {
+  template <bool EXACT>
+  __device__ __forceinline__ float eval(const float* x, float& err) const {
+    err = 0.0f;
     return __fmaf_rn(0.5f, x[0], 0.75f) * __fmaf_rn(0.5f, x[1], 0.75f);
   }
 };
@@ -310,6 +318,8 @@ struct Integrand<QMC_F_BILINEAR2D> {
 template <>
 struct Integrand<QMC_F_GENZ_PRODUCT_PEAK> {
   static constexpr int S = 16;
+  static constexpr bool kAdaptive = false;
+  float wsum = 1.0f;
   uint32_t s;
   float ch[16], cl[16], u[16];  // a^-2 = ch + cl
   __device__ void setup(const float* th, uint32_t s_) {
@@ -323,7 +333,9 @@ struct Integrand<QMC_F_GENZ_PRODUCT_PEAK> {
       ch[j] = ff_recip(a2, e, cl[j]);
     }
   }
-  __device__ __forceinline__ float eval(const float* x) const {
+  template <bool EXACT>
+  __device__ __forceinline__ float eval(const float* x, float& err) const {
+    err = 0.0f;
     float prod = 1.0f;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
@@ -339,6 +351,8 @@ struct Integrand<QMC_F_GENZ_PRODUCT_PEAK> {
 template <>
 struct Integrand<QMC_F_GENZ_OSCILLATORY> {
   static constexpr int S = 16;
+  static constexpr bool kAdaptive = false;
+  float wsum = 1.0f;
   uint32_t s;
   float a[16];
   float c0, s0;  // cos, sin of 2 pi u_1
@@ -349,7 +363,9 @@ struct Integrand<QMC_F_GENZ_OSCILLATORY> {
     sincospif(2.0f * __ldg(th + s), &s0, &c0);
   }
   // cos(2 pi u_1 + B) = cos(2 pi u_1) cos B - sin(2 pi u_1) sin B, B = sum_j a_j x_j
-  __device__ __forceinline__ float eval(const float* x) const {
+  template <bool EXACT>
+  __device__ __forceinline__ float eval(const float* x, float& err) const {
+    err = 0.0f;
     float B = 0.0f;
 #pragma unroll
     for (int j = 0; j < 16; ++j)
@@ -360,18 +376,31 @@ struct Integrand<QMC_F_GENZ_OSCILLATORY> {
   }
 };
 
+constexpr float kLn2 = 0.693147180559945309f;
+
+// Mixture of four separable Gaussians.  G_c = 2^t with t = -q_c k_c,
+// q_c = sum_d (x_d - m_{c,d})^2 and k_c = log2(e)/(2 sigma_c^2) held as a
+// float pair.  In fp32, q carries up to ~8 unit roundoffs of relative error,
+// so G_c's relative error grows like 8u ln2 |t|; err returns sum_c w_c G_c |t_c|
+// for the caller's budget test.  The EXACT path forms |x - m| exactly
+// (Fast2Sum on the ordered pair), squares it with an FMA residual, sums the
+// squares with TwoSum and applies the low word of t as a first-order factor.
 template <>
 struct Integrand<QMC_F_GAUSSMIX4_6D> {
   static constexpr int S = 6;
-  float w[4], mu[4], nu[4], kh[4], kl[4];  // kh + kl = log2(e) / (2 sigma^2)
-  float is2[4], is3[4];                    // 1/sigma^2, 1/sigma^3 (gradient only)
+  static constexpr bool kAdaptive = true;
+  float wsum;
+  float w[4], mu[4], nu[4], kh[4], kl[4];
+  float is2[4], is3[4];  // 1/sigma^2, 1/sigma^3 (gradient only)
   __device__ void setup(const float* th, uint32_t) {
+    wsum = 0.0f;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const float4 t = __ldg(reinterpret_cast<const float4*>(th) + c);
       w[c] = t.x;
       mu[c] = t.y;
       nu[c] = t.z;
+      wsum += fabsf(t.x);
       const float sg = t.w;
       float e;
       const float s2 = two_prod(sg, sg, e);  // sigma^2 = s2 + e exactly
@@ -385,38 +414,76 @@ struct Integrand<QMC_F_GAUSSMIX4_6D> {
       is3[c] = is2[c] * __frcp_rn(sg);
     }
   }
-  __device__ __forceinline__ float eval(const float* x) const {
-    float f = 0.0f;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
+
+  // 2^(-q k) for component c; q_out receives q (its leading word when EXACT).
+  template <bool EXACT>
+  __device__ __forceinline__ float gauss(const float* x, int c, float& q_out, float& t_abs) const {
+    if constexpr (!EXACT) {
       float q = 0.0f;
 #pragma unroll
       for (int d = 0; d < 6; ++d) {
         const float diff = __fsub_rn(x[d], (d & 1) ? nu[c] : mu[c]);
         q = __fmaf_rn(diff, diff, q);
       }
-      const float t = -__fmaf_rn(q, kh[c], __fmul_rn(q, kl[c]));
-      f = __fmaf_rn(w[c], ex2_approx(t), f);
+      const float t = __fmaf_rn(q, kh[c], __fmul_rn(q, kl[c]));
+      q_out = q;
+      t_abs = t;
+      return ex2_approx(-t);
+    } else {
+      float qh = 0.0f, ql = 0.0f;
+#pragma unroll
+      for (int d = 0; d < 6; ++d) {
+        const float m = (d & 1) ? nu[c] : mu[c];
+        const float hi = fmaxf(x[d], m), lo = fminf(x[d], m);
+        const float D = __fsub_rn(hi, lo);                        // |x - m| rounded
+        const float e = __fsub_rn(-lo, __fsub_rn(D, hi));         // exact remainder (Fast2Sum)
+        const float p = __fmul_rn(D, D);
+        const float pe = __fmaf_rn(2.0f * D, e, __fmaf_rn(D, D, -p));
+        float se;
+        qh = two_sum(qh, p, se);
+        ql = __fadd_rn(ql, __fadd_rn(se, pe));
+      }
+      const float th = __fmul_rn(qh, kh[c]);
+      const float tl = __fadd_rn(__fmaf_rn(qh, kh[c], -th), __fmaf_rn(qh, kl[c], __fmul_rn(ql, kh[c])));
+      q_out = qh;
+      t_abs = th;
+      return __fmul_rn(ex2_approx(-th), __fmaf_rn(-kLn2, tl, 1.0f));
+    }
+  }
+
+  template <bool EXACT>
+  __device__ __forceinline__ float eval(const float* x, float& err) const {
+    float f = 0.0f;
+    err = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float q, t;
+      const float wG = __fmul_rn(w[c], gauss<EXACT>(x, c, q, t));
+      f = __fadd_rn(f, wG);
+      err = __fmaf_rn(fabsf(wG), t, err);
     }
     return f;
   }
+
   // f and df/dtheta (theta order w, mu, nu, sigma per component)
-  __device__ __forceinline__ float eval_grad(const float* x, float* g) const {
+  template <bool EXACT>
+  __device__ __forceinline__ float eval_grad(const float* x, float* g, float& err) const {
     float f = 0.0f;
+    err = 0.0f;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      float q = 0.0f, se = 0.0f, so = 0.0f;
+      float se = 0.0f, so = 0.0f;
 #pragma unroll
       for (int d = 0; d < 6; ++d) {
         const float diff = __fsub_rn(x[d], (d & 1) ? nu[c] : mu[c]);
-        q = __fmaf_rn(diff, diff, q);
         if (d & 1) so = __fadd_rn(so, diff); else se = __fadd_rn(se, diff);
       }
-      const float t = -__fmaf_rn(q, kh[c], __fmul_rn(q, kl[c]));
-      const float G = ex2_approx(t);
+      float q, t;
+      const float G = gauss<EXACT>(x, c, q, t);
       const float wG = __fmul_rn(w[c], G);
       const float wg2 = __fmul_rn(wG, is2[c]);
       f = __fadd_rn(f, wG);
+      err = __fmaf_rn(fabsf(wG), t, err);
       g[4 * c + 0] = G;
       g[4 * c + 1] = __fmul_rn(wg2, se);
       g[4 * c + 2] = __fmul_rn(wg2, so);
@@ -457,11 +524,46 @@ __device__ __forceinline__ uint32_t find_integral(const uint32_t* off, uint32_t 
   return lo;
 }
 
+// Per-sample rounding-error coefficient of the fp32 mixture path: relative
+// error of G <= 8 u ln2 |t| (u = 2^-24), see Integrand<GAUSSMIX4_6D>.
+constexpr float kKappa = 8.0f * 5.9604645e-8f * kLn2;
+
+// One pass over the samples of the current item.  Returns nothing; adds into
+// acc and, on the fp32 pass, the squared per-sample error scales into e2.
+template <bool EXACT, bool GRAD, int NV, class Src, class F>
+__device__ __forceinline__ void run_item(const Src& src, const F& f, uint32_t len, Kahan (&acc)[NV],
+                                         float& e2) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t R = (len + 31u) >> 5;
+  for (uint32_t r = 0; r < R; ++r) {
+    const uint32_t il = (r << 5) + lane;
+    const bool valid = il < len;
+    float x[F::S];
+    src.point(r, il, valid, x);
+    float err;
+    if constexpr (GRAD) {
+      float g[16];
+      const float v = f.template eval_grad<EXACT>(x, g, err);
+      if (valid) {
+        acc[0].add(v);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc[1 + k].add(g[k]);
+        if constexpr (F::kAdaptive && !EXACT) e2 = __fmaf_rn(err, err, e2);
+      }
+    } else {
+      const float v = f.template eval<EXACT>(x, err);
+      if (valid) {
+        acc[0].add(v);
+        if constexpr (F::kAdaptive && !EXACT) e2 = __fmaf_rn(err, err, e2);
+      }
+    }
+  }
+}
+
 template <class Src, int FN, bool GRAD>
 __global__ void __launch_bounds__(256) integrate_main(IntegrateArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   using F = Integrand<FN>;
-  constexpr int S = F::S;
   constexpr int NV = GRAD ? 17 : 1;
   Src src;
   src.kernel_setup(a, smem);
@@ -485,23 +587,22 @@ __global__ void __launch_bounds__(256) integrate_main(IntegrateArgs a) {
     src.item_setup(a, p, start);
 
     Kahan acc[NV];
-    const uint32_t R = (len + 31u) >> 5;
-    for (uint32_t r = 0; r < R; ++r) {
-      const uint32_t il = (r << 5) + lane;
-      const bool valid = il < len;
-      float x[S];
-      src.point(r, il, valid, x);
-      if constexpr (GRAD) {
-        float g[16];
-        const float v = f.eval_grad(x, g);
-        if (valid) {
-          acc[0].add(v);
+    float e2 = 0.0f;
+    run_item<false, GRAD>(src, f, len, acc, e2);
+    if constexpr (F::kAdaptive) {
+      // Budget test on the item: the fp32 rounding errors of the samples are
+      // treated as independent, so their sum has scale kKappa sqrt(e2); an
+      // item whose 3-sigma error exceeds 0.6e-6 of its sum (plus its share of
+      // the 1e-12 W absolute floor) is recomputed on the exact path.  The test
+      // depends only on the item's data, so results stay reproducible.
 #pragma unroll
-          for (int k = 0; k < 16; ++k) acc[1 + k].add(g[k]);
-        }
-      } else {
-        const float v = f.eval(x);
-        if (valid) acc[0].add(v);
+      for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+      const Comp tot = warp_comp_sum(acc[0].comp());
+      const float budget = 0.6e-6f * fabsf(tot.sum + tot.err) + 0.5e-12f * f.wsum * (float)len;
+      if (3.0f * kKappa * sqrtf(e2) > budget) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] = Kahan{};
+        run_item<true, GRAD>(src, f, len, acc, e2);
       }
     }
     float* out = a.partials + (size_t)item * (2 * NV);

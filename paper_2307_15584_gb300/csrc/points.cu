@@ -57,7 +57,7 @@ __device__ __forceinline__ void warp_range(uint64_t n_groups, uint64_t& g0, uint
 // K1 fast path.  MODE: 0 none, 1 XOR, 2 nested.  K: 16-byte chunks per lane.
 // Shared memory: cols[s][32] (mirrored for nested), hin[2^u][s].
 // ---------------------------------------------------------------------------
-template <int K, int MODE>
+template <int K, int MODE, bool V4>  // V4: s % 4 == 0, chunks hold 4 consecutive dimensions
 __global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   const uint32_t s = a.s;
@@ -99,12 +99,15 @@ __global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
     }
 
   const uint64_t n_groups = (a.count + Q - 1) >> a.q_log2;
+  const uint64_t full_groups = a.count >> a.q_log2;  // groups whose Q rows all exist
   uint64_t g0, g1;
   warp_range(n_groups, g0, g1);
   const uint32_t G_first = a.index_begin >> a.q_log2;
   const uint32_t hi_shift = a.q_log2 + a.u_log2;
+  const uint64_t step = (uint64_t)Q * s;  // elements per group
+  uint64_t off = g0 * step + 4u * lane;   // this lane's first element in group g0
 
-  for (uint64_t g = g0; g < g1; ++g) {
+  for (uint64_t g = g0; g < g1; ++g, off += step) {
     const uint32_t G = G_first + (uint32_t)g;
     const uint32_t G_in = G & (nin - 1u);
     if (g == g0 || G_in == 0) {
@@ -117,26 +120,33 @@ __global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
         hout[e] = y;
       }
     }
-    const uint64_t row0 = g << a.q_log2;
-    const uint64_t rows_left = a.count - row0;
     const uint32_t* hrow = hin + G_in * s;
 #pragma unroll
     for (int c = 0; c < K; ++c) {
+      uint32_t h[4];
+      if (V4) {  // four consecutive dimensions: one 128-bit shared-memory load
+        const uint4 q = *reinterpret_cast<const uint4*>(hrow + jd[4 * c]);
+        h[0] = q.x, h[1] = q.y, h[2] = q.z, h[3] = q.w;
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) h[t] = hrow[jd[4 * c + t]];
+      }
       uint32_t v[4];
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        uint32_t y = hrow[jd[4 * c + t]] ^ hout[4 * c + t] ^ lo[4 * c + t];
+        uint32_t y = h[t] ^ hout[4 * c + t] ^ lo[4 * c + t];
         if (MODE == 2) y = __brev(nested_mix(y, key[4 * c + t]));
         v[t] = y;
       }
-      const uint32_t e0 = 4u * (lane + 32u * c);
-      const uint64_t off = row0 * s + e0;
-      if ((uint64_t)((e0 + 3) / s) < rows_left) {
-        store4(a.out_u32, a.out_f32, off, v);
-      } else {
+      const uint64_t o = off + 128u * c;
+      if (g < full_groups) {
+        store4(a.out_u32, a.out_f32, o, v);
+      } else {  // ragged last group: per-element row test
+        const uint64_t rows_left = a.count - (g << a.q_log2);
+        const uint32_t e0 = 4u * (lane + 32u * c);
 #pragma unroll
         for (int t = 0; t < 4; ++t)
-          if ((uint64_t)((e0 + t) / s) < rows_left) store1(a.out_u32, a.out_f32, off + t, v[t]);
+          if ((uint64_t)((e0 + t) / s) < rows_left) store1(a.out_u32, a.out_f32, o + t, v[t]);
       }
     }
   }
@@ -182,27 +192,29 @@ __global__ void __launch_bounds__(kThreads) lattice_points_fast(PointsArgs a) {
       lo[4 * c + t] = BACKWARD ? sh - g - phi_p * g : phi_p * g + sh;
     }
   const uint64_t n_groups = (a.count + Q - 1) >> a.q_log2;
+  const uint64_t full_groups = a.count >> a.q_log2;
   uint64_t g0, g1;
   warp_range(n_groups, g0, g1);
   const uint32_t G_first = a.index_begin >> a.q_log2;
-  for (uint64_t g = g0; g < g1; ++g) {
+  const uint64_t step = (uint64_t)Q * s;
+  uint64_t off = g0 * step + 4u * lane;
+  for (uint64_t g = g0; g < g1; ++g, off += step) {
     const uint32_t phib = __brev((G_first + (uint32_t)g) << a.q_log2);
-    const uint64_t row0 = g << a.q_log2;
-    const uint64_t rows_left = a.count - row0;
 #pragma unroll
     for (int c = 0; c < K; ++c) {
       uint32_t v[4];
 #pragma unroll
       for (int t = 0; t < 4; ++t)
         v[t] = BACKWARD ? lo[4 * c + t] - phib * gj[4 * c + t] : phib * gj[4 * c + t] + lo[4 * c + t];
-      const uint32_t e0 = 4u * (lane + 32u * c);
-      const uint64_t off = row0 * s + e0;
-      if ((uint64_t)((e0 + 3) / s) < rows_left) {
-        store4(a.out_u32, a.out_f32, off, v);
-      } else {
+      const uint64_t o = off + 128u * c;
+      if (g < full_groups) {
+        store4(a.out_u32, a.out_f32, o, v);
+      } else {  // ragged last group: per-element row test
+        const uint64_t rows_left = a.count - (g << a.q_log2);
+        const uint32_t e0 = 4u * (lane + 32u * c);
 #pragma unroll
         for (int t = 0; t < 4; ++t)
-          if ((uint64_t)((e0 + t) / s) < rows_left) store1(a.out_u32, a.out_f32, off + t, v[t]);
+          if ((uint64_t)((e0 + t) / s) < rows_left) store1(a.out_u32, a.out_f32, o + t, v[t]);
       }
     }
   }
@@ -291,11 +303,18 @@ cudaError_t launch_sobol_points(PointsArgs a, cudaStream_t stream) {
   a.u_log2 = u;
   const size_t smem = ((size_t)a.s * 32 + ((size_t)1 << u) * a.s) * sizeof(uint32_t);
   const uint64_t groups = (a.count + (1u << a.q_log2) - 1) >> a.q_log2;
-#define QMC_SOBOL_CASE(KK)                                                                    \
-  case KK:                                                                                    \
-    if (a.scramble == 0) return launch_persistent(sobol_points_fast<KK, 0>, groups, smem, stream, a); \
-    if (a.scramble == 1) return launch_persistent(sobol_points_fast<KK, 1>, groups, smem, stream, a); \
-    return launch_persistent(sobol_points_fast<KK, 2>, groups, smem, stream, a);
+  const bool v4 = (a.s & 3u) == 0;
+#define QMC_SOBOL_MODES(KK, V)                                                                        \
+  if (a.scramble == 0) return launch_persistent(sobol_points_fast<KK, 0, V>, groups, smem, stream, a); \
+  if (a.scramble == 1) return launch_persistent(sobol_points_fast<KK, 1, V>, groups, smem, stream, a); \
+  return launch_persistent(sobol_points_fast<KK, 2, V>, groups, smem, stream, a);
+#define QMC_SOBOL_CASE(KK)      \
+  case KK:                      \
+    if (v4) {                   \
+      QMC_SOBOL_MODES(KK, true)  \
+    } else {                    \
+      QMC_SOBOL_MODES(KK, false) \
+    }
   switch (K) {
     QMC_SOBOL_CASE(1)
     QMC_SOBOL_CASE(2)
@@ -304,6 +323,7 @@ cudaError_t launch_sobol_points(PointsArgs a, cudaStream_t stream) {
     default: return cudaErrorInvalidValue;
   }
 #undef QMC_SOBOL_CASE
+#undef QMC_SOBOL_MODES
 }
 
 cudaError_t launch_lattice_points(PointsArgs a, cudaStream_t stream) {

@@ -99,6 +99,22 @@ def test_config4_batched_small(B, oracle):
                            counts[bad][:10])
 
 
+def test_tail_dominated_single_samples(B, oracle):
+    """Pixels with one or a few samples, often far in a Gaussian's tail (where the
+    fp32 exponent argument's rounding error grows with |t|): the adaptive float-float
+    recomputation keeps every estimate within 1e-6 of the fp64 oracle."""
+    n = 8000
+    counts = np.where(np.arange(n) % 4 == 0, 1, np.arange(n) % 7 + 1).astype(np.uint32)
+    C6, theta, seeds, dev, prob = _gaussmix_case(B, n, counts, seed=31)
+    e = _run_forward(B, prob, n, dev, counts)
+    ref = oracle.integrate(oracle.SOURCE_SOBOL, oracle.F_GAUSSMIX4_6D, 6, counts, theta, C=C6,
+                           scramble=oracle.SCRAMBLE_NESTED, seeds=seeds)
+    W = np.abs(theta[:, 0::4]).sum(axis=1)
+    err = np.abs(e - ref["est"])
+    bad = err > est_tol(ref["est"], W)
+    assert not bad.any(), (np.nonzero(bad)[0][:10], (err / np.abs(ref["est"]))[bad][:10])
+
+
 @pytest.mark.parametrize("scramble", [0, 1])
 def test_other_scrambles_and_chunks(B, oracle, scramble):
     n = 200
@@ -142,6 +158,7 @@ def test_capacity_error_is_reported_not_overrun(B):
     n = 64
     counts = np.full(n, 50000, np.uint32)
     C6, theta, seeds, dev, prob = _gaussmix_case(B, n, counts)
+    prob.with_gradient = 0  # forward-only sizing: one partial per work item
     small = B.qmc_integrate_workspace_bytes(prob, n, np.full(n, 100, np.uint32))
     ws = torch.zeros(small, dtype=torch.uint8, device="cuda")
     est = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -174,7 +191,10 @@ def test_config5_fwd_bwd_small(B, oracle):
     r = ref["est"] - target
     assert loss.item() == pytest.approx(float((r * r).sum()), rel=1e-5)
     g_ref = 2.0 * r[:, None] * ref["grad"]
-    g_tol = 1e-5 * 2.0 * np.abs(r)[:, None] * (np.abs(ref["grad"]) + ref["grad_mass"]) + 1e-12 * W[:, None]
+    # d(2 (I - T) J) = 2 dI J + 2 (I - T) dJ: the estimate's own tolerance enters through dI
+    e_tol = est_tol(ref["est"], W)
+    g_tol = 2.0 * (e_tol[:, None] * np.abs(ref["grad"])
+                   + 1e-5 * np.abs(r)[:, None] * (np.abs(ref["grad"]) + ref["grad_mass"])) + 1e-12 * W[:, None]
     g = gth.cpu().numpy()
     assert (np.abs(g - g_ref) <= g_tol).all(), np.max(np.abs(g - g_ref) / g_tol)
     # unfused backward with an upstream gradient of 2 (I - T)
