@@ -233,6 +233,38 @@ QMC_API qmc_status qmc_integrate_points(const qmc_problem* p, uint32_t n_integra
                                 double* d_estimate, void* d_workspace, size_t workspace_bytes,
                                 qmc_stream_t stream);
 
+/* Size of the device array qmc_integrate_static works in (16 MiB per GPU that
+ * loads the library, held until the process exits). */
+#define QMC_STATIC_WORKSPACE_BYTES (16u << 20)
+
+/*
+ * qmc_integrate for callers that cannot allocate device memory.  The paper has
+ * no counterpart: this is an interface for hosts such as a plug-in inside an
+ * application that owns all GPU memory, a frame loop that cannot afford
+ * cudaMalloc's implicit synchronisation, or a process whose memory budget is
+ * fixed at start-up.  It takes the same inputs and output as qmc_integrate but
+ * no workspace: the scratch is a fixed device array of
+ * QMC_STATIC_WORKSPACE_BYTES inside the library.  It allocates nothing and calls
+ * no allocating routine.
+ *   p->max_count must bound every count; the call is rejected with
+ *   QMC_ERR_WORKSPACE when the worst case for n_integrals integrals of up to
+ *   max_count samples (forward only) does not fit the array, and with
+ *   QMC_ERR_INVALID_ARG when max_count is 0.  Counts above max_count that do not
+ *   fit are caught on the device: the estimates become NaN.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current); make that first call
+ *   before capturing any stream into a CUDA graph.
+ *   Every call on a device shares the one array, and it keeps the previous
+ *   call's contents; each call's first kernel resets the scheduler and error
+ *   words, and every other region is written before it is read.  Calls whose
+ *   work overlaps on the GPU (different streams or threads without ordering)
+ *   race on the array and corrupt each other's results: order them on one
+ *   stream.
+ */
+QMC_API qmc_status qmc_integrate_static(const qmc_problem* p, uint32_t n_integrals,
+                                        const uint32_t* d_counts, const float* d_theta,
+                                        double* d_estimate, qmc_stream_t stream);
+
 /* In-kernel error bits of the last integration that used this workspace
  * (0 = none; bit 0: more work items than the workspace holds).  Synchronises
  * `stream`. */

@@ -34,7 +34,7 @@ F_BILINEAR2D, F_GENZ_PRODUCT_PEAK, F_GENZ_OSCILLATORY, F_GAUSSMIX4_6D = 0, 1, 2,
 EXPORTED = ["qmc_abi_version", "qmc_status_string", "qmc_sobol_matrices", "qmc_sobol_points",
             "qmc_lattice_points", "qmc_integrate_workspace_bytes", "qmc_integrate",
             "qmc_integrate_backward", "qmc_integrate_fwd_bwd", "qmc_integrate_points",
-            "qmc_read_device_error"]
+            "qmc_read_device_error", "qmc_integrate_static"]
 
 
 class QMCError(RuntimeError):
@@ -67,6 +67,7 @@ _sigs = {
     "qmc_integrate_points": (ctypes.c_int, [ctypes.POINTER(qmc_problem), c_uint32, _P, _P, c_uint32, _P, _P,
                                             _P, c_size_t, _P]),
     "qmc_read_device_error": (ctypes.c_int, [_P, ctypes.POINTER(c_uint32), _P]),
+    "qmc_integrate_static": (ctypes.c_int, [ctypes.POINTER(qmc_problem), c_uint32, _P, _P, _P, _P]),
 }
 for _name, (_res, _args) in _sigs.items():
     _fn = getattr(_lib, _name)
@@ -169,6 +170,15 @@ def qmc_integrate_points(problem, n_integrals, counts, points, points_shared, th
     _check(_lib.qmc_integrate_points(ctypes.byref(problem), n_integrals, _dev(counts), _dev(points),
                                      int(points_shared), _dev(theta), _dev(estimate), _dev(workspace), wb,
                                      _stream(stream)), "qmc_integrate_points")
+
+
+def qmc_integrate_static(problem, n_integrals, counts, theta, estimate, stream=None):
+    """qmc_integrate without a workspace argument, for callers that cannot allocate
+    device memory: the library integrates in its own fixed device array (see
+    include/qmc.h for the size limit and the rule that calls on a device must not
+    overlap)."""
+    _check(_lib.qmc_integrate_static(ctypes.byref(problem), n_integrals, _dev(counts), _dev(theta),
+                                     _dev(estimate), _stream(stream)), "qmc_integrate_static")
 
 
 def qmc_read_device_error(workspace, stream=None) -> int:
