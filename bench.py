@@ -12,16 +12,18 @@ Also reported in the same JSON line:
   roofline      the point kernel against the measured HBM copy bandwidth
   cpu_baseline  the oracle on a bounded sample, on the host's cores
   fused         fused forward+backward of the differentiable integro-
-                approximation (1024x1024 integrals x 4096 samples), the
+                approximation (1024x1024 integrals x 4096 samples) against the
                 unfused forward + backward kernels, the batched 1920x1080
-                integration and the fused rank-1 lattice Genz integration,
-                each in Gsamples/s with its error against the oracle on a
-                sample of results
+                integration, and the rank-1 lattice Genz integration (fused,
+                and unfused through 4 GiB of materialised points), each in
+                Gsamples/s with its error against the oracle on sampled results
+                and its instruction-issue roofline
 
---impl reference times the oracle (the plain CPU reference of the same
-computation) on a bounded sample of the headline workload.
-Under torchrun every rank materialises its own index window (weak scaling,
-no collective on the data path); rank 0 prints the line.
+--only {fwd_bwd,batched,lattice} --small runs one integration workload alone at a
+reduced size (for ncu captures); --impl reference times the oracle (the plain
+CPU reference of the same computation) on a bounded sample of the headline
+workload.  Under torchrun every rank materialises its own index window (weak
+scaling, no collective on the data path); rank 0 prints the line.
 """
 from __future__ import annotations
 
@@ -40,6 +42,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "scrambled Sobol Gdims/s; fused QMC fwd+bwd Gsamples/s at stated err, % roofline"
 S_DIMS, N_POINTS = 32, 1 << 24
+SMS, SCHEDULERS_PER_SM, WARP = 152, 4, 32  # GB300: one warp-instruction per scheduler per clock
 
 
 def parse():
@@ -51,6 +54,9 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="headline only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     ap.add_argument("--log2-points", type=int, default=24, help="points per GPU (2^k); 24 is the workload")
+    ap.add_argument("--only", choices=["fwd_bwd", "batched", "lattice"], default=None,
+                    help="run one integration workload alone (no headline)")
+    ap.add_argument("--small", action="store_true", help="reduced integration sizes (profiling)")
     return ap.parse_args()
 
 
@@ -66,14 +72,15 @@ def rank_window(rank: int, world: int, n: int = N_POINTS):
     return rank * n, n
 
 
-# ------------------------------------------------------------------ peaks, clocks
+# ------------------------------------------------------------------ peaks, clocks, profiles
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
             d = json.load(f)
-        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
-    return {"hbm_gbs": 6800.0, "source": "fallback"}
+        return {"hbm_gbs": float(d["hbm_gbs"]), "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
 
 
 class ClockSampler:
@@ -115,23 +122,44 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-KERNEL_SOURCES = {"sobol_points_fast<1,2>": ["points.cu", "qmc_device.cuh", "qmc_internal.h"]}
+POINTS_SOURCES = ["points.cu", "qmc_device.cuh", "qmc_internal.h"]
+INTEGRATE_SOURCES = ["integrate.cu", "qmc_device.cuh", "qmc_integrate.h", "qmc_internal.h"]
+KERNEL_SOURCES = {"sobol_points_fast<1,2>": POINTS_SOURCES}
 
 
-def profile_traffic(kernel_key: str):
-    """dram bytes per launch from the committed ncu summary, or None when the
+def _profile_value(fname: str, key: str, files):
+    """A per-kernel figure from a committed profile summary, or None when the
     kernel's sources changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    path = os.path.join(ROOT, "profiles", fname)
     if not os.path.exists(path):
         return None
     from paper_2307_15584_gb300.build import source_digest
 
-    digest = source_digest(KERNEL_SOURCES[kernel_key])
+    digest = source_digest(files)
     for line in open(path):
         parts = line.split()
-        if len(parts) == 3 and parts[0] == kernel_key and parts[1] == digest:
+        if len(parts) == 3 and parts[0] == key and parts[1] == digest:
             return float(parts[2])
     return None
+
+
+def profile_traffic(kernel_key: str):
+    return _profile_value("traffic.txt", kernel_key, KERNEL_SOURCES[kernel_key])
+
+
+def issue_roofline(samples_per_s: float, key: str, sm_mhz):
+    """Instruction-issue roofline of a fused integration kernel: thread-instructions
+    per sample (ncu, committed in profiles/inst_per_sample.txt) x samples/s against
+    SMs x schedulers x 32 lanes x SM clock."""
+    ips = _profile_value("inst_per_sample.txt", key, INTEGRATE_SOURCES)
+    clock = sm_mhz or measured_peaks()["sm_max_mhz"]
+    peak = SMS * SCHEDULERS_PER_SM * WARP * clock * 1e6 / 1e9  # Ginst/s
+    if ips is None:
+        return {"bound": "alu", "achieved": None, "peak": peak, "unit": "Ginst/s", "frac": None,
+                "inst_per_sample": None, "kernel": key}
+    achieved = samples_per_s * ips / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Ginst/s", "frac": achieved / peak,
+            "inst_per_sample": ips, "kernel": key, "clock_mhz": clock}
 
 
 # ------------------------------------------------------------------ oracle baseline
@@ -160,13 +188,13 @@ def run_reference(args, world, rank):
     C = oracle.sobol_matrices(S_DIMS, inputs.sobol_raw_init(S_DIMS))
     seeds = inputs.scramble_seeds(S_DIMS)
     threads = os.cpu_count() or 1
-    rows = 1 << 14
+    rows = 1 << 17
     for _ in range(args.warmup):
         oracle.sobol_points(C, 0, rows, oracle.SCRAMBLE_NESTED, seeds, threads=threads)
     times = []
     for k in range(args.steps):
         t0 = time.perf_counter()
-        oracle.sobol_points(C, k * rows, rows, oracle.SCRAMBLE_NESTED, seeds, threads=threads)
+        oracle.sobol_points(C, (k * rows) % N_POINTS, rows, oracle.SCRAMBLE_NESTED, seeds, threads=threads)
         times.append(time.perf_counter() - t0)
     ms = 1e3 * sum(times) / len(times)
     value = rows * S_DIMS / (ms * 1e-3) / 1e9
@@ -199,8 +227,8 @@ def timed(fn, steps, warmup, stream):
     return [s.elapsed_time(e) for s, e in zip(start, end)]
 
 
-def bench_extra(dev, steps, warmup):
-    """Integration workloads: throughput and error against the oracle on a sample."""
+def bench_fwd_bwd(dev, steps, warmup, small, sm_mhz):
+    """Config 5: 1024x1024 integrals (2^16 when small) x 4096 samples, 16 parameters each."""
     import torch
 
     import oracle
@@ -208,11 +236,8 @@ def bench_extra(dev, steps, warmup):
     from paper_2307_15584_gb300 import inputs
 
     stream = torch.cuda.current_stream()
-    out = {}
     rng = np.random.default_rng(1)
-
-    # -- differentiable integro-approximation: 1024x1024 x 4096, fused fwd+bwd
-    n = 1 << 20
+    n = 1 << (16 if small else 20)
     counts = np.full(n, 4096, np.uint32)
     C6 = B.qmc_sobol_matrices(6, inputs.sobol_raw_init(6))
     theta = inputs.gaussmix_theta(n)
@@ -238,8 +263,16 @@ def bench_extra(dev, steps, warmup):
         B.qmc_integrate_backward(prob, n, d["c"], d["th"], ge, gb, ws)
 
     samples = float(counts.sum())
+    tuned = B.qmc_tune_integrate(prob, n, d["c"], d["th"], est, ws, target=d["tg"], grad_theta=gth, loss=loss)
+    B.qmc_tune_integrate(prob, n, d["c"], d["th"], est, ws)  # the unfused forward's own split
     tf = timed(fused, steps, warmup, stream)
-    tu = timed(unfused, max(2, steps // 2), 2, stream)
+    out = {"pixels": n, "samples_per_pixel": 4096, "tuned": {"chunk": tuned.chunk, "block": tuned.block}}
+    out["fused_ms"] = statistics.median(tf)
+    out["fused_gsamples_s"] = samples / (out["fused_ms"] * 1e-3) / 1e9
+    if not small:
+        tu = timed(unfused, max(2, steps // 2), 2, stream)
+        out["unfused_ms"] = statistics.median(tu)
+        out["unfused_gsamples_s"] = samples / (out["unfused_ms"] * 1e-3) / 1e9
     fused()
     torch.cuda.synchronize()
     pix = np.sort(rng.choice(n, 64, replace=False))
@@ -247,22 +280,34 @@ def bench_extra(dev, steps, warmup):
                            scramble=oracle.SCRAMBLE_NESTED, seeds=seeds[pix], with_grad=True)
     e = est.cpu().numpy()[pix]
     g = gth.cpu().numpy()[pix]
+    W = np.abs(theta[pix][:, 0::4]).sum(axis=1)
     r = ref["est"] - target[pix]
+    tol_i = 1e-6 * np.abs(ref["est"]) + 1e-12 * W
     g_ref = 2 * r[:, None] * ref["grad"]
-    g_scale = 2 * np.abs(r)[:, None] * (np.abs(ref["grad"]) + ref["grad_mass"])
-    out["fwd_bwd_1024x1024x4096"] = {
-        "fused_gsamples_s": samples / (statistics.median(tf) * 1e-3) / 1e9,
-        "unfused_gsamples_s": samples / (statistics.median(tu) * 1e-3) / 1e9,
-        "fused_ms": statistics.median(tf), "unfused_ms": statistics.median(tu),
-        "est_max_rel_err_vs_oracle": float(np.max(np.abs(e - ref["est"]) / np.abs(ref["est"]))),
-        "grad_max_err_over_scale": float(np.max(np.abs(g - g_ref) / np.maximum(g_scale, 1e-300))),
-        "oracle_sample_pixels": int(pix.size)}
-    del ws, est, gth, gb, d
-    torch.cuda.empty_cache()
+    g_tol = 2 * (tol_i[:, None] * np.abs(ref["grad"]) + 1e-5 * np.abs(r)[:, None] *
+                 (np.abs(ref["grad"]) + ref["grad_mass"])) + 1e-12 * W[:, None]
+    out["est_max_rel_err_vs_oracle"] = float(np.max(np.abs(e - ref["est"]) / np.abs(ref["est"])))
+    out["est_within_tol"] = f"{int((np.abs(e - ref['est']) <= tol_i).sum())}/{pix.size}"
+    out["grad_max_err_over_tol"] = float(np.max(np.abs(g - g_ref) / g_tol))
+    out["oracle_sample_pixels"] = int(pix.size)
+    out["roofline"] = issue_roofline(out["fused_gsamples_s"] * 1e9, "integrate_main<sobol6,nested,gaussmix,grad>",
+                                     sm_mhz)
+    return out
 
-    # -- batched 1920x1080, log-uniform counts in [1, 65536]
-    n = 1920 * 1080
+
+def bench_batched(dev, steps, warmup, small, sm_mhz):
+    """Config 4: 1920x1080 integrals (480x270 when small), log-uniform counts in [1, 65536]."""
+    import torch
+
+    import oracle
+    from paper_2307_15584_gb300 import binding as B
+    from paper_2307_15584_gb300 import inputs
+
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(2)
+    n = 480 * 270 if small else 1920 * 1080
     counts = inputs.log_uniform_counts(n)
+    C6 = B.qmc_sobol_matrices(6, inputs.sobol_raw_init(6))
     theta = inputs.gaussmix_theta(n, seed=7)
     seeds = inputs.pixel_seeds(n, 6, seed=7)
     d = {"C": B.u32_tensor(C6, dev), "c": B.u32_tensor(counts, dev), "th": torch.from_numpy(theta).to(dev),
@@ -272,45 +317,96 @@ def bench_extra(dev, steps, warmup):
     ws = B.alloc_workspace(prob, n, counts, dev)
     est = torch.empty(n, dtype=torch.float64, device=dev)
 
-    def batched():
-        B.qmc_integrate(prob, n, d["c"], d["th"], est, ws)
+    tuned = B.qmc_tune_integrate(prob, n, d["c"], d["th"], est, ws)
+    # the whole batch (scans, persistent kernel, reduction) as one CUDA graph
+    side = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        B.qmc_graph_begin(side)
+        B.qmc_integrate(prob, n, d["c"], d["th"], est, ws, stream=side)
+        graph = B.qmc_graph_end(side)
 
-    tb = timed(batched, max(2, steps // 2), 2, stream)
+    def batched():
+        B.qmc_graph_launch(graph, stream)
+
+    tb = timed(batched, steps, warmup, stream)
     batched()
     torch.cuda.synchronize()
+    B.qmc_graph_destroy(graph)
     pix = np.sort(rng.choice(n, 256, replace=False))
     ref = oracle.integrate(oracle.SOURCE_SOBOL, oracle.F_GAUSSMIX4_6D, 6, counts[pix], theta[pix], C=C6,
                            scramble=oracle.SCRAMBLE_NESTED, seeds=seeds[pix])
     e = est.cpu().numpy()[pix]
     W = np.abs(theta[pix][:, 0::4]).sum(axis=1)
     err = np.abs(e - ref["est"])
-    out["batched_1920x1080"] = {
-        "gsamples_s": float(counts.sum()) / (statistics.median(tb) * 1e-3) / 1e9, "ms": statistics.median(tb),
-        "samples": int(counts.sum()),
-        "max_rel_err_vs_oracle": float(np.max(err / np.maximum(np.abs(ref["est"]), 1e-300))),
-        "within_tol": int((err <= 1e-6 * np.abs(ref["est"]) + 1e-12 * W).sum()), "oracle_sample_pixels": int(pix.size)}
-    del ws, est, d
-    torch.cuda.empty_cache()
+    ms = statistics.median(tb)
+    gs = float(counts.sum()) / (ms * 1e-3) / 1e9
+    return {"pixels": n, "samples": int(counts.sum()), "ms": ms, "gsamples_s": gs, "graph": True,
+            "tuned": {"chunk": tuned.chunk, "block": tuned.block},
+            "max_rel_err_vs_oracle": float(np.max(err / np.maximum(np.abs(ref["est"]), 1e-300))),
+            "within_tol": f"{int((err <= 1e-6 * np.abs(ref['est']) + 1e-12 * W).sum())}/{pix.size}",
+            "oracle_sample_pixels": int(pix.size),
+            "roofline": issue_roofline(gs * 1e9, "integrate_main<sobol6,nested,gaussmix>", sm_mhz)}
 
-    # -- rank-1 lattice s = 16, 2^26 points, Genz product peak + oscillatory, 4 sets each
-    s, N = 16, 1 << 26
+
+def bench_lattice(dev, steps, warmup, small, sm_mhz):
+    """Config 3: rank-1 lattice s = 16, 2^26 points (2^22 when small) with CP shift, Genz
+    product peak and oscillatory, 4 seeded parameter sets each; fused, and unfused
+    through materialised fp32 points."""
+    import torch
+
+    import oracle
+    from paper_2307_15584_gb300 import binding as B
+    from paper_2307_15584_gb300 import inputs
+
+    stream = torch.cuda.current_stream()
+    s, N = 16, 1 << (22 if small else 26)
     g, sh = inputs.lattice_generator(s), inputs.lattice_shift(s)
-    res = {}
+    gd, shd = B.u32_tensor(g, dev), B.u32_tensor(sh, dev)
+    pts = None if small else torch.empty((N, s), dtype=torch.float32, device=dev)
+    res = {"points": N, "s": s}
     for fam, kind in (("product_peak", B.F_GENZ_PRODUCT_PEAK), ("oscillatory", B.F_GENZ_OSCILLATORY)):
         theta = np.stack([inputs.genz_params(fam, s, k) for k in range(4)])
         counts = np.full(4, N, np.uint32)
-        d = {"g": B.u32_tensor(g, dev), "sh": B.u32_tensor(sh, dev), "c": B.u32_tensor(counts, dev),
-             "th": torch.from_numpy(theta).to(dev)}
-        prob = B.make_problem(B.SOURCE_LATTICE, kind, s, 0, g=d["g"], seeds=d["sh"])
+        cd, thd = B.u32_tensor(counts, dev), torch.from_numpy(theta).to(dev)
+        prob = B.make_problem(B.SOURCE_LATTICE, kind, s, 0, g=gd, seeds=shd)
         ws = B.alloc_workspace(prob, 4, counts, dev)
         est = torch.empty(4, dtype=torch.float64, device=dev)
-        tl = timed(lambda: B.qmc_integrate(prob, 4, d["c"], d["th"], est, ws), max(2, steps // 2), 2, stream)
+        tuned = B.qmc_tune_integrate(prob, 4, cd, thd, est, ws)
+        tl = timed(lambda: B.qmc_integrate(prob, 4, cd, thd, est, ws), steps, warmup, stream)
         e = est.cpu().numpy()
         exact = np.array([oracle.exact_genz_product_peak(t, s) if fam == "product_peak"
                           else oracle.exact_genz_oscillatory(t, s) for t in theta])
-        res[fam] = {"gsamples_s": 4.0 * N / (statistics.median(tl) * 1e-3) / 1e9, "ms": statistics.median(tl),
-                    "rel_err_vs_exact": [float(v) for v in np.abs(e - exact) / np.abs(exact)]}
-    out["lattice_genz_s16_2p26"] = res
+        ms = statistics.median(tl)
+        gs = 4.0 * N / (ms * 1e-3) / 1e9
+        entry = {"ms": ms, "gsamples_s": gs, "tuned": {"chunk": tuned.chunk, "block": tuned.block},
+                 "rel_err_vs_exact": [float(v) for v in np.abs(e - exact) / np.abs(exact)],
+                 "roofline": issue_roofline(gs * 1e9, f"integrate_main<lattice16,{fam}>", sm_mhz)}
+        if pts is not None:
+            est_u = torch.empty(4, dtype=torch.float64, device=dev)
+
+            def unfused():
+                B.qmc_lattice_points(gd, shd, s, 0, N, 0, None, pts)
+                B.qmc_integrate_points(prob, 4, cd, pts, 1, thd, est_u, ws)
+
+            tu = timed(unfused, max(2, steps // 2), 2, stream)
+            entry["unfused_ms"] = statistics.median(tu)
+            entry["unfused_gsamples_s"] = 4.0 * N / (entry["unfused_ms"] * 1e-3) / 1e9
+            entry["unfused_equals_fused"] = bool(torch.equal(est_u, est))
+        res[fam] = entry
+    return res
+
+
+def run_extras(args, dev, sm_mhz):
+    which = [args.only] if args.only else ["fwd_bwd", "batched", "lattice"]
+    fns = {"fwd_bwd": bench_fwd_bwd, "batched": bench_batched, "lattice": bench_lattice}
+    out = {}
+    for name in which:
+        steps = 3 if args.small else 5
+        out[name] = fns[name](dev, steps, 3, args.small, sm_mhz)
+        import torch
+
+        torch.cuda.empty_cache()
     return out
 
 
@@ -322,6 +418,9 @@ def run_ours(args, world, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.only:  # one integration workload alone (profiling); no headline line
+        print(json.dumps({"only": args.only, "small": args.small, **run_extras(args, dev, None)}), flush=True)
+        return
     if world > 1:
         import torch.distributed as dist
 
@@ -349,7 +448,6 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     ev[0].record(stream)
-    per = []
     for k in range(args.steps):
         step()
         ev[k + 1].record(stream)
@@ -397,9 +495,9 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": "Gdims/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "materialised scrambled Sobol: s=32 dims, 2^24 indices per GPU, nested scramble, "
-                               "u32+fp32 outputs [2^24][32] each", "s": S_DIMS, "points_per_gpu": count,
-                   "scramble": "nested", "outputs": "u32+f32",
+        "config": {"workload": f"materialised scrambled Sobol: s={S_DIMS} dims, {count} indices per GPU, nested "
+                               f"scramble, u32+fp32 outputs [{count}][{S_DIMS}] each", "s": S_DIMS,
+                   "points_per_gpu": count, "scramble": "nested", "outputs": "u32+f32",
                    "l2": "outputs (4 GiB per step) exceed the 129 MB L2; no flush needed"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": profile_traffic("sobol_points_fast<1,2>"),
@@ -413,7 +511,7 @@ def run_ours(args, world, rank, local):
     del out_u, out_f, h_u, h_f
     torch.cuda.empty_cache()
     if not args.no_extra:
-        line["fused"] = bench_extra(dev, 5, 3)
+        line["fused"] = run_extras(args, dev, clk.get("sm_mhz"))
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

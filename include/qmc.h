@@ -233,6 +233,49 @@ QMC_API qmc_status qmc_integrate_points(const qmc_problem* p, uint32_t n_integra
                                 double* d_estimate, void* d_workspace, size_t workspace_bytes,
                                 qmc_stream_t stream);
 
+/*
+ * Autotuner of the work split (Sec. 2.5: the batch is cut into work items of
+ * `chunk` samples, each processed by one warp of a CTA of `block` threads).
+ * Times every (chunk, block) in {1024, 2048, 4096, 8192} x {128, 256} on the
+ * given problem and inputs (one warm-up and three timed runs each, CUDA events
+ * on `stream`; synchronises), returns the fastest and records it for the
+ * problem class (device, source, integrand, s, randomisation, per-integral
+ * seeds, forward or forward+backward, ceil(log2 n_integrals)); later calls of
+ * that class with p->chunk == 0 / p->block == 0 use the recorded values.
+ * With d_grad_theta NULL it tunes qmc_integrate, otherwise qmc_integrate_fwd_bwd
+ * (d_target and d_loss then required).  The workspace must be sized with
+ * p->chunk == 0 (covering every candidate).  Outputs are overwritten.
+ */
+typedef struct qmc_tuning {
+    uint32_t chunk;
+    uint32_t block;
+    float ms; /* median time of the chosen split */
+} qmc_tuning;
+
+QMC_API qmc_status qmc_tune_integrate(const qmc_problem* p, uint32_t n_integrals, const uint32_t* d_counts,
+                                      const float* d_theta, const double* d_target, double* d_estimate,
+                                      float* d_grad_theta, double* d_loss, void* d_workspace,
+                                      size_t workspace_bytes, qmc_stream_t stream, qmc_tuning* h_best);
+
+/* Forget every recorded tuning result (later calls use the defaults). */
+QMC_API qmc_status qmc_tune_clear(void);
+
+/*
+ * CUDA-graph capture of qmc_* calls (Sec. 2.5: many integrals in one launch
+ * sequence replayed without host work).  qmc_graph_begin starts a thread-local
+ * capture of `stream` (not the legacy NULL stream); every qmc_* call enqueued
+ * on it until qmc_graph_end is recorded with its arguments (pointers, sizes and
+ * the problem's values at capture time) and instantiated into a graph that
+ * qmc_graph_launch replays on any stream.  The captured buffers must stay alive
+ * and in place while the graph exists.  qmc_graph_destroy frees the graph.
+ */
+typedef struct qmc_graph_st* qmc_graph_t;
+
+QMC_API qmc_status qmc_graph_begin(qmc_stream_t stream);
+QMC_API qmc_status qmc_graph_end(qmc_stream_t stream, qmc_graph_t* out_graph);
+QMC_API qmc_status qmc_graph_launch(qmc_graph_t graph, qmc_stream_t stream);
+QMC_API qmc_status qmc_graph_destroy(qmc_graph_t graph);
+
 /* Size of the device array qmc_integrate_static works in (16 MiB per GPU that
  * loads the library, held until the process exits). */
 #define QMC_STATIC_WORKSPACE_BYTES (16u << 20)

@@ -34,7 +34,8 @@ F_BILINEAR2D, F_GENZ_PRODUCT_PEAK, F_GENZ_OSCILLATORY, F_GAUSSMIX4_6D = 0, 1, 2,
 EXPORTED = ["qmc_abi_version", "qmc_status_string", "qmc_sobol_matrices", "qmc_sobol_points",
             "qmc_lattice_points", "qmc_integrate_workspace_bytes", "qmc_integrate",
             "qmc_integrate_backward", "qmc_integrate_fwd_bwd", "qmc_integrate_points",
-            "qmc_read_device_error", "qmc_integrate_static"]
+            "qmc_read_device_error", "qmc_integrate_static", "qmc_tune_integrate", "qmc_tune_clear",
+            "qmc_graph_begin", "qmc_graph_end", "qmc_graph_launch", "qmc_graph_destroy"]
 
 
 class QMCError(RuntimeError):
@@ -42,6 +43,10 @@ class QMCError(RuntimeError):
         self.status = status
         msg = _lib.qmc_status_string(status).decode()
         super().__init__(f"{where}: {msg}")
+
+
+class qmc_tuning(ctypes.Structure):
+    _fields_ = [("chunk", c_uint32), ("block", c_uint32), ("ms", ctypes.c_float)]
 
 
 class qmc_problem(ctypes.Structure):
@@ -68,6 +73,13 @@ _sigs = {
                                             _P, c_size_t, _P]),
     "qmc_read_device_error": (ctypes.c_int, [_P, ctypes.POINTER(c_uint32), _P]),
     "qmc_integrate_static": (ctypes.c_int, [ctypes.POINTER(qmc_problem), c_uint32, _P, _P, _P, _P]),
+    "qmc_tune_integrate": (ctypes.c_int, [ctypes.POINTER(qmc_problem), c_uint32, _P, _P, _P, _P, _P, _P, _P,
+                                          c_size_t, _P, ctypes.POINTER(qmc_tuning)]),
+    "qmc_tune_clear": (ctypes.c_int, []),
+    "qmc_graph_begin": (ctypes.c_int, [_P]),
+    "qmc_graph_end": (ctypes.c_int, [_P, ctypes.POINTER(c_void_p)]),
+    "qmc_graph_launch": (ctypes.c_int, [c_void_p, _P]),
+    "qmc_graph_destroy": (ctypes.c_int, [c_void_p]),
 }
 for _name, (_res, _args) in _sigs.items():
     _fn = getattr(_lib, _name)
@@ -179,6 +191,38 @@ def qmc_integrate_static(problem, n_integrals, counts, theta, estimate, stream=N
     overlap)."""
     _check(_lib.qmc_integrate_static(ctypes.byref(problem), n_integrals, _dev(counts), _dev(theta),
                                      _dev(estimate), _stream(stream)), "qmc_integrate_static")
+
+
+def qmc_tune_integrate(problem, n_integrals, counts, theta, estimate, workspace, target=None, grad_theta=None,
+                       loss=None, workspace_bytes=None, stream=None) -> qmc_tuning:
+    wb = workspace.numel() * workspace.element_size() if workspace_bytes is None else workspace_bytes
+    best = qmc_tuning()
+    _check(_lib.qmc_tune_integrate(ctypes.byref(problem), n_integrals, _dev(counts), _dev(theta), _dev(target),
+                                   _dev(estimate), _dev(grad_theta), _dev(loss), _dev(workspace), wb,
+                                   _stream(stream), ctypes.byref(best)), "qmc_tune_integrate")
+    return best
+
+
+def qmc_tune_clear() -> None:
+    _check(_lib.qmc_tune_clear(), "qmc_tune_clear")
+
+
+def qmc_graph_begin(stream=None) -> None:
+    _check(_lib.qmc_graph_begin(_stream(stream)), "qmc_graph_begin")
+
+
+def qmc_graph_end(stream=None) -> int:
+    g = c_void_p()
+    _check(_lib.qmc_graph_end(_stream(stream), ctypes.byref(g)), "qmc_graph_end")
+    return g.value
+
+
+def qmc_graph_launch(graph: int, stream=None) -> None:
+    _check(_lib.qmc_graph_launch(graph, _stream(stream)), "qmc_graph_launch")
+
+
+def qmc_graph_destroy(graph: int) -> None:
+    _check(_lib.qmc_graph_destroy(graph), "qmc_graph_destroy")
 
 
 def qmc_read_device_error(workspace, stream=None) -> int:

@@ -51,7 +51,7 @@ WsLayout workspace_layout(uint32_t n, uint64_t capacity_items, uint32_t values_p
   L.block_rows = off;
   off += up(nb * 8);
   L.loss_terms = off;
-  off += up((size_t)n * 8);
+  off += up(((size_t)n + 256) * 8);  // per-integral terms, then the loss kernel's block sums
   L.partials = off;
   off += up((size_t)capacity_items * values_per_item * 2 * sizeof(float));
   L.total = off;
@@ -255,7 +255,6 @@ uint32_t values_per_item(const qmc_problem* p, bool grad) {
   return grad ? 17u : 1u;
 }
 
-uint32_t chunk_for(const qmc_problem* p) { return p->chunk ? p->chunk : kDefaultChunk; }
 
 struct Prepared {
   IntegrateArgs a;
@@ -286,7 +285,16 @@ qmc_status prepare(const qmc_problem* p, uint32_t n, const uint32_t* d_counts, c
   a.g = p->d_g;
   a.seeds = p->d_seeds;
   a.seeds_per_integral = p->seeds_per_integral;
-  a.chunk_log2 = ilog2(chunk_for(p));
+  // work split: explicit values, else the tuner's record for this problem class, else defaults
+  uint32_t chunk = p->chunk, block = p->block;
+  if (chunk == 0 || block == 0) {
+    uint32_t tc = 0, tb = 0;
+    if (tuned_lookup(p, n, grad, &tc, &tb)) {
+      if (chunk == 0) chunk = tc;
+      if (block == 0) block = tb;
+    }
+  }
+  a.chunk_log2 = ilog2(chunk ? chunk : kDefaultChunk);
   a.n = n;
   a.counts = d_counts;
   a.theta = d_theta;
@@ -302,7 +310,7 @@ qmc_status prepare(const qmc_problem* p, uint32_t n, const uint32_t* d_counts, c
   a.partials = reinterpret_cast<float*>(base + L.partials);
   a.capacity_items = capacity;
   (void)L.row_off;
-  out.block = p->block ? p->block : kDefaultBlock;
+  out.block = block ? block : kDefaultBlock;
   return QMC_OK;
 }
 

@@ -156,7 +156,9 @@ __global__ void __launch_bounds__(kScanThreads) scan_write(IntegrateArgs a) {
 
 // ---------------------------------------------------------------------------
 // Point sources.  Each produces the S coordinates of local sample il of the
-// current item (sample index start + il) as fp32 in [0,1).
+// current item (sample index start + il) in the scaled form X = x * 2^32 of
+// unifloat_x2p32 (exact: x = map_u32_to_unifloat(u) = X * 2^-32); the
+// integrands fold the 2^-32 into their constants.
 // ---------------------------------------------------------------------------
 template <int S, int SCR>  // SCR: 0 none, 1 XOR, 2 nested
 struct SobolSource {
@@ -224,7 +226,7 @@ struct SobolSource {
     for (int j = 0; j < S; ++j) {
       uint32_t y = row[j] ^ yl[j];
       if (SCR == 2) y = __brev(nested_mix(y, key[j]));
-      x[j] = map_u32_to_unifloat(y);
+      x[j] = unifloat_x2p32(y);
     }
   }
 };
@@ -255,7 +257,7 @@ struct LatticeSource {
     const uint32_t k = start + il;
     const uint32_t phi = __brev(BACKWARD ? ~k : k);
 #pragma unroll
-    for (int j = 0; j < S; ++j) x[j] = map_u32_to_unifloat(phi * g[j] + sh[j]);
+    for (int j = 0; j < S; ++j) x[j] = unifloat_x2p32(phi * g[j] + sh[j]);
   }
 };
 
@@ -277,7 +279,8 @@ struct PointsSource {
   __device__ __forceinline__ void point(uint32_t, uint32_t il, bool valid, float* x) const {
     const float* r = rows + (size_t)il * s;
 #pragma unroll
-    for (int j = 0; j < S; ++j) x[j] = (valid && (uint32_t)j < s) ? __ldcs(r + j) : 0.5f;
+    for (int j = 0; j < S; ++j)
+      x[j] = (valid && (uint32_t)j < s) ? __fmul_rn(__ldcs(r + j), 0x1p32f) : 0x1p31f;  // exact scale
   }
 };
 
@@ -311,7 +314,7 @@ struct Integrand<QMC_F_BILINEAR2D> {
   template <bool EXACT>
   __device__ __forceinline__ float eval(const float* x, float& err) const {
     err = 0.0f;
-    return __fmaf_rn(0.5f, x[0], 0.75f) * __fmaf_rn(0.5f, x[1], 0.75f);
+    return __fmaf_rn(0x1p-33f, x[0], 0.75f) * __fmaf_rn(0x1p-33f, x[1], 0.75f);  // 0.75 + x/2
   }
 };
 
@@ -340,7 +343,7 @@ struct Integrand<QMC_F_GENZ_PRODUCT_PEAK> {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       if ((uint32_t)j < s) {
-        const float d = __fsub_rn(x[j], u[j]);
+        const float d = __fmaf_rn(x[j], 0x1p-32f, -u[j]);  // x - u, one rounding
         prod = __fmul_rn(prod, __fadd_rn(__fmaf_rn(d, d, ch[j]), cl[j]));
       }
     }
@@ -359,7 +362,7 @@ struct Integrand<QMC_F_GENZ_OSCILLATORY> {
   __device__ void setup(const float* th, uint32_t s_) {
     s = s_;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) a[j] = (uint32_t)j < s ? __ldg(th + j) : 0.0f;
+    for (int j = 0; j < 16; ++j) a[j] = (uint32_t)j < s ? __ldg(th + j) * 0x1p-32f : 0.0f;  // a_j x_j = (a_j 2^-32) X_j
     sincospif(2.0f * __ldg(th + s), &s0, &c0);
   }
   // cos(2 pi u_1 + B) = cos(2 pi u_1) cos B - sin(2 pi u_1) sin B, B = sum_j a_j x_j
@@ -415,15 +418,21 @@ struct Integrand<QMC_F_GAUSSMIX4_6D> {
     }
   }
 
-  // 2^(-q k) for component c; q_out receives q (its leading word when EXACT).
-  template <bool EXACT>
-  __device__ __forceinline__ float gauss(const float* x, int c, float& q_out, float& t_abs) const {
+  // 2^(-q k) for component c of the scaled point X (x = X 2^-32); q_out receives q
+  // (its leading word when EXACT); with SUMS, se / so receive the sums of the
+  // differences over the even / odd dimensions (gradient).
+  template <bool EXACT, bool SUMS>
+  __device__ __forceinline__ float gauss(const float* X, int c, float& q_out, float& t_abs, float& se,
+                                         float& so) const {
     if constexpr (!EXACT) {
       float q = 0.0f;
 #pragma unroll
       for (int d = 0; d < 6; ++d) {
-        const float diff = __fsub_rn(x[d], (d & 1) ? nu[c] : mu[c]);
+        const float diff = __fmaf_rn(X[d], 0x1p-32f, (d & 1) ? -nu[c] : -mu[c]);  // x - m, one rounding
         q = __fmaf_rn(diff, diff, q);
+        if constexpr (SUMS) {
+          if (d & 1) so = __fadd_rn(so, diff); else se = __fadd_rn(se, diff);
+        }
       }
       const float t = __fmaf_rn(q, kh[c], __fmul_rn(q, kl[c]));
       q_out = q;
@@ -434,7 +443,12 @@ struct Integrand<QMC_F_GAUSSMIX4_6D> {
 #pragma unroll
       for (int d = 0; d < 6; ++d) {
         const float m = (d & 1) ? nu[c] : mu[c];
-        const float hi = fmaxf(x[d], m), lo = fminf(x[d], m);
+        const float xd = __fmul_rn(X[d], 0x1p-32f);  // exact
+        if constexpr (SUMS) {
+          const float diff = __fsub_rn(xd, m);
+          if (d & 1) so = __fadd_rn(so, diff); else se = __fadd_rn(se, diff);
+        }
+        const float hi = fmaxf(xd, m), lo = fminf(xd, m);
         const float D = __fsub_rn(hi, lo);                        // |x - m| rounded
         const float e = __fsub_rn(-lo, __fsub_rn(D, hi));         // exact remainder (Fast2Sum)
         const float p = __fmul_rn(D, D);
@@ -457,8 +471,8 @@ struct Integrand<QMC_F_GAUSSMIX4_6D> {
     err = 0.0f;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      float q, t;
-      const float wG = __fmul_rn(w[c], gauss<EXACT>(x, c, q, t));
+      float q, t, se, so;
+      const float wG = __fmul_rn(w[c], gauss<EXACT, false>(x, c, q, t, se, so));
       f = __fadd_rn(f, wG);
       err = __fmaf_rn(fabsf(wG), t, err);
     }
@@ -472,14 +486,8 @@ struct Integrand<QMC_F_GAUSSMIX4_6D> {
     err = 0.0f;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      float se = 0.0f, so = 0.0f;
-#pragma unroll
-      for (int d = 0; d < 6; ++d) {
-        const float diff = __fsub_rn(x[d], (d & 1) ? nu[c] : mu[c]);
-        if (d & 1) so = __fadd_rn(so, diff); else se = __fadd_rn(se, diff);
-      }
-      float q, t;
-      const float G = gauss<EXACT>(x, c, q, t);
+      float q, t, se = 0.0f, so = 0.0f;
+      const float G = gauss<EXACT, true>(x, c, q, t, se, so);
       const float wG = __fmul_rn(w[c], G);
       const float wg2 = __fmul_rn(wG, is2[c]);
       f = __fadd_rn(f, wG);
@@ -530,33 +538,47 @@ constexpr float kKappa = 8.0f * 5.9604645e-8f * kLn2;
 
 // One pass over the samples of the current item.  Returns nothing; adds into
 // acc and, on the fp32 pass, the squared per-sample error scales into e2.
+// Samples are summed in blocks of kBlock consecutive iterations with plain fp32
+// adds, and each block sum enters the lane's Kahan sum (a two-level reduction,
+// Sec. 2.5.1): the block adds carry at most (kBlock-1) unit roundoffs of the
+// block's absolute sum, the compensated sum carries almost nothing.
+constexpr uint32_t kBlock = 4;
+
 template <bool EXACT, bool GRAD, int NV, class Src, class F>
 __device__ __forceinline__ void run_item(const Src& src, const F& f, uint32_t len, Kahan (&acc)[NV],
                                          float& e2) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t R = (len + 31u) >> 5;
-  for (uint32_t r = 0; r < R; ++r) {
-    const uint32_t il = (r << 5) + lane;
-    const bool valid = il < len;
-    float x[F::S];
-    src.point(r, il, valid, x);
-    float err;
-    if constexpr (GRAD) {
-      float g[16];
-      const float v = f.template eval_grad<EXACT>(x, g, err);
-      if (valid) {
-        acc[0].add(v);
+  for (uint32_t r0 = 0; r0 < R; r0 += kBlock) {
+    float blk[NV];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) acc[1 + k].add(g[k]);
-        if constexpr (F::kAdaptive && !EXACT) e2 = __fmaf_rn(err, err, e2);
-      }
-    } else {
-      const float v = f.template eval<EXACT>(x, err);
-      if (valid) {
-        acc[0].add(v);
-        if constexpr (F::kAdaptive && !EXACT) e2 = __fmaf_rn(err, err, e2);
+    for (int v = 0; v < NV; ++v) blk[v] = 0.0f;
+    const uint32_t r1 = min(R, r0 + kBlock);
+    for (uint32_t r = r0; r < r1; ++r) {
+      const uint32_t il = (r << 5) + lane;
+      const bool valid = il < len;
+      float x[F::S];
+      src.point(r, il, valid, x);
+      float err;
+      if constexpr (GRAD) {
+        float g[16];
+        const float v = f.template eval_grad<EXACT>(x, g, err);
+        if (valid) {
+          blk[0] = __fadd_rn(blk[0], v);
+#pragma unroll
+          for (int k = 0; k < 16; ++k) blk[1 + k] = __fadd_rn(blk[1 + k], g[k]);
+          if constexpr (F::kAdaptive && !EXACT) e2 = __fmaf_rn(err, err, e2);
+        }
+      } else {
+        const float v = f.template eval<EXACT>(x, err);
+        if (valid) {
+          blk[0] = __fadd_rn(blk[0], v);
+          if constexpr (F::kAdaptive && !EXACT) e2 = __fmaf_rn(err, err, e2);
+        }
       }
     }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v].add(blk[v]);
   }
 }
 
@@ -619,14 +641,16 @@ __global__ void __launch_bounds__(256) integrate_main(IntegrateArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// 5-6: fp64 reductions, one warp per integral, partials in item order.
+// 5-6: per-integral reductions.  The compensated partials of an integral are
+// merged in item order with error-free fp32 transformations (TwoSum), which
+// keep the sum exact to ~2^-48; fp64 -- slow on GB300 -- is used only for the
+// final combination of that float pair and the division by n_p.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void neumaier64(double& s, double& c, double v) {
-  const double t = s + v;
-  c += (fabs(s) >= fabs(v)) ? (s - t) + v : (v - t) + s;
-  s = t;
-}
+__device__ __forceinline__ Comp comp_load(const float* q) { return {q[0], q[1]}; }
 
+__device__ __forceinline__ double comp_to_double(Comp c) { return (double)c.sum + (double)c.err; }
+
+// One warp per integral: lane l merges items l, l+32, ..., then a fixed butterfly.
 __global__ void __launch_bounds__(256) reduce_forward(IntegrateArgs a) {
   const uint64_t p = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t lane = threadIdx.x & 31u;
@@ -636,27 +660,19 @@ __global__ void __launch_bounds__(256) reduce_forward(IntegrateArgs a) {
     return;
   }
   const uint32_t b = a.item_off[p], e = a.item_off[p + 1];
-  double s = 0.0, c = 0.0;
-  for (uint32_t it = b + lane; it < e; it += 32) {
-    neumaier64(s, c, (double)a.partials[2 * (size_t)it]);
-    neumaier64(s, c, (double)a.partials[2 * (size_t)it + 1]);
-  }
-  // fixed-order tree over lanes (lane 0 ends with the sum of all)
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double os = __shfl_down_sync(0xffffffffu, s, o);
-    const double oc = __shfl_down_sync(0xffffffffu, c, o);
-    neumaier64(s, c, os);
-    c += oc;
-  }
+  Comp acc{0.0f, 0.0f};
+  for (uint32_t it = b + lane; it < e; it += 32) acc = comp_merge(acc, comp_load(a.partials + 2 * (size_t)it));
+  acc = warp_comp_sum(acc);
   if (lane == 0) {
     const uint32_t n_p = a.counts[p];
-    a.estimate[p] = n_p ? (s + c) / (double)n_p : 0.0;
+    a.estimate[p] = n_p ? comp_to_double(acc) / (double)n_p : 0.0;
   }
 }
 
-// GRAD partials: 17 values per item (f, 16 derivatives).  Lane v < 17 adds
-// value v over the integral's items in item order.
+// GRAD partials: 17 values per item (f, 16 derivatives).  Lane v < 17 merges
+// value v over the integral's items in item order.  The estimate I_p and the
+// loss term are fp64; the Jacobian J = sum/n_p and the gradient product are fp32
+// (relative error ~2e-7, far inside the gradient tolerance).
 __global__ void __launch_bounds__(256) reduce_grad(IntegrateArgs a) {
   const uint64_t p = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t lane = threadIdx.x & 31u;
@@ -671,55 +687,60 @@ __global__ void __launch_bounds__(256) reduce_grad(IntegrateArgs a) {
     return;
   }
   const uint32_t b = a.item_off[p], e = a.item_off[p + 1];
-  double s = 0.0, c = 0.0;
+  Comp acc{0.0f, 0.0f};
   if (lane < 17)
-    for (uint32_t it = b; it < e; ++it) {
-      const float* q = a.partials + (size_t)it * 34 + 2 * lane;
-      neumaier64(s, c, (double)q[0]);
-      neumaier64(s, c, (double)q[1]);
-    }
+    for (uint32_t it = b; it < e; ++it) acc = comp_merge(acc, comp_load(a.partials + (size_t)it * 34 + 2 * lane));
   const uint32_t n_p = a.counts[p];
-  const double mean = n_p ? (s + c) / (double)n_p : 0.0;  // lane 0: I_p; lane 1+k: J_pk
-  const double I = __shfl_sync(0xffffffffu, mean, 0);
-  double scale;
-  if (a.target) {  // fused squared-error loss
-    const double diff = I - a.target[p];
-    scale = 2.0 * diff;
-    if (lane == 0) {
+  float scale = 0.0f;
+  if (lane == 0) {
+    const double I = n_p ? comp_to_double(acc) / (double)n_p : 0.0;
+    if (a.target) {  // fused squared-error loss
+      const double diff = I - a.target[p];
       a.estimate[p] = I;
       a.ws_loss_terms[p] = diff * diff;
+      scale = (float)(2.0 * diff);
+    } else {
+      scale = (float)a.grad_est[p];
     }
-  } else {
-    scale = a.grad_est[p];
   }
-  if (lane >= 1 && lane < 17) a.grad_theta[p * 16 + (lane - 1)] = (float)(scale * mean);
+  scale = __shfl_sync(0xffffffffu, scale, 0);
+  if (lane >= 1 && lane < 17) {
+    const float J = n_p ? __fadd_rn(acc.sum, acc.err) * __frcp_rn((float)n_p) : 0.0f;
+    a.grad_theta[p * 16 + (lane - 1)] = scale * J;
+  }
 }
 
-__global__ void __launch_bounds__(1024) loss_reduce(IntegrateArgs a) {
-  __shared__ double sh_s[32], sh_c[32];
-  double s = 0.0, c = 0.0;
-  for (uint64_t p = threadIdx.x; p < a.n; p += blockDim.x) neumaier64(s, c, a.ws_loss_terms[p]);
+// Fixed-order sum of the loss terms: kLossBlocks blocks each add a contiguous
+// range (thread-strided, then a block tree), one block adds the block sums.
+constexpr uint32_t kLossBlocks = 256;
+
+__device__ __forceinline__ double block_sum_f64(double v, double* sh) {
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double os = __shfl_down_sync(0xffffffffu, s, o);
-    const double oc = __shfl_down_sync(0xffffffffu, c, o);
-    neumaier64(s, c, os);
-    c += oc;
-  }
-  if (lane == 0) {
-    sh_s[warp] = s;
-    sh_c[warp] = c;
-  }
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) sh[warp] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double S = 0.0, Cc = 0.0;
-    for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
-      neumaier64(S, Cc, sh_s[w]);
-      Cc += sh_c[w];
-    }
-    a.loss[0] = S + Cc;
-  }
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (uint32_t w = 0; w < blockDim.x / 32; ++w) t += sh[w];
+  return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(256) loss_partial(IntegrateArgs a) {
+  __shared__ double sh[8];
+  const uint64_t per = (a.n + kLossBlocks - 1) / kLossBlocks;
+  const uint64_t lo = blockIdx.x * per, hi = min((uint64_t)a.n, lo + per);
+  double s = 0.0;
+  for (uint64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) s += a.ws_loss_terms[p];
+  const double t = block_sum_f64(s, sh);
+  if (threadIdx.x == 0) a.ws_loss_terms[a.n + blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(256) loss_final(IntegrateArgs a) {
+  __shared__ double sh[8];
+  const double s = threadIdx.x < kLossBlocks ? a.ws_loss_terms[a.n + threadIdx.x] : 0.0;
+  const double t = block_sum_f64(s, sh);
+  if (threadIdx.x == 0) a.loss[0] = t;
 }
 
 // ---------------------------------------------------------------------------
@@ -787,7 +808,10 @@ cudaError_t launch_integrate(const IntegrateArgs& a, uint32_t block, bool grad, 
   const unsigned rblocks = (unsigned)((threads + 255) / 256);
   if (grad) {
     reduce_grad<<<rblocks, 256, 0, stream>>>(a);
-    if (a.target) loss_reduce<<<1, 1024, 0, stream>>>(a);
+    if (a.target) {
+      loss_partial<<<kLossBlocks, 256, 0, stream>>>(a);
+      loss_final<<<1, 256, 0, stream>>>(a);
+    }
   } else {
     reduce_forward<<<rblocks, 256, 0, stream>>>(a);
   }

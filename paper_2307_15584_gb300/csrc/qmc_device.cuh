@@ -20,6 +20,11 @@ __device__ __forceinline__ float map_u32_to_unifloat(uint32_t u) {
   return __uint2float_rz(u) * 0x1p-32f;
 }
 
+// The same value before the exact scale: map_u32_to_unifloat(u) == unifloat_x2p32(u) * 2^-32
+// bit for bit.  Fused integrands take this form and fold the power of two into
+// their own constants (x - m == fma(X, 2^-32, -m) with the same single rounding).
+__device__ __forceinline__ float unifloat_x2p32(uint32_t u) { return __uint2float_rz(u); }
+
 // Hash-based nested (Owen-type) scramble, applied in the mirrored digit domain
 // where the first digit 2^-1 sits in bit 0.  Each step changes bit b only as a
 // function of bits below b -- an add, a multiply by an odd number, an XOR

@@ -7,6 +7,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include "../../include/qmc.h"
+
 namespace qmc {
 
 struct DeviceInfo {
@@ -35,5 +37,8 @@ struct PointsArgs {
 
 cudaError_t launch_sobol_points(PointsArgs a, cudaStream_t stream);
 cudaError_t launch_lattice_points(PointsArgs a, cudaStream_t stream);
+
+// Work split recorded by qmc_tune_integrate for this problem class, if any.
+bool tuned_lookup(const qmc_problem* p, uint32_t n, bool grad, uint32_t* chunk, uint32_t* block);
 
 }  // namespace qmc

@@ -127,3 +127,19 @@ def test_integrate_validation(B):
     # n = 0 with valid arguments is a no-op
     assert L.qmc_integrate(ref(p), 0, FAKE, FAKE, FAKE, ws, 1 << 30, None) == 0
     assert L.qmc_read_device_error(None, ctypes.byref(ctypes.c_uint32()), None) == 1
+
+
+def test_runtime_validation(B):
+    L = B._lib
+    assert L.qmc_graph_begin(None) == 1  # the legacy default stream cannot be captured
+    assert L.qmc_graph_end(None, None) == 1
+    assert L.qmc_graph_launch(None, None) == 1
+    assert L.qmc_graph_destroy(None) == 1
+    assert L.qmc_tune_clear() == 0
+    best = B.qmc_tuning()
+    assert L.qmc_tune_integrate(None, 4, FAKE, FAKE, None, FAKE, None, None, FAKE, 1 << 20, None,
+                                ctypes.byref(best)) == 1
+    p = _problem(B)
+    # forward+backward tuning needs a target and a loss buffer
+    assert L.qmc_tune_integrate(ctypes.byref(p), 4, FAKE, FAKE, None, FAKE, FAKE, None, FAKE, 1 << 20, None,
+                                ctypes.byref(best)) == 1

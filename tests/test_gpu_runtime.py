@@ -1,0 +1,122 @@
+"""GPU tests of the runtime around the kernels: the torch.autograd Function over
+the hand-written adjoint, the work-split autotuner and CUDA-graph capture."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2307_15584_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2307_15584_gb300 import binding
+
+    return binding
+
+
+def _mixture(B, n, counts, seed):
+    C6 = B.qmc_sobol_matrices(6, inputs.sobol_raw_init(6))
+    theta = inputs.gaussmix_theta(n, seed=seed)
+    seeds = inputs.pixel_seeds(n, 6, seed=seed)
+    return C6, theta, seeds
+
+
+def test_autograd_backward_matches_fused_and_oracle(B, oracle):
+    """loss = sum (I(theta) - T)^2 through QMCIntegrate: backward recomputes the
+    points in the adjoint kernel; the gradient equals the fused forward+backward
+    and the oracle's analytic-on-points gradient."""
+    from paper_2307_15584_gb300.autograd import GaussMixIntegrator
+
+    n = 300
+    counts = inputs.log_uniform_counts(n, hi=8192, seed=51)
+    C6, theta, seeds = _mixture(B, n, counts, 51)
+    target = inputs.gaussmix_target(inputs.gaussmix_theta(n, seed=52))
+    integ = GaussMixIntegrator(C6, counts, seeds)
+    th = torch.from_numpy(theta).cuda().requires_grad_(True)
+    tg = torch.from_numpy(target).cuda()
+    est = integ(th)
+    loss = ((est - tg) ** 2).sum()
+    loss.backward()
+    g_auto = th.grad.cpu().numpy()
+
+    est_f = torch.empty(n, dtype=torch.float64, device="cuda")
+    g_f = torch.empty((n, 16), dtype=torch.float32, device="cuda")
+    loss_f = torch.empty(1, dtype=torch.float64, device="cuda")
+    B.qmc_integrate_fwd_bwd(integ.problem, n, integ.counts, th.detach(), tg, est_f, g_f, loss_f, integ.workspace)
+    np.testing.assert_array_equal(est.detach().cpu().numpy(), est_f.cpu().numpy())
+    np.testing.assert_allclose(g_auto, g_f.cpu().numpy(), rtol=1e-6, atol=0)
+    assert loss.item() == pytest.approx(loss_f.item(), rel=1e-12)
+
+    ref = oracle.integrate(oracle.SOURCE_SOBOL, oracle.F_GAUSSMIX4_6D, 6, counts, theta, C=C6,
+                           scramble=oracle.SCRAMBLE_NESTED, seeds=seeds, with_grad=True)
+    W = np.abs(theta[:, 0::4]).sum(axis=1)
+    tol_i = 1e-6 * np.abs(ref["est"]) + 1e-12 * W
+    r = ref["est"] - target
+    g_ref = 2 * r[:, None] * ref["grad"]
+    g_tol = 2 * (tol_i[:, None] * np.abs(ref["grad"]) + 1e-5 * np.abs(r)[:, None] *
+                 (np.abs(ref["grad"]) + ref["grad_mass"])) + 1e-12 * W[:, None]
+    assert (np.abs(g_auto - g_ref) <= g_tol).all()
+
+
+def test_autotuner_records_and_applies(B, oracle):
+    n = 2000
+    counts = inputs.log_uniform_counts(n, seed=61)
+    C6, theta, seeds = _mixture(B, n, counts, 61)
+    d = {"C": B.u32_tensor(C6), "c": B.u32_tensor(counts), "th": torch.from_numpy(theta).cuda(),
+         "sd": B.u32_tensor(seeds)}
+    prob = B.make_problem(B.SOURCE_SOBOL, B.F_GAUSSMIX4_6D, 6, B.SCRAMBLE_NESTED, matrices=d["C"], seeds=d["sd"],
+                          seeds_per_integral=True)
+    ws = B.alloc_workspace(prob, n, counts)  # chunk 0: sized for every candidate
+    est = torch.empty(n, dtype=torch.float64, device="cuda")
+    B.qmc_tune_clear()
+    best = B.qmc_tune_integrate(prob, n, d["c"], d["th"], est, ws)
+    assert best.chunk in (1024, 2048, 4096, 8192) and best.block in (128, 256) and best.ms > 0
+    # a call with chunk = block = 0 now uses the recorded split: bitwise equal to the explicit one
+    e_auto = torch.empty(n, dtype=torch.float64, device="cuda")
+    B.qmc_integrate(prob, n, d["c"], d["th"], e_auto, ws)
+    explicit = B.make_problem(B.SOURCE_SOBOL, B.F_GAUSSMIX4_6D, 6, B.SCRAMBLE_NESTED, matrices=d["C"],
+                              seeds=d["sd"], seeds_per_integral=True, chunk=best.chunk, block=best.block)
+    e_exp = torch.empty(n, dtype=torch.float64, device="cuda")
+    B.qmc_integrate(explicit, n, d["c"], d["th"], e_exp, ws)
+    np.testing.assert_array_equal(e_auto.cpu().numpy(), e_exp.cpu().numpy())
+    ref = oracle.integrate(oracle.SOURCE_SOBOL, oracle.F_GAUSSMIX4_6D, 6, counts, theta, C=C6,
+                           scramble=oracle.SCRAMBLE_NESTED, seeds=seeds)
+    W = np.abs(theta[:, 0::4]).sum(axis=1)
+    assert (np.abs(e_auto.cpu().numpy() - ref["est"]) <= 1e-6 * np.abs(ref["est"]) + 1e-12 * W).all()
+    B.qmc_tune_clear()
+
+
+def test_graph_capture_replays_the_batch(B):
+    """The whole batched integration (scan kernels, persistent kernel, reduction)
+    recorded once and replayed: replays equal direct calls, also after the
+    parameters change in place."""
+    n = 1500
+    counts = inputs.log_uniform_counts(n, seed=71)
+    C6, theta, seeds = _mixture(B, n, counts, 71)
+    d = {"C": B.u32_tensor(C6), "c": B.u32_tensor(counts), "th": torch.from_numpy(theta).cuda(),
+         "sd": B.u32_tensor(seeds)}
+    prob = B.make_problem(B.SOURCE_SOBOL, B.F_GAUSSMIX4_6D, 6, B.SCRAMBLE_NESTED, matrices=d["C"], seeds=d["sd"],
+                          seeds_per_integral=True)
+    ws = B.alloc_workspace(prob, n, counts)
+    est_direct = torch.empty(n, dtype=torch.float64, device="cuda")
+    est_graph = torch.empty(n, dtype=torch.float64, device="cuda")
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        B.qmc_graph_begin(side)
+        B.qmc_integrate(prob, n, d["c"], d["th"], est_graph, ws, stream=side)
+        graph = B.qmc_graph_end(side)
+    try:
+        for k in range(2):
+            if k:
+                d["th"].mul_(0.9)
+            B.qmc_integrate(prob, n, d["c"], d["th"], est_direct, ws)
+            torch.cuda.synchronize()
+            with torch.cuda.stream(side):
+                B.qmc_graph_launch(graph, side)
+            side.synchronize()
+            np.testing.assert_array_equal(est_graph.cpu().numpy(), est_direct.cpu().numpy())
+    finally:
+        B.qmc_graph_destroy(graph)
