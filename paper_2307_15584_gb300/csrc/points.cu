@@ -45,6 +45,36 @@ __device__ __forceinline__ void store1(uint32_t* out_u32, float* out_f32, uint64
   if (out_f32) out_f32[off] = map_u32_to_unifloat(v);
 }
 
+// --- TMA bulk stores (cp.async.bulk): shared memory -> global, asynchronous ---
+__device__ __forceinline__ void fence_smem_to_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+               "r"((uint32_t)__cvta_generic_to_shared(ssrc)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// at most one bulk group may still be reading its shared-memory source
+__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// every bulk group of this thread has completed its global writes
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Build-time choices of the Sobol' store path: TMA bulk stores from staged
+// shared-memory tiles (1) or direct 128-bit stores (0), and the groups per
+// staged tile (per warp, double-buffered).  Measured on GB300 at s = 32, 2^24
+// points, u32 + f32: direct stores 0.714 ms; TMA with 1 / 2 / 4 / 8 groups per
+// tile 0.726 / 0.728 / 0.653 / 0.866 ms (4 groups: 2 KiB bulk stores, 2 CTAs per
+// SM; 8 groups: 1 CTA per SM).
+#ifndef QMC_POINTS_TMA
+#define QMC_POINTS_TMA 1
+#endif
+#ifndef QMC_POINTS_STAGE_GROUPS
+#define QMC_POINTS_STAGE_GROUPS 4
+#endif
+constexpr bool kPointsTma = QMC_POINTS_TMA != 0;
+constexpr uint32_t kStageGroups = QMC_POINTS_STAGE_GROUPS;
+
 // This warp's contiguous share [g0, g1) of n_groups groups.
 __device__ __forceinline__ void warp_range(uint64_t n_groups, uint64_t& g0, uint64_t& g1) {
   const uint64_t w = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -57,13 +87,18 @@ __device__ __forceinline__ void warp_range(uint64_t n_groups, uint64_t& g0, uint
 // K1 fast path.  MODE: 0 none, 1 XOR, 2 nested.  K: 16-byte chunks per lane.
 // Shared memory: cols[s][32] (mirrored for nested), hin[2^u][s].
 // ---------------------------------------------------------------------------
-template <int K, int MODE, bool V4>  // V4: s % 4 == 0, chunks hold 4 consecutive dimensions
+// TMA: full groups are staged per warp in shared memory (two tiles of
+// kStageGroups groups, u32 and f32 halves) and written by lane 0 with one bulk
+// store per output; the warp refills a tile once the copy engine has read it.
+template <int K, int MODE, bool V4, bool TMA>  // V4: s % 4 == 0, chunks hold 4 consecutive dimensions
 __global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
-  extern __shared__ __align__(16) uint32_t smem[];
+  extern __shared__ __align__(128) uint32_t smem[];
   const uint32_t s = a.s;
-  uint32_t* cols = smem;
-  uint32_t* hin = smem + s * 32;
   const uint32_t nin = 1u << a.u_log2;
+  constexpr uint32_t kTileWords = kStageGroups * 128u * K;  // one output of one tile
+  uint32_t* stage = smem;  // [warps][2 tiles][2 outputs][kTileWords]
+  uint32_t* cols = smem + (TMA ? (kThreads / 32) * 4 * kTileWords : 0);
+  uint32_t* hin = cols + s * 32;
 
   for (uint32_t idx = threadIdx.x; idx < s * 32; idx += blockDim.x) {
     const uint32_t c = __ldg(a.matrices + idx);
@@ -107,6 +142,25 @@ __global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
   const uint64_t step = (uint64_t)Q * s;  // elements per group
   uint64_t off = g0 * step + 4u * lane;   // this lane's first element in group g0
 
+  uint32_t* my_stage = stage + (threadIdx.x >> 5) * 4 * kTileWords;
+  uint32_t tile = 0, staged = 0;
+  uint64_t tile_off = 0;  // global element offset of the tile's first group
+  auto flush = [&]() {   // send the staged groups of the current tile (warp-uniform call)
+    fence_smem_to_async();
+    __syncwarp();
+    if (lane == 0) {
+      const uint32_t bytes = staged * 128u * K * 4u;
+      const uint32_t* t = my_stage + tile * 2 * kTileWords;
+      if (a.out_u32) bulk_store(a.out_u32 + tile_off, t, bytes);
+      if (a.out_f32) bulk_store(a.out_f32 + tile_off, t + kTileWords, bytes);
+      bulk_commit();
+      bulk_wait_read_1();  // the other tile's previous copy has read its source
+    }
+    __syncwarp();
+    tile ^= 1u;
+    staged = 0;
+  };
+
   for (uint64_t g = g0; g < g1; ++g, off += step) {
     const uint32_t G = G_first + (uint32_t)g;
     const uint32_t G_in = G & (nin - 1u);
@@ -140,7 +194,15 @@ __global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
       }
       const uint64_t o = off + 128u * c;
       if (g < full_groups) {
-        store4(a.out_u32, a.out_f32, o, v);
+        if (TMA) {
+          uint32_t* t = my_stage + tile * 2 * kTileWords + staged * 128u * K + 4u * (lane + 32u * c);
+          *reinterpret_cast<uint4*>(t) = make_uint4(v[0], v[1], v[2], v[3]);
+          *reinterpret_cast<float4*>(t + kTileWords) =
+              make_float4(map_u32_to_unifloat(v[0]), map_u32_to_unifloat(v[1]), map_u32_to_unifloat(v[2]),
+                          map_u32_to_unifloat(v[3]));
+        } else {
+          store4(a.out_u32, a.out_f32, o, v);
+        }
       } else {  // ragged last group: per-element row test
         const uint64_t rows_left = a.count - (g << a.q_log2);
         const uint32_t e0 = 4u * (lane + 32u * c);
@@ -149,7 +211,12 @@ __global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
           if ((uint64_t)((e0 + t) / s) < rows_left) store1(a.out_u32, a.out_f32, o + t, v[t]);
       }
     }
+    if (TMA && g < full_groups) {
+      if (staged == 0) tile_off = off - 4u * lane;
+      if (++staged == kStageGroups || g + 1 == g1 || g + 1 == full_groups) flush();
+    }
   }
+  if (TMA && lane == 0) bulk_wait_all();  // writes complete before the kernel ends
 }
 
 // K1 generic path: one element per thread, columns read through the cache.
@@ -301,13 +368,14 @@ cudaError_t launch_sobol_points(PointsArgs a, cudaStream_t stream) {
   uint32_t u = 0;
   while (u < 8 && (2u << u) * a.s * 4u <= 16384u) ++u;
   a.u_log2 = u;
-  const size_t smem = ((size_t)a.s * 32 + ((size_t)1 << u) * a.s) * sizeof(uint32_t);
+  const size_t stage_words = kPointsTma ? (size_t)(kThreads / 32) * 4 * kStageGroups * 128u * K : 0;
+  const size_t smem = (stage_words + (size_t)a.s * 32 + ((size_t)1 << u) * a.s) * sizeof(uint32_t);
   const uint64_t groups = (a.count + (1u << a.q_log2) - 1) >> a.q_log2;
   const bool v4 = (a.s & 3u) == 0;
 #define QMC_SOBOL_MODES(KK, V)                                                                        \
-  if (a.scramble == 0) return launch_persistent(sobol_points_fast<KK, 0, V>, groups, smem, stream, a); \
-  if (a.scramble == 1) return launch_persistent(sobol_points_fast<KK, 1, V>, groups, smem, stream, a); \
-  return launch_persistent(sobol_points_fast<KK, 2, V>, groups, smem, stream, a);
+  if (a.scramble == 0) return launch_persistent(sobol_points_fast<KK, 0, V, kPointsTma>, groups, smem, stream, a); \
+  if (a.scramble == 1) return launch_persistent(sobol_points_fast<KK, 1, V, kPointsTma>, groups, smem, stream, a); \
+  return launch_persistent(sobol_points_fast<KK, 2, V, kPointsTma>, groups, smem, stream, a);
 #define QMC_SOBOL_CASE(KK)      \
   case KK:                      \
     if (v4) {                   \
