@@ -338,6 +338,18 @@ cudaError_t launch_persistent(KernelT kernel, uint64_t warps_needed, size_t smem
   return cudaGetLastError();
 }
 
+// True for device (or managed) memory and for null; false for host memory the
+// GPU reaches through the interconnect (pinned or registered host buffers).
+bool device_resident(const void* p) {
+  if (!p) return true;
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
 template <typename KernelT>
 cudaError_t launch_grid_stride(KernelT kernel, uint64_t elements, cudaStream_t stream,
                                const PointsArgs& a) {
@@ -368,20 +380,27 @@ cudaError_t launch_sobol_points(PointsArgs a, cudaStream_t stream) {
   uint32_t u = 0;
   while (u < 8 && (2u << u) * a.s * 4u <= 16384u) ++u;
   a.u_log2 = u;
-  const size_t stage_words = kPointsTma ? (size_t)(kThreads / 32) * 4 * kStageGroups * 128u * K : 0;
+  // TMA bulk stores target device memory; outputs in host memory that the GPU
+  // writes directly (pinned, mapped) take the 128-bit store path.
+  const bool tma = kPointsTma && device_resident(a.out_u32) && device_resident(a.out_f32);
+  const size_t stage_words = tma ? (size_t)(kThreads / 32) * 4 * kStageGroups * 128u * K : 0;
   const size_t smem = (stage_words + (size_t)a.s * 32 + ((size_t)1 << u) * a.s) * sizeof(uint32_t);
   const uint64_t groups = (a.count + (1u << a.q_log2) - 1) >> a.q_log2;
   const bool v4 = (a.s & 3u) == 0;
-#define QMC_SOBOL_MODES(KK, V)                                                                        \
-  if (a.scramble == 0) return launch_persistent(sobol_points_fast<KK, 0, V, kPointsTma>, groups, smem, stream, a); \
-  if (a.scramble == 1) return launch_persistent(sobol_points_fast<KK, 1, V, kPointsTma>, groups, smem, stream, a); \
-  return launch_persistent(sobol_points_fast<KK, 2, V, kPointsTma>, groups, smem, stream, a);
-#define QMC_SOBOL_CASE(KK)      \
-  case KK:                      \
-    if (v4) {                   \
-      QMC_SOBOL_MODES(KK, true)  \
-    } else {                    \
-      QMC_SOBOL_MODES(KK, false) \
+#define QMC_SOBOL_MODES(KK, V, T)                                                                       \
+  if (a.scramble == 0) return launch_persistent(sobol_points_fast<KK, 0, V, T>, groups, smem, stream, a); \
+  if (a.scramble == 1) return launch_persistent(sobol_points_fast<KK, 1, V, T>, groups, smem, stream, a); \
+  return launch_persistent(sobol_points_fast<KK, 2, V, T>, groups, smem, stream, a);
+#define QMC_SOBOL_CASE(KK)                \
+  case KK:                                \
+    if (v4 && tma) {                      \
+      QMC_SOBOL_MODES(KK, true, kPointsTma)  \
+    } else if (v4) {                      \
+      QMC_SOBOL_MODES(KK, true, false)    \
+    } else if (tma) {                     \
+      QMC_SOBOL_MODES(KK, false, kPointsTma) \
+    } else {                              \
+      QMC_SOBOL_MODES(KK, false, false)   \
     }
   switch (K) {
     QMC_SOBOL_CASE(1)

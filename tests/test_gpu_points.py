@@ -150,3 +150,21 @@ def test_map_exhaustive_all_2pow32(B, oracle):
         np.testing.assert_array_equal(ff.view(np.uint32), oracle.map_u32_to_unifloat(uu).view(np.uint32))
         top = max(top, float(ff.max()))
     assert top == float(np.float32(1.0) - np.float32(2.0**-24))
+
+
+def test_outputs_in_pinned_host_memory(B, oracle):
+    """Outputs may live in pinned host memory that the GPU writes directly (the
+    launcher then uses the direct-store path): same bits as device outputs."""
+    s, n = 32, (1 << 16) + 12
+    C = B.qmc_sobol_matrices(s, inputs.sobol_raw_init(s))
+    seeds = inputs.scramble_seeds(s)
+    Cd, sd = B.u32_tensor(C), B.u32_tensor(seeds)
+    hu = torch.empty((n, s), dtype=torch.int32).pin_memory()
+    hf = torch.empty((n, s), dtype=torch.float32).pin_memory()
+    B.qmc_sobol_points(Cd, s, 0, n, 2, sd, hu.data_ptr(), hf.data_ptr())
+    torch.cuda.synchronize()
+    du, df = B.sobol_points(Cd, n, scramble=2, seeds=sd)
+    np.testing.assert_array_equal(hu.numpy(), du.cpu().numpy())
+    np.testing.assert_array_equal(hf.numpy().view(np.uint32), _f32_bits(df))
+    ou, _ = oracle.sobol_points(C, n - 100, 100, 2, seeds)
+    np.testing.assert_array_equal(hu.numpy().view(np.uint32)[-100:], ou)
