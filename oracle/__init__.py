@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qmc_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-SOURCE_SOBOL, SOURCE_LATTICE = 0, 1
+SOURCE_SOBOL, SOURCE_LATTICE, SOURCE_PIXEL_LATTICE = 0, 1, 2
 SCRAMBLE_NONE, SCRAMBLE_XOR, SCRAMBLE_NESTED = 0, 1, 2
 F_BILINEAR2D, F_GENZ_PRODUCT_PEAK, F_GENZ_OSCILLATORY, F_GAUSSMIX4_6D = 0, 1, 2, 3
 
@@ -61,6 +61,9 @@ def lib() -> ctypes.CDLL:
             "qo_sobol_points": (None, [P, u32, u64, u64, u32, P, P, P]),
             "qo_lattice_u32": (u32, [u32, u32, u32, u32]),
             "qo_lattice_points": (None, [P, P, u32, u64, u64, u32, P, P]),
+            "qo_hilbert_index": (u32, [u32, u32, u32]),
+            "qo_pixel_shift": (u32, [u32, u32, u32]),
+            "qo_pixel_lattice_u32": (u32, [u32, u32, u32]),
             "qo_integrate_one": (i32, [u32, u32, u32, u32, P, P, P, u32, P, P, P, P, P]),
             "qo_integrand": (dbl, [u32, u32, P, P, P]),
             "qo_gaussmix_f64": (dbl, [P, P]),
@@ -234,3 +237,41 @@ def exact_gaussmix(theta, with_grad=False):
     grad = np.zeros(16)
     v = lib().qo_exact_gaussmix(_p(th), _p(grad) if with_grad else None)
     return (v, grad) if with_grad else v
+
+
+def hilbert_index(x: int, y: int, k: int) -> int:
+    return lib().qo_hilbert_index(x, y, k)
+
+
+def pixel_shift(px: int, py: int, k: int) -> int:
+    return lib().qo_pixel_shift(px, py, k)
+
+
+def grid_log2(width: int, height: int) -> int:
+    """Order k of the smallest 2^k x 2^k grid that covers the image."""
+    k = 0
+    while (1 << k) < max(width, height):
+        k += 1
+    return k
+
+
+def pixel_lattice_points(g, width, n_pixels, spp, pixel_begin=0, height=None):
+    """u32 [n_pixels * spp][s]: samples 0..spp-1 of pixels pixel_begin.. (row-major image)."""
+    g = np.ascontiguousarray(g, dtype=np.uint32)
+    height = height or -(-(pixel_begin + n_pixels) // width)
+    k = grid_log2(width, height)
+    out = np.empty((n_pixels * spp, g.size), np.uint32)
+    for q in range(n_pixels):
+        p = pixel_begin + q
+        sh = pixel_shift(p % width, p // width, k)
+        for i in range(spp):
+            for j in range(g.size):
+                out[q * spp + i, j] = lib().qo_pixel_lattice_u32(i, int(g[j]), sh)
+    return out
+
+
+def pixel_shifts(width, n, height=None):
+    """Per-integral shift words of an image of n pixels (row-major), for integrate(source=2)."""
+    height = height or -(-n // width)
+    k = grid_log2(width, height)
+    return np.array([[pixel_shift(p % width, p // width, k)] for p in range(n)], np.uint32)

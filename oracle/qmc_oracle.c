@@ -34,7 +34,7 @@
 
 #define QO_EXPORT __attribute__((visibility("default")))
 
-enum { QO_SOURCE_SOBOL = 0, QO_SOURCE_LATTICE = 1 };
+enum { QO_SOURCE_SOBOL = 0, QO_SOURCE_LATTICE = 1, QO_SOURCE_PIXEL_LATTICE = 2 };
 enum { QO_SCRAMBLE_NONE = 0, QO_SCRAMBLE_XOR = 1, QO_SCRAMBLE_NESTED = 2 };
 enum {
     QO_F_BILINEAR2D = 0,
@@ -251,6 +251,49 @@ QO_EXPORT void qo_lattice_points(const uint32_t* g, const uint32_t* shift, uint3
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sec. 3, Eq. (PixelShiftedR1LS): the pixel-shifted rank-1 lattice.         */
+/* ------------------------------------------------------------------------ */
+
+/* Position of pixel (x, y) along the Hilbert curve filling the 2^k x 2^k grid
+ * (the inverse of the curve's index -> position map).  The curve starts at the
+ * origin, visits the quadrants in the order (0,0), (0,1), (1,1), (1,0) of
+ * (x-bit, y-bit), and each quadrant holds a copy of the curve turned so that
+ * consecutive positions stay neighbours: the lower-left copy is mirrored in
+ * the diagonal, the lower-right one in the anti-diagonal. */
+QO_EXPORT uint32_t qo_hilbert_index(uint32_t x, uint32_t y, uint32_t k)
+{
+    uint32_t d = 0;
+    for (int level = (int)k - 1; level >= 0; --level) {
+        uint32_t rx = (x >> level) & 1u, ry = (y >> level) & 1u;
+        uint32_t quad = rx ? (ry ? 2u : 3u) : (ry ? 1u : 0u);
+        d = d * 4u + quad;
+        uint32_t mask = (1u << level) - 1u;  /* the coordinates inside the quadrant */
+        uint32_t lx = x & mask, ly = y & mask;
+        if (!ry) {
+            if (rx) { lx = mask - lx; ly = mask - ly; }  /* anti-diagonal mirror */
+            uint32_t t = lx; lx = ly; ly = t;          /* diagonal mirror */
+        }
+        x = lx;
+        y = ly;
+    }
+    return d;
+}
+
+/* One shift per pixel: floor(phi_3(h) 2^32) of its Hilbert index h. */
+QO_EXPORT uint32_t qo_pixel_shift(uint32_t px, uint32_t py, uint32_t k)
+{
+    return qo_radical_inverse_u32(3, qo_hilbert_index(px, py, k));
+}
+
+/* Component j of sample i of the pixel with shift `shift` (units of 2^-32):
+ * (phi_2(i) + phi_3(h)) g_j mod 1, with g_j forced odd. */
+QO_EXPORT uint32_t qo_pixel_lattice_u32(uint32_t i, uint32_t g, uint32_t shift)
+{
+    uint64_t base = ((uint64_t)qo_bit_reverse(i) + shift) & 0xFFFFFFFFull;
+    return (uint32_t)((base * (uint64_t)(g | 1u)) & 0xFFFFFFFFull);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sec. 2.6: test integrands with analytic integrals, in fp64.               */
 /* Parameters are fp32 values promoted exactly to double.                    */
 /* ------------------------------------------------------------------------ */
@@ -331,7 +374,9 @@ static void neu_add(neumaier* a, double v)
  *   source 0 (Sobol'): x_i = Sobol' point i of C[s][32] randomised by
  *     `scramble` with seeds[s];
  *   source 1 (lattice): x_i = lattice point i of g[s] shifted by seeds[s]
- *     (the Cranley-Patterson rotation), backward when scramble & 1.
+ *     (the Cranley-Patterson rotation), backward when scramble & 1;
+ *   source 2 (pixel-shifted lattice, Eq. (PixelShiftedR1LS)): seeds[0] holds
+ *     the pixel's shift floor(phi_3(h) 2^32) from qo_pixel_shift.
  * Coordinates are the fp32 values of the float mapping, promoted to fp64.
  * Outputs (each may be NULL except est): est = estimate; mass = (1/n) sum |f|;
  * grad[16] = (1/n) sum df/dtheta and grad_mass[16] = (1/n) sum |df/dtheta|
@@ -345,7 +390,7 @@ QO_EXPORT int qo_integrate_one(uint32_t source, uint32_t integrand, uint32_t s,
     if (s == 0 || s > 32) return -1;
     if (integrand == QO_F_BILINEAR2D && s != 2) return -1;
     if (integrand == QO_F_GAUSSMIX4_6D && s != 6) return -1;
-    if (integrand > QO_F_GAUSSMIX4_6D || source > QO_SOURCE_LATTICE) return -1;
+    if (integrand > QO_F_GAUSSMIX4_6D || source > QO_SOURCE_PIXEL_LATTICE) return -1;
 
     neumaier sum = {0, 0}, abs_sum = {0, 0};
     neumaier gsum[16], gabs[16];
@@ -357,8 +402,10 @@ QO_EXPORT int qo_integrate_one(uint32_t source, uint32_t integrand, uint32_t s,
             uint32_t v;
             if (source == QO_SOURCE_SOBOL)
                 v = randomise_sobol(qo_sobol_u32(C + 32 * j, i), scramble, seeds ? seeds[j] : 0u);
-            else
+            else if (source == QO_SOURCE_LATTICE)
                 v = qo_lattice_u32(i, g[j], seeds ? seeds[j] : 0u, scramble & 1u);
+            else  /* pixel-shifted lattice: seeds[0] is the pixel's shift (qo_pixel_shift) */
+                v = qo_pixel_lattice_u32(i, g[j], seeds ? seeds[0] : 0u);
             x[j] = (double)qo_map_u32_to_unifloat(v);
         }
         double f;
