@@ -61,8 +61,15 @@ typedef enum qmc_scramble {
 #define QMC_LATTICE_BACKWARD 1u /* enumerate phi_2(2^32-1-k) as Alg. 4 does: the origin comes last */
 
 typedef enum qmc_source {
-    QMC_SOURCE_SOBOL = 0,   /* digital (t,s)-sequence in base 2, Eq. (ts) */
-    QMC_SOURCE_LATTICE = 1  /* rank-1 lattice sequence in base 2, Eq. (R1LS) */
+    QMC_SOURCE_SOBOL = 0,         /* digital (t,s)-sequence in base 2, Eq. (ts) */
+    QMC_SOURCE_LATTICE = 1,       /* rank-1 lattice sequence in base 2, Eq. (R1LS) */
+    QMC_SOURCE_PIXEL_LATTICE = 2  /* pixel-shifted rank-1 lattice, Eq. (PixelShiftedR1LS):
+                                     integral p is pixel (x, y) = (p % image_width, p / image_width);
+                                     sample i = (phi_2(i) + phi_3(h)) g mod 1 with h the pixel's
+                                     position along the Hilbert curve of the smallest 2^k x 2^k
+                                     grid covering the image (computed in integers: floor(phi_3
+                                     2^32) is added to phi_2(i) 2^32 mod 2^32, then multiplied
+                                     by g mod 2^32) */
 } qmc_source;
 
 /* Integrands with closed-form integrals (Sec. 2.6 recommends such test
@@ -91,7 +98,8 @@ typedef struct qmc_problem {
     uint32_t s;                  /* dimension of the points = of the integrand */
     uint32_t randomize;          /* SOBOL: qmc_scramble; LATTICE: 0 or QMC_LATTICE_BACKWARD */
     const uint32_t* d_matrices;  /* SOBOL: [s][32] generator columns (see qmc_sobol_points) */
-    const uint32_t* d_g;         /* LATTICE: [s] generator words, low bit forced to 1 */
+    const uint32_t* d_g;         /* LATTICE, PIXEL_LATTICE: [s] generator words, low bit forced
+                                    to 1 (PIXEL_LATTICE takes no seeds and no randomize flags) */
     const uint32_t* d_seeds;     /* SOBOL: scramble seeds; LATTICE: Cranley-Patterson shifts
                                     (units of 2^-32).  [s], or [n_integrals][s] when
                                     seeds_per_integral = 1.  NULL: no randomisation/shift. */
@@ -103,6 +111,8 @@ typedef struct qmc_problem {
                                     host does not pass counts to qmc_integrate_workspace_bytes */
     uint32_t with_gradient;      /* 1: size the workspace for qmc_integrate_backward and
                                     qmc_integrate_fwd_bwd (17 partial sums per work item) */
+    uint32_t image_width;        /* PIXEL_LATTICE: pixels per image row (>= 1); the image has
+                                    ceil(n_integrals / image_width) rows.  Ignored otherwise. */
 } qmc_problem;
 
 /* ABI revision of this header (bumped on any incompatible change). */
@@ -157,8 +167,26 @@ QMC_API qmc_status qmc_sobol_points(const uint32_t* d_matrices, uint32_t s, uint
  * Other arguments, layouts and errors as for qmc_sobol_points.
  */
 QMC_API qmc_status qmc_lattice_points(const uint32_t* d_g, const uint32_t* d_shift, uint32_t s,
-                              uint64_t index_begin, uint64_t count, uint32_t flags,
-                              uint32_t* d_out_u32, float* d_out_f32, qmc_stream_t stream);
+                                      uint64_t index_begin, uint64_t count, uint32_t flags,
+                                      uint32_t* d_out_u32, float* d_out_f32, qmc_stream_t stream);
+
+/*
+ * Materialised pixel-shifted rank-1 lattice samples (Sec. 3, Eq.
+ * (PixelShiftedR1LS)): for pixels pixel_begin .. pixel_begin+n_pixels-1 of a
+ * row-major image_width x image_height image, samples 0 .. spp-1 of each pixel,
+ *   x_j(i) = (phi_2(i) + phi_3(h)) g_j mod 1,
+ * h = the pixel's position along the Hilbert curve of the smallest 2^k x 2^k
+ * grid covering the image, in integers as for QMC_SOURCE_PIXEL_LATTICE.
+ *   d_g        [s] generator words (low bit forced to 1), 1 <= s <= 1024
+ *   outputs    [n_pixels * spp][s]: row q*spp + i is sample i of pixel pixel_begin+q;
+ *              4-byte aligned; u32 (units of 2^-32) and/or f32 (map_u32_to_unifloat)
+ * Errors: QMC_ERR_INVALID_ARG (null g, zero sizes, no output), QMC_ERR_RANGE
+ * (pixels beyond the image), QMC_ERR_ALIGN.  n_pixels = 0 is a no-op.
+ */
+QMC_API qmc_status qmc_pixel_lattice_points(const uint32_t* d_g, uint32_t s, uint32_t image_width,
+                                            uint32_t image_height, uint64_t pixel_begin, uint64_t n_pixels,
+                                            uint32_t spp, uint32_t* d_out_u32, float* d_out_f32,
+                                            qmc_stream_t stream);
 
 /*
  * Bytes of workspace qmc_integrate / qmc_integrate_backward /

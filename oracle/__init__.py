@@ -185,7 +185,7 @@ def integrate(source, integrand, s, counts, theta, *, C=None, g=None, scramble=0
         seeds = np.asarray(seeds, dtype=np.uint32)
         if seeds.ndim == 1:  # one seed vector shared by every integral
             seeds = np.tile(seeds.reshape(1, s), (n, 1))
-        seeds = np.ascontiguousarray(seeds.reshape(n, s))
+        seeds = np.ascontiguousarray(seeds.reshape(n, -1))  # [n][s], or [n][1] pixel shifts
     est = np.zeros(n)
     mass = np.zeros(n)
     grad = np.zeros((n, 16)) if with_grad else None

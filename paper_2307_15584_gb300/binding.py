@@ -28,14 +28,15 @@ STATUS_NAMES = {0: "QMC_OK", 1: "QMC_ERR_INVALID_ARG", 2: "QMC_ERR_RANGE", 3: "Q
                 4: "QMC_ERR_CUDA", 5: "QMC_ERR_TIMEOUT", 6: "QMC_ERR_UNSUPPORTED", 7: "QMC_ERR_WORKSPACE"}
 SCRAMBLE_NONE, SCRAMBLE_XOR, SCRAMBLE_NESTED = 0, 1, 2
 LATTICE_BACKWARD = 1
-SOURCE_SOBOL, SOURCE_LATTICE = 0, 1
+SOURCE_SOBOL, SOURCE_LATTICE, SOURCE_PIXEL_LATTICE = 0, 1, 2
 F_BILINEAR2D, F_GENZ_PRODUCT_PEAK, F_GENZ_OSCILLATORY, F_GAUSSMIX4_6D = 0, 1, 2, 3
 
 EXPORTED = ["qmc_abi_version", "qmc_status_string", "qmc_sobol_matrices", "qmc_sobol_points",
             "qmc_lattice_points", "qmc_integrate_workspace_bytes", "qmc_integrate",
             "qmc_integrate_backward", "qmc_integrate_fwd_bwd", "qmc_integrate_points",
             "qmc_read_device_error", "qmc_integrate_static", "qmc_tune_integrate", "qmc_tune_clear",
-            "qmc_graph_begin", "qmc_graph_end", "qmc_graph_launch", "qmc_graph_destroy"]
+            "qmc_graph_begin", "qmc_graph_end", "qmc_graph_launch", "qmc_graph_destroy",
+            "qmc_pixel_lattice_points"]
 
 
 class QMCError(RuntimeError):
@@ -53,7 +54,7 @@ class qmc_problem(ctypes.Structure):
     _fields_ = [("source", c_uint32), ("integrand", c_uint32), ("s", c_uint32), ("randomize", c_uint32),
                 ("d_matrices", c_void_p), ("d_g", c_void_p), ("d_seeds", c_void_p),
                 ("seeds_per_integral", c_uint32), ("chunk", c_uint32), ("block", c_uint32),
-                ("max_count", c_uint32), ("with_gradient", c_uint32)]
+                ("max_count", c_uint32), ("with_gradient", c_uint32), ("image_width", c_uint32)]
 
 
 _P = c_void_p
@@ -63,6 +64,8 @@ _sigs = {
     "qmc_sobol_matrices": (ctypes.c_int, [c_uint32, _P, _P]),
     "qmc_sobol_points": (ctypes.c_int, [_P, c_uint32, c_uint64, c_uint64, c_uint32, _P, _P, _P, _P]),
     "qmc_lattice_points": (ctypes.c_int, [_P, _P, c_uint32, c_uint64, c_uint64, c_uint32, _P, _P, _P]),
+    "qmc_pixel_lattice_points": (ctypes.c_int, [_P, c_uint32, c_uint32, c_uint32, c_uint64, c_uint64, c_uint32,
+                                                _P, _P, _P]),
     "qmc_integrate_workspace_bytes": (c_size_t, [ctypes.POINTER(qmc_problem), c_uint32, _P]),
     "qmc_integrate": (ctypes.c_int, [ctypes.POINTER(qmc_problem), c_uint32, _P, _P, _P, _P, c_size_t, _P]),
     "qmc_integrate_backward": (ctypes.c_int, [ctypes.POINTER(qmc_problem), c_uint32, _P, _P, _P, _P, _P,
@@ -141,6 +144,12 @@ def qmc_sobol_matrices(s: int, raw_init) -> np.ndarray:
 def qmc_sobol_points(matrices, s, index_begin, count, scramble, seeds, out_u32, out_f32, stream=None):
     _check(_lib.qmc_sobol_points(_dev(matrices), s, index_begin, count, scramble, _dev(seeds), _dev(out_u32),
                                  _dev(out_f32), _stream(stream)), "qmc_sobol_points")
+
+
+def qmc_pixel_lattice_points(g, s, image_width, image_height, pixel_begin, n_pixels, spp, out_u32, out_f32,
+                             stream=None):
+    _check(_lib.qmc_pixel_lattice_points(_dev(g), s, image_width, image_height, pixel_begin, n_pixels, spp,
+                                         _dev(out_u32), _dev(out_f32), _stream(stream)), "qmc_pixel_lattice_points")
 
 
 def qmc_lattice_points(g, shift, s, index_begin, count, flags, out_u32, out_f32, stream=None):
@@ -234,11 +243,12 @@ def qmc_read_device_error(workspace, stream=None) -> int:
 
 # ----------------------------------------------------------------- conveniences
 def make_problem(source, integrand, s, randomize=0, matrices=None, g=None, seeds=None,
-                 seeds_per_integral=False, chunk=0, block=0, max_count=0, with_gradient=False) -> qmc_problem:
+                 seeds_per_integral=False, chunk=0, block=0, max_count=0, with_gradient=False,
+                 image_width=0) -> qmc_problem:
     """A qmc_problem holding device pointers of the given tensors; the problem keeps
     references to them so their memory stays valid while it is alive."""
     p = qmc_problem(source, integrand, s, randomize, _dev(matrices), _dev(g), _dev(seeds),
-                    int(bool(seeds_per_integral)), chunk, block, max_count, int(bool(with_gradient)))
+                    int(bool(seeds_per_integral)), chunk, block, max_count, int(bool(with_gradient)), image_width)
     p._tensors = (matrices, g, seeds)
     return p
 

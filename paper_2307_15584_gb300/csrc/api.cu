@@ -118,7 +118,7 @@ using namespace qmc;
 
 extern "C" {
 
-uint32_t qmc_abi_version(void) { return 1u; }
+uint32_t qmc_abi_version(void) { return 2u; }
 
 const char* qmc_status_string(qmc_status st) {
   switch (st) {
@@ -193,6 +193,33 @@ qmc_status qmc_sobol_points(const uint32_t* d_matrices, uint32_t s, uint64_t ind
   return launch_sobol_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 
+qmc_status qmc_pixel_lattice_points(const uint32_t* d_g, uint32_t s, uint32_t image_width,
+                                    uint32_t image_height, uint64_t pixel_begin, uint64_t n_pixels,
+                                    uint32_t spp, uint32_t* d_out_u32, float* d_out_f32,
+                                    qmc_stream_t stream) {
+  if (!d_g || s == 0 || s > 1024 || image_width == 0 || image_height == 0 || spp == 0)
+    return QMC_ERR_INVALID_ARG;
+  const uint64_t pixels = (uint64_t)image_width * image_height;
+  if (pixel_begin > pixels || n_pixels > pixels - pixel_begin) return QMC_ERR_RANGE;
+  if (n_pixels == 0) return QMC_OK;
+  if (!d_out_u32 && !d_out_f32) return QMC_ERR_INVALID_ARG;
+  if (((uintptr_t)d_out_u32 & 3u) || ((uintptr_t)d_out_f32 & 3u)) return QMC_ERR_ALIGN;
+  PixelPointsArgs a{};
+  a.g = d_g;
+  a.out_u32 = d_out_u32;
+  a.out_f32 = d_out_f32;
+  a.pixel_begin = pixel_begin;
+  a.n_pixels = n_pixels;
+  a.spp = spp;
+  a.s = s;
+  a.width = image_width;
+  uint32_t k = 0;
+  const uint32_t side = image_width > image_height ? image_width : image_height;
+  while (((uint64_t)1 << k) < side) ++k;
+  a.grid_log2 = k;
+  return launch_pixel_lattice_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
 qmc_status qmc_lattice_points(const uint32_t* d_g, const uint32_t* d_shift, uint32_t s,
                               uint64_t index_begin, uint64_t count, uint32_t flags,
                               uint32_t* d_out_u32, float* d_out_f32, qmc_stream_t stream) {
@@ -229,7 +256,7 @@ uint32_t ilog2(uint32_t v) {
 
 qmc_status validate_problem(const qmc_problem* p, bool need_source) {
   if (!p) return QMC_ERR_INVALID_ARG;
-  if (p->integrand > QMC_F_GAUSSMIX4_6D || p->source > QMC_SOURCE_LATTICE) return QMC_ERR_INVALID_ARG;
+  if (p->integrand > QMC_F_GAUSSMIX4_6D || p->source > QMC_SOURCE_PIXEL_LATTICE) return QMC_ERR_INVALID_ARG;
   const uint32_t s = p->s;
   if (p->integrand == QMC_F_BILINEAR2D && s != 2) return QMC_ERR_INVALID_ARG;
   if (p->integrand == QMC_F_GAUSSMIX4_6D && s != 6) return QMC_ERR_INVALID_ARG;
@@ -244,11 +271,23 @@ qmc_status validate_problem(const qmc_problem* p, bool need_source) {
     if (p->source == QMC_SOURCE_SOBOL) {
       if (!p->d_matrices || p->randomize > QMC_SCRAMBLE_NESTED) return QMC_ERR_INVALID_ARG;
       if (p->randomize != QMC_SCRAMBLE_NONE && !p->d_seeds) return QMC_ERR_INVALID_ARG;
-    } else {
+    } else if (p->source == QMC_SOURCE_LATTICE) {
       if (!p->d_g || (p->randomize & ~QMC_LATTICE_BACKWARD)) return QMC_ERR_INVALID_ARG;
+    } else {  // pixel-shifted lattice: generator words and an image width, nothing else
+      if (!p->d_g || p->randomize != 0 || p->image_width == 0) return QMC_ERR_INVALID_ARG;
     }
   }
   return QMC_OK;
+}
+
+// Order k of the smallest 2^k x 2^k Hilbert grid covering an image of n pixels,
+// image_width per row.
+uint32_t image_grid_log2(uint32_t n, uint32_t width) {
+  const uint64_t rows = width ? ((uint64_t)n + width - 1) / width : 0;
+  const uint64_t side = rows > width ? rows : width;
+  uint32_t k = 0;
+  while (((uint64_t)1 << k) < side) ++k;
+  return k;
 }
 
 uint32_t values_per_item(const qmc_problem* p, bool grad) {
@@ -285,6 +324,11 @@ qmc_status prepare(const qmc_problem* p, uint32_t n, const uint32_t* d_counts, c
   a.g = p->d_g;
   a.seeds = p->d_seeds;
   a.seeds_per_integral = p->seeds_per_integral;
+  if (p->source == QMC_SOURCE_PIXEL_LATTICE) {
+    a.seeds = nullptr;
+    a.image_width = p->image_width;
+    a.grid_log2 = image_grid_log2(n, p->image_width);
+  }
   // work split: explicit values, else the tuner's record for this problem class, else defaults
   uint32_t chunk = p->chunk, block = p->block;
   if (chunk == 0 || block == 0) {

@@ -261,6 +261,34 @@ struct LatticeSource {
   }
 };
 
+// Pixel-shifted rank-1 lattice (Sec. 3, Eq. (PixelShiftedR1LS)): integral p
+// is the pixel (p % width, p / width); its samples are
+// (phi_2(i) + phi_3(hilbert(x, y))) g mod 1, one shift per pixel.
+template <int S>
+struct PixelLatticeSource {
+  uint32_t start;
+  uint32_t shift;
+  uint32_t g[S];
+
+  static size_t smem_bytes(uint32_t, uint32_t) { return 0; }
+
+  __device__ void kernel_setup(const IntegrateArgs& a, uint32_t*) {
+#pragma unroll
+    for (int j = 0; j < S; ++j) g[j] = (uint32_t)j < a.s ? (__ldg(a.g + j) | 1u) : 1u;
+  }
+
+  __device__ void item_setup(const IntegrateArgs& a, uint32_t p, uint32_t st) {
+    start = st;
+    shift = pixel_shift(p % a.image_width, p / a.image_width, a.grid_log2);
+  }
+
+  __device__ __forceinline__ void point(uint32_t, uint32_t il, bool, float* x) const {
+    const uint32_t base = __brev(start + il) + shift;  // mod 2^32
+#pragma unroll
+    for (int j = 0; j < S; ++j) x[j] = unifloat_x2p32(base * g[j]);
+  }
+};
+
 // Unfused comparison path: coordinates read back from HBM.
 template <int S>
 struct PointsSource {
@@ -767,6 +795,7 @@ template <int FN, bool GRAD>
 cudaError_t launch_main_fn(const IntegrateArgs& a, uint32_t block, cudaStream_t stream) {
   constexpr int S = Integrand<FN>::S;
   if (a.points) return launch_main_t<PointsSource<S>, FN, GRAD>(a, block, stream);
+  if (a.source == QMC_SOURCE_PIXEL_LATTICE) return launch_main_t<PixelLatticeSource<S>, FN, GRAD>(a, block, stream);
   if (a.source == QMC_SOURCE_LATTICE)
     return (a.randomize & QMC_LATTICE_BACKWARD) ? launch_main_t<LatticeSource<S, true>, FN, GRAD>(a, block, stream)
                                                 : launch_main_t<LatticeSource<S, false>, FN, GRAD>(a, block, stream);

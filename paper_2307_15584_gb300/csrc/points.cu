@@ -304,6 +304,20 @@ __global__ void __launch_bounds__(kThreads) lattice_points_generic(PointsArgs a)
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+// Pixel-shifted rank-1 lattice (Sec. 3): one thread per (pixel, sample) row;
+// row r holds sample r % spp of pixel pixel_begin + r / spp.
+__global__ void __launch_bounds__(kThreads) pixel_lattice_points_kernel(PixelPointsArgs a) {
+  const uint64_t rows = a.n_pixels * a.spp;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride) {
+    const uint64_t p = a.pixel_begin + r / a.spp;
+    const uint32_t i = (uint32_t)(r % a.spp);
+    const uint32_t shift = pixel_shift((uint32_t)(p % a.width), (uint32_t)(p / a.width), a.grid_log2);
+    const uint32_t base = __brev(i) + shift;
+    for (uint32_t j = 0; j < a.s; ++j) store1(a.out_u32, a.out_f32, r * a.s + j, base * (__ldg(a.g + j) | 1u));
+  }
+}
+
 // Chunks per lane of the fast path, or 0 when the generic path must run.
 uint32_t fast_k(uint32_t s) {
   uint32_t g = 128;
@@ -411,6 +425,16 @@ cudaError_t launch_sobol_points(PointsArgs a, cudaStream_t stream) {
   }
 #undef QMC_SOBOL_CASE
 #undef QMC_SOBOL_MODES
+}
+
+cudaError_t launch_pixel_lattice_points(const PixelPointsArgs& a, cudaStream_t stream) {
+  const DeviceInfo& dev = device_info();
+  uint64_t blocks = (a.n_pixels * a.spp + kThreads - 1) / kThreads;
+  const uint64_t cap = (uint64_t)dev.sm_count * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  pixel_lattice_points_kernel<<<(unsigned)blocks, kThreads, 0, stream>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_lattice_points(PointsArgs a, cudaStream_t stream) {

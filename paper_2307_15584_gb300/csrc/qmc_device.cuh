@@ -51,6 +51,57 @@ __device__ __forceinline__ uint32_t nested_mix(uint32_t v, NestedKey k) {
 }
 
 // ---------------------------------------------------------------------------
+// Sec. 3, Eq. (PixelShiftedR1LS): one shift per pixel, phi_3 of the pixel's
+// position along the Hilbert curve, added to phi_2(i) before the generator
+// multiplication.
+// ---------------------------------------------------------------------------
+
+// Position of (x, y) along the Hilbert curve of the 2^k x 2^k grid (curve from
+// the origin through quadrants (0,0), (0,1), (1,1), (1,0) of (x-bit, y-bit)):
+// per level, the quadrant code, then the point is carried into the frame of
+// the quadrant's sub-curve (reflected through the centre for the lower-right
+// quadrant, transposed for both lower quadrants).
+__device__ __forceinline__ uint32_t hilbert_position(uint32_t x, uint32_t y, uint32_t k) {
+  const uint32_t n = 1u << k;
+  uint32_t d = 0;
+  for (uint32_t half = n >> 1; half > 0; half >>= 1) {
+    const uint32_t rx = (x & half) ? 1u : 0u, ry = (y & half) ? 1u : 0u;
+    d += half * half * ((3u * rx) ^ ry);
+    if (ry == 0) {
+      if (rx == 1) {
+        x = n - 1u - x;
+        y = n - 1u - y;
+      }
+      const uint32_t t = x;
+      x = y;
+      y = t;
+    }
+  }
+  return d;
+}
+
+// floor(phi_3(h) * 2^32): two base-3 digits per step through the base-9 digit
+// reversal of Alg. 2 ({0,3,6,1,4,7,2,5,8}, packed as nibbles), exact division.
+__device__ __forceinline__ uint32_t radinv3_u32(uint32_t h) {
+  constexpr uint64_t kPerm9 = 0x852741630ull;  // nibble d holds the reversal of digit pair d
+  uint64_t num = 0, den = 1;
+  while (h) {
+    num = num * 9u + ((kPerm9 >> (4u * (h % 9u))) & 15u);
+    den *= 9u;
+    h /= 9u;
+  }
+  // num < den <= 9^11 < 2^35, so num * 2^32 < 2^67 would overflow 64 bits:
+  // divide in two 16-bit steps (exact long division).
+  const uint64_t q1 = (num << 16) / den, r1 = (num << 16) % den;
+  const uint64_t q2 = (r1 << 16) / den;
+  return (uint32_t)((q1 << 16) | q2);
+}
+
+__device__ __forceinline__ uint32_t pixel_shift(uint32_t px, uint32_t py, uint32_t k) {
+  return radinv3_u32(hilbert_position(px, py, k));
+}
+
+// ---------------------------------------------------------------------------
 // Compensated fp32 summation (Sec. 2.5.1 names Kahan's algorithm; this is
 // the Neumaier variant, whose error term is exact for either operand order).
 // ---------------------------------------------------------------------------

@@ -25,6 +25,8 @@ struct IntegrateArgs {
   const uint32_t* seeds;
   uint32_t seeds_per_integral;
   uint32_t chunk_log2;
+  uint32_t image_width;  // pixel-shifted lattice: integral p is pixel (p % width, p / width)
+  uint32_t grid_log2;    // ... on the 2^grid_log2 square grid of the Hilbert curve
   uint32_t n;
   const uint32_t* counts;
   const float* theta;

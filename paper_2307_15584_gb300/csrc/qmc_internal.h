@@ -35,6 +35,16 @@ struct PointsArgs {
   uint32_t u_log2;           // set by the launcher
 };
 
+// Arguments of the pixel-shifted lattice points (Sec. 3).
+struct PixelPointsArgs {
+  const uint32_t* g;  // [s] generator words
+  uint32_t* out_u32;  // [n_pixels * spp][s] or null
+  float* out_f32;     // [n_pixels * spp][s] or null
+  uint64_t pixel_begin, n_pixels;
+  uint32_t spp, s, width, grid_log2;
+};
+
+cudaError_t launch_pixel_lattice_points(const PixelPointsArgs& a, cudaStream_t stream);
 cudaError_t launch_sobol_points(PointsArgs a, cudaStream_t stream);
 cudaError_t launch_lattice_points(PointsArgs a, cudaStream_t stream);
 

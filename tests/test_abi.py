@@ -35,7 +35,8 @@ def test_header_symbols_exported(B):
     for name in declared:
         assert hasattr(lib, name), name
     assert sorted(B.EXPORTED) == sorted(declared)
-    assert B.qmc_abi_version() == 1
+    assert B.qmc_abi_version() == 2
+    assert ctypes.sizeof(B.qmc_problem) == 64  # 4 + 3 pointers + 6 words, as in include/qmc.h
     assert "INVALID" in B.qmc_status_string(1)
 
 
