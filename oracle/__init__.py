@@ -62,6 +62,9 @@ def lib() -> ctypes.CDLL:
             "qo_lattice_u32": (u32, [u32, u32, u32, u32]),
             "qo_lattice_points": (None, [P, P, u32, u64, u64, u32, P, P]),
             "qo_hilbert_index": (u32, [u32, u32, u32]),
+            "qo_prime": (u32, [u32]),
+            "qo_faure": (u32, [u32, u32]),
+            "qo_halton_u32": (u32, [u32, u32, u32, u32]),
             "qo_pixel_shift": (u32, [u32, u32, u32]),
             "qo_pixel_lattice_u32": (u32, [u32, u32, u32]),
             "qo_integrate_one": (i32, [u32, u32, u32, u32, P, P, P, u32, P, P, P, P, P]),
@@ -275,3 +278,20 @@ def pixel_shifts(width, n, height=None):
     height = height or -(-n // width)
     k = grid_log2(width, height)
     return np.array([[pixel_shift(p % width, p // width, k)] for p in range(n)], np.uint32)
+
+
+HALTON_NONE, HALTON_FAURE, HALTON_LINEAR = 0, 1, 2
+
+
+def halton_points(s, begin, count, mode=HALTON_NONE, multipliers=None, threads=None):
+    """u32 [count][s]: Halton points begin.. (bases = the first s primes)."""
+    mult = np.zeros(s, np.uint32) if multipliers is None else np.asarray(multipliers, np.uint32)
+    out = np.empty((count, s), np.uint32)
+
+    def run(r0, n):
+        for r in range(r0, min(count, r0 + n)):
+            for j in range(s):
+                out[r, j] = lib().qo_halton_u32((begin + r) & 0xFFFFFFFF, j, mode, int(mult[j]))
+
+    _chunked(count, threads, run)
+    return out

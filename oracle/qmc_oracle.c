@@ -88,6 +88,67 @@ QO_EXPORT uint32_t qo_radical_inverse_u32(uint32_t b, uint64_t i)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sec. 2.2: radical inversion in prime bases, digit permutations, Halton.   */
+/* ------------------------------------------------------------------------ */
+
+/* The j-th prime (j = 0 gives 2), by trial division. */
+QO_EXPORT uint32_t qo_prime(uint32_t j)
+{
+    uint32_t count = 0;
+    for (uint32_t p = 2;; ++p) {
+        int is_prime = 1;
+        for (uint32_t q = 2; q * q <= p; ++q)
+            if (p % q == 0) { is_prime = 0; break; }
+        if (is_prime && count++ == j) return p;
+    }
+}
+
+/* Faure's permutation sigma_b(d), by its recursive definition (Sec. 2.2):
+ * sigma_2 = (0, 1); for even b, sigma_b = 2 sigma_{b/2} followed by
+ * 2 sigma_{b/2} + 1; for odd b, sigma_b is sigma_{b-1} with every value
+ * >= (b-1)/2 raised by one and (b-1)/2 inserted in the middle. */
+QO_EXPORT uint32_t qo_faure(uint32_t b, uint32_t d)
+{
+    if (b <= 2) return d;
+    if (b % 2 == 0) {
+        uint32_t h = b / 2;
+        return d < h ? 2 * qo_faure(h, d) : 2 * qo_faure(h, d - h) + 1;
+    }
+    uint32_t c = (b - 1) / 2;
+    if (d == c) return c;
+    uint32_t v = qo_faure(b - 1, d < c ? d : d - 1);
+    return v >= c ? v + 1 : v;
+}
+
+/* Component j of Halton point i (base b = the j-th prime), as
+ * floor(phi(i') 2^32) where the digits of i' are permuted digit by digit:
+ *   mode 0: identity; mode 1: Faure sigma_b; mode 2: linear d -> (m d) mod b
+ *   (Alg. 2, radinv_linscramble, multiplier m).
+ * i' = i for base 2 (bit reversal covers every 32-bit index), otherwise
+ * i mod b^K with b^K the largest power of b below 2^32 (Alg. 1's domain
+ * limit).  Digits are peeled off one at a time. */
+QO_EXPORT uint32_t qo_halton_u32(uint32_t i, uint32_t j, uint32_t mode, uint32_t m)
+{
+    uint32_t b = qo_prime(j);
+    uint64_t ii = i;
+    if (b != 2) {
+        uint64_t maxp = 1;
+        while (maxp * b <= 0xFFFFFFFFull) maxp *= b;
+        ii %= maxp;
+    }
+    unsigned __int128 num = 0, den = 1;
+    while (ii > 0) {
+        uint32_t dgt = (uint32_t)(ii % b);
+        if (mode == 1) dgt = qo_faure(b, dgt);
+        else if (mode == 2) dgt = (uint32_t)(((uint64_t)m * dgt) % b);
+        num = num * b + dgt;
+        den *= b;
+        ii /= b;
+    }
+    return (uint32_t)((num << 32) / den);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sec. 2.3, Eq. (ts): Sobol' generator matrices over GF(2).                 */
 /* ------------------------------------------------------------------------ */
 
