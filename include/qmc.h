@@ -170,6 +170,29 @@ QMC_API qmc_status qmc_lattice_points(const uint32_t* d_g, const uint32_t* d_shi
                                       uint64_t index_begin, uint64_t count, uint32_t flags,
                                       uint32_t* d_out_u32, float* d_out_f32, qmc_stream_t stream);
 
+/* Digit permutations of the Halton engine (Sec. 2.2). */
+typedef enum qmc_halton_mode {
+    QMC_HALTON_PLAIN = 0,  /* phi_b: the digits mirrored */
+    QMC_HALTON_FAURE = 1,  /* Faure's recursive permutation sigma_b of every digit */
+    QMC_HALTON_LINEAR = 2  /* linear digit scramble d -> (m_j d) mod b (Alg. 2, radinv_linscramble) */
+} qmc_halton_mode;
+
+/*
+ * Materialised Halton points (Sec. 2.2, Alg. 1, Alg. 2): component j of point
+ * i is the radical inverse of i in base b_j = the j-th prime (2, 3, 5, ...),
+ * digits permuted per `mode`, as floor(phi 2^32) (u32) and its float mapping.
+ * Base 2 uses the bit reversal of the full 32-bit index; other bases reduce the
+ * index modulo the largest power of b_j below 2^32 first (Alg. 1's domain
+ * limit), so point i and point i + b_j^K coincide in that dimension.
+ *   s              1 <= s <= 64
+ *   h_multipliers  HOST array [s] for QMC_HALTON_LINEAR: 1 <= m_j < b_j
+ *                  (ignored for base 2); NULL otherwise
+ * Other arguments, layouts and errors as for qmc_sobol_points.
+ */
+QMC_API qmc_status qmc_halton_points(uint32_t s, uint32_t mode, const uint32_t* h_multipliers,
+                                     uint64_t index_begin, uint64_t count, uint32_t* d_out_u32,
+                                     float* d_out_f32, qmc_stream_t stream);
+
 /*
  * Materialised pixel-shifted rank-1 lattice samples (Sec. 3, Eq.
  * (PixelShiftedR1LS)): for pixels pixel_begin .. pixel_begin+n_pixels-1 of a

@@ -36,7 +36,8 @@ EXPORTED = ["qmc_abi_version", "qmc_status_string", "qmc_sobol_matrices", "qmc_s
             "qmc_integrate_backward", "qmc_integrate_fwd_bwd", "qmc_integrate_points",
             "qmc_read_device_error", "qmc_integrate_static", "qmc_tune_integrate", "qmc_tune_clear",
             "qmc_graph_begin", "qmc_graph_end", "qmc_graph_launch", "qmc_graph_destroy",
-            "qmc_pixel_lattice_points"]
+            "qmc_pixel_lattice_points", "qmc_halton_points"]
+HALTON_PLAIN, HALTON_FAURE, HALTON_LINEAR = 0, 1, 2
 
 
 class QMCError(RuntimeError):
@@ -66,6 +67,7 @@ _sigs = {
     "qmc_lattice_points": (ctypes.c_int, [_P, _P, c_uint32, c_uint64, c_uint64, c_uint32, _P, _P, _P]),
     "qmc_pixel_lattice_points": (ctypes.c_int, [_P, c_uint32, c_uint32, c_uint32, c_uint64, c_uint64, c_uint32,
                                                 _P, _P, _P]),
+    "qmc_halton_points": (ctypes.c_int, [c_uint32, c_uint32, _P, c_uint64, c_uint64, _P, _P, _P]),
     "qmc_integrate_workspace_bytes": (c_size_t, [ctypes.POINTER(qmc_problem), c_uint32, _P]),
     "qmc_integrate": (ctypes.c_int, [ctypes.POINTER(qmc_problem), c_uint32, _P, _P, _P, _P, c_size_t, _P]),
     "qmc_integrate_backward": (ctypes.c_int, [ctypes.POINTER(qmc_problem), c_uint32, _P, _P, _P, _P, _P,
@@ -150,6 +152,13 @@ def qmc_pixel_lattice_points(g, s, image_width, image_height, pixel_begin, n_pix
                              stream=None):
     _check(_lib.qmc_pixel_lattice_points(_dev(g), s, image_width, image_height, pixel_begin, n_pixels, spp,
                                          _dev(out_u32), _dev(out_f32), _stream(stream)), "qmc_pixel_lattice_points")
+
+
+def qmc_halton_points(s, mode, multipliers, index_begin, count, out_u32, out_f32, stream=None):
+    """multipliers: host array [s] for HALTON_LINEAR, else None."""
+    m = None if multipliers is None else np.ascontiguousarray(multipliers, dtype=np.uint32)
+    _check(_lib.qmc_halton_points(s, mode, None if m is None else m.ctypes.data, index_begin, count,
+                                  _dev(out_u32), _dev(out_f32), _stream(stream)), "qmc_halton_points")
 
 
 def qmc_lattice_points(g, shift, s, index_begin, count, flags, out_u32, out_f32, stream=None):

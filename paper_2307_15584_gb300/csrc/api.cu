@@ -193,6 +193,30 @@ qmc_status qmc_sobol_points(const uint32_t* d_matrices, uint32_t s, uint64_t ind
   return launch_sobol_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 
+qmc_status qmc_halton_points(uint32_t s, uint32_t mode, const uint32_t* h_multipliers, uint64_t index_begin,
+                             uint64_t count, uint32_t* d_out_u32, float* d_out_f32, qmc_stream_t stream) {
+  if (s == 0 || s > kHaltonMaxDims || mode > QMC_HALTON_LINEAR) return QMC_ERR_INVALID_ARG;
+  if (mode == QMC_HALTON_LINEAR && !h_multipliers) return QMC_ERR_INVALID_ARG;
+  const qmc_status st = check_points_args(1, index_begin, count, d_out_u32, d_out_f32);
+  if (st != QMC_OK || count == 0) return st;
+  HaltonArgs a{};
+  a.out_u32 = d_out_u32;
+  a.out_f32 = d_out_f32;
+  a.count = count;
+  a.index_begin = (uint32_t)index_begin;
+  a.s = s;
+  a.mode = mode;
+  for (uint32_t j = 0; j < s; ++j) {
+    const uint32_t b = halton_base(j);
+    if (mode == QMC_HALTON_LINEAR) {
+      const uint32_t m = h_multipliers[j];
+      if (b > 2 && (m == 0 || m >= b)) return QMC_ERR_INVALID_ARG;  // must permute the digits
+      a.mult[j] = b > 2 ? m : 1u;
+    }
+  }
+  return launch_halton_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
 qmc_status qmc_pixel_lattice_points(const uint32_t* d_g, uint32_t s, uint32_t image_width,
                                     uint32_t image_height, uint64_t pixel_begin, uint64_t n_pixels,
                                     uint32_t spp, uint32_t* d_out_u32, float* d_out_f32,

@@ -20,6 +20,8 @@
 // 2^u groups.  For the lattice, phi_2 of disjoint bit fields adds without
 // carries, so x = phi_2(G*Q) g_j + lo_e with one bit reversal per group.
 #include <cstdint>
+#include <mutex>
+#include <vector>
 
 #include "qmc_device.cuh"
 #include "qmc_internal.h"
@@ -318,6 +320,52 @@ __global__ void __launch_bounds__(kThreads) pixel_lattice_points_kernel(PixelPoi
   }
 }
 
+// Halton points: element (r, j) = phi_b(i') of index i = index_begin + r with
+// b the j-th prime; digits permuted (Faure table or linear multiplier),
+// i' = i for b = 2 (the bit reversal covers every 32-bit index), otherwise
+// i mod b^K (Alg. 1's domain limit).  Division by b through a 64-bit
+// multiply-high with the precomputed reciprocal (exact for 32-bit operands).
+constexpr uint32_t kHaltonPermWords = 8896;  // sum of the first 64 primes (8893), rounded up
+struct HaltonTables {
+  uint32_t base[kHaltonMaxDims];
+  uint32_t max_power[kHaltonMaxDims];  // largest power of the base below 2^32
+  uint32_t perm_off[kHaltonMaxDims];   // Faure table of dimension j at perm[perm_off[j]]
+  uint64_t magic[kHaltonMaxDims];      // floor(2^64 / base) + 1: x / base = umulhi(x, magic)
+  uint16_t perm[kHaltonPermWords];
+};
+__device__ HaltonTables g_halton;
+
+__global__ void __launch_bounds__(kThreads) halton_points_kernel(HaltonArgs p) {
+  const uint64_t total = p.count * p.s;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += stride) {
+    const uint64_t r = f / p.s;
+    const uint32_t j = (uint32_t)(f - r * p.s);
+    const uint32_t i = p.index_begin + (uint32_t)r;
+    const uint32_t b = g_halton.base[j];
+    uint32_t v;
+    if (b == 2) {
+      v = __brev(i);  // every permutation of {0, 1} that fixes 0 is the identity
+    } else {
+      uint64_t x = i % g_halton.max_power[j];
+      const uint64_t magic = g_halton.magic[j];
+      const uint32_t poff = g_halton.perm_off[j];
+      uint64_t num = 0, den = 1;
+      while (x) {
+        const uint64_t q = __umul64hi(x, magic);
+        uint32_t d = (uint32_t)(x - q * b);
+        if (p.mode == 1) d = __ldg(g_halton.perm + poff + d);
+        else if (p.mode == 2) d = (uint32_t)(((uint64_t)p.mult[j] * d) % b);
+        num = num * b + d;
+        den *= b;
+        x = q;
+      }
+      v = (uint32_t)((num << 32) / den);
+    }
+    store1(p.out_u32, p.out_f32, f, v);
+  }
+}
+
 // Chunks per lane of the fast path, or 0 when the generic path must run.
 uint32_t fast_k(uint32_t s) {
   uint32_t g = 128;
@@ -425,6 +473,92 @@ cudaError_t launch_sobol_points(PointsArgs a, cudaStream_t stream) {
   }
 #undef QMC_SOBOL_CASE
 #undef QMC_SOBOL_MODES
+}
+
+// Faure permutations sigma_k for k = 0 .. max_k, built bottom-up from Sec. 2.2's
+// rule (even k: twice sigma_{k/2}, then twice plus one; odd k: sigma_{k-1} with
+// the middle value (k-1)/2 inserted and the values above it moved up).
+static std::vector<std::vector<uint16_t>> faure_tables(uint32_t max_k) {
+  std::vector<std::vector<uint16_t>> t(max_k + 1);
+  for (uint32_t k = 0; k <= max_k; ++k) {
+    if (k <= 2) {
+      for (uint32_t d = 0; d < k; ++d) t[k].push_back((uint16_t)d);
+    } else if (k % 2 == 0) {
+      for (uint16_t v : t[k / 2]) t[k].push_back((uint16_t)(2 * v));
+      for (uint16_t v : t[k / 2]) t[k].push_back((uint16_t)(2 * v + 1));
+    } else {
+      const uint32_t mid = (k - 1) / 2;
+      for (uint32_t d = 0; d < k - 1; ++d) {
+        if (d == mid) t[k].push_back((uint16_t)mid);
+        const uint16_t v = t[k - 1][d];
+        t[k].push_back((uint16_t)(v >= mid ? v + 1 : v));
+      }
+    }
+  }
+  return t;
+}
+
+static const std::vector<uint32_t>& first_primes() {
+  static const std::vector<uint32_t> primes = [] {
+    std::vector<uint32_t> v;
+    for (uint32_t c = 2; v.size() < kHaltonMaxDims; ++c) {
+      bool prime = true;
+      for (uint32_t q : v)
+        if (c % q == 0) {
+          prime = false;
+          break;
+        }
+      if (prime) v.push_back(c);
+    }
+    return v;
+  }();
+  return primes;
+}
+
+// Writes g_halton on the current device once (synchronous copy, under a mutex).
+static cudaError_t ensure_halton_tables() {
+  static std::mutex mu;
+  static uint64_t ready_mask = 0;  // bit d: device d holds the table
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (ready_mask & (1ull << dev)) return cudaSuccess;
+  static HaltonTables h;  // 18 KB: kept off the stack
+  h = HaltonTables{};
+  const std::vector<uint32_t>& primes = first_primes();
+  const std::vector<std::vector<uint16_t>> faure = faure_tables(primes.back());
+  uint32_t off = 0;
+  for (uint32_t j = 0; j < kHaltonMaxDims; ++j) {
+    const uint32_t b = primes[j];
+    uint64_t mp = 1;
+    while (mp * b <= 0xFFFFFFFFull) mp *= b;
+    h.base[j] = b;
+    h.max_power[j] = (uint32_t)mp;
+    h.magic[j] = UINT64_MAX / b + 1;
+    h.perm_off[j] = off;
+    if (off + b > kHaltonPermWords) return cudaErrorInvalidValue;  // table sized for the first 64 primes
+    for (uint32_t d = 0; d < b; ++d) h.perm[off + d] = faure[b][d];
+    off += b;
+  }
+  e = cudaMemcpyToSymbol(g_halton, &h, sizeof(h));
+  if (e == cudaSuccess) ready_mask |= 1ull << dev;
+  return e;
+}
+
+uint32_t halton_base(uint32_t j) { return first_primes()[j]; }
+
+cudaError_t launch_halton_points(const HaltonArgs& p, cudaStream_t stream) {
+  const cudaError_t e = ensure_halton_tables();
+  if (e != cudaSuccess) return e;
+  const DeviceInfo& dev = device_info();
+  uint64_t blocks = (p.count * p.s + kThreads - 1) / kThreads;
+  const uint64_t cap = (uint64_t)dev.sm_count * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  halton_points_kernel<<<(unsigned)blocks, kThreads, 0, stream>>>(p);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pixel_lattice_points(const PixelPointsArgs& a, cudaStream_t stream) {

@@ -1,0 +1,34 @@
+"""GPU parity of the Halton engine (Sec. 2.2): radical inverses in the first
+64 prime bases, plain, Faure-permuted and linearly scrambled, bit-exact."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2307_15584_gb300 import binding
+
+    return binding
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("s,begin,count", [(8, 0, 4099), (64, 12345, 777), (16, (1 << 32) - 1500, 1500)])
+def test_halton_bit_exact(B, oracle, mode, s, begin, count):
+    primes = [oracle.lib().qo_prime(j) for j in range(s)]
+    mult = np.array([1 + (7 * j + 3) % (p - 1) if p > 2 else 1 for j, p in enumerate(primes)], np.uint32)
+    u = torch.empty((count, s), dtype=torch.int32, device="cuda")
+    f = torch.empty((count, s), dtype=torch.float32, device="cuda")
+    B.qmc_halton_points(s, mode, mult if mode == 2 else None, begin, count, u, f)
+    ref = oracle.halton_points(s, begin, count, mode, mult)
+    np.testing.assert_array_equal(B.as_u32(u), ref)
+    np.testing.assert_array_equal(f.cpu().numpy().view(np.uint32), oracle.map_u32_to_unifloat(ref).view(np.uint32))
+
+
+def test_halton_argument_errors(B):
+    u = torch.empty(64, dtype=torch.int32, device="cuda")
+    for args in ((0, 0, None), (65, 0, None), (4, 3, None), (4, 2, None), (4, 2, np.array([1, 3, 1, 1]))):
+        with pytest.raises(B.QMCError):
+            B.qmc_halton_points(args[0], args[1], args[2], 0, 8, u, None)
