@@ -56,6 +56,13 @@ def lib() -> ctypes.CDLL:
             "qo_radical_inverse_u32": (u32, [u32, u64]),
             "qo_primitive_polynomials": (u32, [u32, P, u32]),
             "qo_sobol_matrices": (i32, [u32, P, P]),
+            "qo_sobol_matrices_wide": (i32, [u32, u32, P, P]),
+            "qo_sobol_u64": (u32, [P, u32, u64]),
+            "qo_sobol_points_wide": (None, [P, u32, u32, u64, u64, u32, P, P, P]),
+            "qo_partition_index": (u64, [u32, u32, u64, u64]),
+            "qo_sobol_points_partitioned": (None, [P, u32, u32, u32, u64, u64, u64, u32, P, P, P]),
+            "qo_halton_u64": (u32, [u64, u32, u32, u32]),
+            "qo_halton_points_partitioned": (None, [u32, u32, P, u32, u64, u64, u64, P]),
             "qo_sobol_u32": (u32, [P, u32]),
             "qo_nested_scramble": (u32, [u32, u32]),
             "qo_sobol_points": (None, [P, u32, u64, u64, u32, P, P, P]),
@@ -128,6 +135,22 @@ def sobol_matrices(s: int, raw_init: np.ndarray) -> np.ndarray:
     return C
 
 
+def sobol_matrices_wide(s: int, m: int, raw_init: np.ndarray) -> np.ndarray:
+    """u32 [s][m]: generator columns for indices of up to m bits (32 <= m <= 64)."""
+    raw = np.ascontiguousarray(raw_init, dtype=np.uint32).reshape(-1)
+    if raw.size < 7 * s:
+        raise ValueError("raw_init needs 7 words per dimension")
+    C = np.zeros((s, m), np.uint32)
+    if lib().qo_sobol_matrices_wide(s, m, _p(raw), _p(C)) != 0:
+        raise ValueError("bad dimension count or column count")
+    return C
+
+
+def partition_index(b: int, q: int, p: int, J: int) -> int:
+    """Global index of the J-th point of processing element p of P = b^q."""
+    return lib().qo_partition_index(b, q, p, J)
+
+
 def nested_scramble(y: int, seed: int) -> int:
     return lib().qo_nested_scramble(y, seed)
 
@@ -153,6 +176,44 @@ def sobol_points(C, begin, count, mode=SCRAMBLE_NONE, seeds=None, threads=None):
                               u[r0:].ctypes.data, f[r0:].ctypes.data)
 
     _chunked(count, threads, run)
+    return u, f
+
+
+def sobol_points_wide(C, begin, count, mode=SCRAMBLE_NONE, seeds=None, threads=None):
+    """(u32, f32) [count][s] of points begin .. begin+count-1 (64-bit indices) of the
+    wide matrices C [s][m]."""
+    C = np.ascontiguousarray(C, dtype=np.uint32)
+    s, m = C.shape
+    seeds = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint32)
+    u = np.empty((count, s), np.uint32)
+    f = np.empty((count, s), np.float32)
+
+    def run(r0, n):
+        n = min(n, count - r0)
+        lib().qo_sobol_points_wide(_p(C), m, s, begin + r0, n, mode, _p(seeds),
+                                   u[r0:].ctypes.data, f[r0:].ctypes.data)
+
+    if count:
+        _chunked(count, threads, run)
+    return u, f
+
+
+def sobol_points_partitioned(C, q, p, j_begin, count, mode=SCRAMBLE_NONE, seeds=None, threads=None):
+    """(u32, f32) [count][s]: dimensions 1..s of the points of processing element p
+    of 2^q (partitioned by dimension 0 of C [s+1][m]), local indices j_begin.."""
+    C = np.ascontiguousarray(C, dtype=np.uint32)
+    s, m = C.shape[0] - 1, C.shape[1]
+    seeds = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint32)
+    u = np.empty((count, s), np.uint32)
+    f = np.empty((count, s), np.float32)
+
+    def run(r0, n):
+        n = min(n, count - r0)
+        lib().qo_sobol_points_partitioned(_p(C), m, s, q, p, j_begin + r0, n, mode, _p(seeds),
+                                          u[r0:].ctypes.data, f[r0:].ctypes.data)
+
+    if count:
+        _chunked(count, threads, run)
     return u, f
 
 
@@ -294,4 +355,20 @@ def halton_points(s, begin, count, mode=HALTON_NONE, multipliers=None, threads=N
                 out[r, j] = lib().qo_halton_u32((begin + r) & 0xFFFFFFFF, j, mode, int(mult[j]))
 
     _chunked(count, threads, run)
+    return out
+
+
+def halton_points_partitioned(s, q, p, j_begin, count, mode=HALTON_NONE, multipliers=None, threads=None):
+    """u32 [count][s]: dimensions 1..s (bases 3, 5, ..) of the Halton points of
+    processing element p of 2^q (partitioned by dimension 0, base 2)."""
+    mult = None if multipliers is None else np.ascontiguousarray(multipliers, np.uint32)
+    out = np.empty((count, s), np.uint32)
+
+    def run(r0, n):
+        n = min(n, count - r0)
+        lib().qo_halton_points_partitioned(s, mode, _p(mult), q, p, j_begin + r0, n,
+                                           out[r0:].ctypes.data)
+
+    if count:
+        _chunked(count, threads, run)
     return out

@@ -20,7 +20,11 @@
  * brute-force counting; the polynomial enumeration against the counts
  * phi(2^d-1)/d; dimension 1 against the Pascal matrix mod 2; the lattice
  * against its closed form; integrands against closed-form integrals and
- * numerical quadrature; gradients against finite differences.
+ * numerical quadrature; gradients against finite differences; the wide
+ * (up to 64-column) matrices against the Pascal closed form and Niederreiter's
+ * rank criterion for the t-value of the first 2^m points, m up to 64; the
+ * partitioning of Sec. 2.5.1 against brute-force selection by the extra
+ * coordinate and the (t, s-1)-sequence property of each element's points.
  *
  * Parity unpinned: the exact output bits of qo_nested_scramble.  The paper
  * names Owen scrambling but prints no algorithm; the hash below is this
@@ -124,18 +128,20 @@ QO_EXPORT uint32_t qo_faure(uint32_t b, uint32_t d)
  * floor(phi(i') 2^32) where the digits of i' are permuted digit by digit:
  *   mode 0: identity; mode 1: Faure sigma_b; mode 2: linear d -> (m d) mod b
  *   (Alg. 2, radinv_linscramble, multiplier m).
- * i' = i for base 2 (bit reversal covers every 32-bit index), otherwise
- * i mod b^K with b^K the largest power of b below 2^32 (Alg. 1's domain
- * limit).  Digits are peeled off one at a time. */
-QO_EXPORT uint32_t qo_halton_u32(uint32_t i, uint32_t j, uint32_t mode, uint32_t m)
+ * i' = i mod b^K with b^K the largest power of b that the 32-bit result
+ * resolves: 2^32 for base 2 (the bit reversal of the low 32 index bits),
+ * otherwise the largest power of b below 2^32 (Alg. 1's domain limit).  Digits
+ * are peeled off one at a time.  Indices take 64 bits (Sec. 2.5.1). */
+QO_EXPORT uint32_t qo_halton_u64(uint64_t i, uint32_t j, uint32_t mode, uint32_t m)
 {
     uint32_t b = qo_prime(j);
-    uint64_t ii = i;
-    if (b != 2) {
-        uint64_t maxp = 1;
+    uint64_t maxp = 1;
+    if (b == 2) {
+        maxp = 1ull << 32;
+    } else {
         while (maxp * b <= 0xFFFFFFFFull) maxp *= b;
-        ii %= maxp;
     }
+    uint64_t ii = i % maxp;
     unsigned __int128 num = 0, den = 1;
     while (ii > 0) {
         uint32_t dgt = (uint32_t)(ii % b);
@@ -146,6 +152,11 @@ QO_EXPORT uint32_t qo_halton_u32(uint32_t i, uint32_t j, uint32_t mode, uint32_t
         ii /= b;
     }
     return (uint32_t)((num << 32) / den);
+}
+
+QO_EXPORT uint32_t qo_halton_u32(uint32_t i, uint32_t j, uint32_t mode, uint32_t m)
+{
+    return qo_halton_u64(i, j, mode, m);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -189,40 +200,53 @@ static uint32_t degree_of(uint32_t p)
     return d;
 }
 
-/* Generator matrices of the s-dimensional Sobol' sequence, as 32 columns per
- * dimension: C[32*j + k] is the image of index bit k, bit 31 being the first
- * digit b^-1 of Eq. (ts).
- *   dimension 0: the identity (van der Corput, phi_2);
+/* Generator matrices of the s-dimensional Sobol' sequence for indices of up
+ * to m bits (32 <= m <= 64; Alg. 3 stores 52), as m columns per dimension:
+ * C[m*j + k] is the image of index bit k, truncated to the first 32 digits of
+ * Eq. (ts), bit 31 being the first digit b^-1.
+ *   dimension 0: the identity (van der Corput, phi_2); its columns beyond the
+ *   32nd are zero (2^-k has no digit among the first 32 when k > 32);
  *   dimension j >= 1: the j-th primitive polynomial of the enumeration above,
  *   initial direction numbers m_k = (raw[7*j + k - 1] mod 2^k) | 1 for k <= deg,
  *   then m_k = m_{k-d} ^ (m_{k-d} << d) ^ XOR_{l=1}^{d-1} a_l (m_{k-l} << l)
- *   for k = d+1..32 (a_l the coefficient of x^(d-l)), column k-1 = m_k << (32-k).
- * Returns 0, or -1 when s exceeds 1 + the number of polynomials of degree <= 7. */
-QO_EXPORT int qo_sobol_matrices(uint32_t s, const uint32_t* raw, uint32_t* C)
+ *   for k = d+1..m (a_l the coefficient of x^(d-l)).  Column k-1 holds the
+ *   first 32 digits of v_k = m_k / 2^k: m_k << (32-k) for k <= 32 and
+ *   m_k >> (k-32) beyond.  m_k < 2^k is carried exactly in 128 bits.
+ * Returns 0, or -1 when s exceeds 1 + the number of polynomials of degree <= 7
+ * or m lies outside [32, 64]. */
+QO_EXPORT int qo_sobol_matrices_wide(uint32_t s, uint32_t m, const uint32_t* raw, uint32_t* C)
 {
     uint32_t polys[64];
     uint32_t npoly = qo_primitive_polynomials(7, polys, 64);
-    if (s > npoly + 1) return -1;
+    if (s > npoly + 1 || m < 32 || m > 64) return -1;
     for (uint32_t j = 0; j < s; ++j) {
+        uint32_t* Cj = C + (uint64_t)m * j;
         if (j == 0) {
-            for (uint32_t k = 0; k < 32; ++k) C[k] = 1u << (31 - k);
+            for (uint32_t k = 0; k < m; ++k) Cj[k] = k < 32 ? 1u << (31 - k) : 0u;
             continue;
         }
         uint32_t p = polys[j - 1];
         uint32_t d = degree_of(p);
-        uint64_t m[33];
+        unsigned __int128 mk[65];
         for (uint32_t k = 1; k <= d; ++k)
-            m[k] = (raw[7 * j + (k - 1)] % (1ull << k)) | 1ull;
-        for (uint32_t k = d + 1; k <= 32; ++k) {
-            uint64_t v = m[k - d] ^ (m[k - d] << d);
+            mk[k] = (raw[7 * j + (k - 1)] % (1ull << k)) | 1ull;
+        for (uint32_t k = d + 1; k <= m; ++k) {
+            unsigned __int128 v = mk[k - d] ^ (mk[k - d] << d);
             for (uint32_t l = 1; l < d; ++l)
-                if ((p >> (d - l)) & 1u) v ^= m[k - l] << l;
-            m[k] = v;
+                if ((p >> (d - l)) & 1u) v ^= mk[k - l] << l;
+            mk[k] = v;
         }
-        for (uint32_t k = 1; k <= 32; ++k)
-            C[32 * j + (k - 1)] = (uint32_t)(m[k] << (32 - k));
+        for (uint32_t k = 1; k <= m; ++k)
+            Cj[k - 1] = k <= 32 ? (uint32_t)(mk[k] << (32 - k)) : (uint32_t)(mk[k] >> (k - 32));
     }
     return 0;
+}
+
+/* The 32-column matrices (indices below 2^32): the first 32 columns of the
+ * wide construction. */
+QO_EXPORT int qo_sobol_matrices(uint32_t s, const uint32_t* raw, uint32_t* C)
+{
+    return qo_sobol_matrices_wide(s, 32, raw, C);
 }
 
 /* Eq. (ts) over F_2 and Alg. 3 with a zero scramble: the XOR of the columns
@@ -279,6 +303,90 @@ QO_EXPORT void qo_sobol_points(const uint32_t* C, uint32_t s, uint64_t begin, ui
             if (out_u32) out_u32[r * s + j] = y;
             if (out_f32) out_f32[r * s + j] = qo_map_u32_to_unifloat(y);
         }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alg. 3 with wide indices, and Sec. 2.5.1: partitioning one sequence.      */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. (ts) for an index of up to m bits: the XOR of the columns of Cj (m of
+ * them) selected by the set bits of i.  Bits of i at or above m must be 0. */
+QO_EXPORT uint32_t qo_sobol_u64(const uint32_t* Cj, uint32_t m, uint64_t i)
+{
+    uint32_t y = 0;
+    for (uint32_t k = 0; k < m; ++k)
+        if ((i >> k) & 1u) y ^= Cj[k];
+    return y;
+}
+
+/* Materialised Sobol' points with 64-bit indices: row r holds point begin + r
+ * of the matrices C ([s][m]); randomisation and outputs as qo_sobol_points. */
+QO_EXPORT void qo_sobol_points_wide(const uint32_t* C, uint32_t m, uint32_t s, uint64_t begin,
+                                    uint64_t count, uint32_t mode, const uint32_t* seeds,
+                                    uint32_t* out_u32, float* out_f32)
+{
+    for (uint64_t r = 0; r < count; ++r) {
+        uint64_t i = begin + r;
+        for (uint32_t j = 0; j < s; ++j) {
+            uint32_t y = qo_sobol_u64(C + (uint64_t)m * j, m, i);
+            y = randomise_sobol(y, mode, seeds ? seeds[j] : 0u);
+            if (out_u32) out_u32[r * s + j] = y;
+            if (out_f32) out_f32[r * s + j] = qo_map_u32_to_unifloat(y);
+        }
+    }
+}
+
+/* Sec. 2.5.1: the sequence is extended by one radical-inversion dimension in
+ * base b, whose unit interval is cut into P = b^q intervals; processing element
+ * p (0 <= p < P) owns the points whose extra coordinate phi_b(i) lies in
+ * [p/P, (p+1)/P).  The first q digits of phi_b(i) are the q lowest base-b digits
+ * of i in reverse order, so those points are exactly i = J P + c_p, J = 0, 1,
+ * .., where c_p is p with its q base-b digits reversed.  Returns the global
+ * index of the J-th point of element p (the caller keeps it below 2^64). */
+QO_EXPORT uint64_t qo_partition_index(uint32_t b, uint32_t q, uint64_t p, uint64_t J)
+{
+    uint64_t P = 1, c = 0, rest = p;
+    for (uint32_t k = 0; k < q; ++k) {
+        c = c * b + rest % b;  /* digit k of p becomes digit q-1-k of c */
+        rest /= b;
+        P *= b;
+    }
+    return J * P + c;
+}
+
+/* Points J = j_begin .. j_begin+count-1 of element p of P = 2^q, partitioned by
+ * dimension 0 of the Sobol' matrices C ([s+1][m], dimension 0 the identity =
+ * phi_2): row r holds dimensions 1..s of point qo_partition_index(2, q, p,
+ * j_begin + r); seeds[s] randomise those s dimensions. */
+QO_EXPORT void qo_sobol_points_partitioned(const uint32_t* C, uint32_t m, uint32_t s,
+                                           uint32_t q, uint64_t p, uint64_t j_begin,
+                                           uint64_t count, uint32_t mode,
+                                           const uint32_t* seeds, uint32_t* out_u32,
+                                           float* out_f32)
+{
+    for (uint64_t r = 0; r < count; ++r) {
+        uint64_t i = qo_partition_index(2, q, p, j_begin + r);
+        for (uint32_t j = 0; j < s; ++j) {
+            uint32_t y = qo_sobol_u64(C + (uint64_t)m * (j + 1), m, i);
+            y = randomise_sobol(y, mode, seeds ? seeds[j] : 0u);
+            if (out_u32) out_u32[r * s + j] = y;
+            if (out_f32) out_f32[r * s + j] = qo_map_u32_to_unifloat(y);
+        }
+    }
+}
+
+/* Halton points partitioned by dimension 0 (base 2, P = 2^q elements): row r
+ * holds dimensions 1..s (bases 3, 5, ..) of point qo_partition_index(2, q, p,
+ * j_begin + r); mult[j] is the linear multiplier of output dimension j. */
+QO_EXPORT void qo_halton_points_partitioned(uint32_t s, uint32_t mode, const uint32_t* mult,
+                                            uint32_t q, uint64_t p, uint64_t j_begin,
+                                            uint64_t count, uint32_t* out_u32)
+{
+    for (uint64_t r = 0; r < count; ++r) {
+        uint64_t i = qo_partition_index(2, q, p, j_begin + r);
+        for (uint32_t j = 0; j < s; ++j)
+            out_u32[r * s + j] = qo_halton_u64(i, j + 1, mode, mult ? mult[j] : 0u);
     }
 }
 
