@@ -16,9 +16,11 @@
  *   - Invalid arguments are rejected before anything is enqueued.  No C++
  *     exception crosses this boundary.
  *   - Point layouts are row-major [count][s]: row r holds point index_begin + r.
- *   - Indices are 32-bit: index_begin + count must not exceed 2^32 (Sec. 2.5
- *     warns that indices wrapping around in 32 bits cause subtle errors, so
- *     the range is checked instead of wrapped).
+ *   - Indices are 32-bit unless an entry point says otherwise: index_begin +
+ *     count must not exceed 2^32 (Sec. 2.5 warns that indices wrapping around
+ *     in 32 bits cause subtle errors, so the range is checked instead of
+ *     wrapped).  The *_wide and *_partitioned entry points take 64-bit index
+ *     ranges (Alg. 3, Sec. 2.5.1), checked the same way.
  */
 #ifndef QMC_GB300_H
 #define QMC_GB300_H
@@ -140,6 +142,20 @@ QMC_API const char* qmc_status_string(qmc_status status);
 QMC_API qmc_status qmc_sobol_matrices(uint32_t s, const uint32_t* h_raw_init, uint32_t* h_matrices);
 
 /*
+ * Sobol' generator matrices for indices of up to m bits (Alg. 3 stores 52
+ * columns per dimension; host only, no CUDA call).
+ *   m            columns per dimension, 32 <= m <= 64
+ *   h_matrices   out: [s][m]; column k of dimension j is the first 32 digits of
+ *                the image of index bit k (bit 31 = digit 2^-1)
+ * Other arguments as for qmc_sobol_matrices, whose [s][32] output equals the
+ * first 32 columns.  Column k-1 holds the first 32 digits of m_k / 2^k for
+ * every k (m_k >> (k-32) beyond the 32nd); dimension 0's columns beyond the
+ * 32nd are zero, since 2^-k has no digit among the first 32 for k > 32.
+ */
+QMC_API qmc_status qmc_sobol_matrices_wide(uint32_t s, uint32_t m, const uint32_t* h_raw_init,
+                                           uint32_t* h_matrices);
+
+/*
  * Materialised Sobol' points (Alg. 3, Eq. (ts), Sec. 2.1 float conversion).
  *   d_matrices   [s][32] generator columns (layout of qmc_sobol_matrices)
  *   s            1 <= s <= 1024
@@ -156,6 +172,44 @@ QMC_API qmc_status qmc_sobol_matrices(uint32_t s, const uint32_t* h_raw_init, ui
 QMC_API qmc_status qmc_sobol_points(const uint32_t* d_matrices, uint32_t s, uint64_t index_begin,
                             uint64_t count, uint32_t scramble, const uint32_t* d_seeds,
                             uint32_t* d_out_u32, float* d_out_f32, qmc_stream_t stream);
+
+/*
+ * Materialised Sobol' points with 64-bit indices (Alg. 3: the index bits
+ * beyond the 32nd select further generator columns).
+ *   d_matrices   [s][m] columns (layout of qmc_sobol_matrices_wide), 32 <= m <= 64
+ *   index_begin, count   indices index_begin .. index_begin+count-1, all below
+ *                2^m (QMC_ERR_RANGE otherwise; for m = 64 the range may end at
+ *                2^64 - 1)
+ * Other arguments, layouts, paths and errors as for qmc_sobol_points, whose
+ * output this reproduces for m = 32.
+ */
+QMC_API qmc_status qmc_sobol_points_wide(const uint32_t* d_matrices, uint32_t m, uint32_t s,
+                                         uint64_t index_begin, uint64_t count, uint32_t scramble,
+                                         const uint32_t* d_seeds, uint32_t* d_out_u32,
+                                         float* d_out_f32, qmc_stream_t stream);
+
+/*
+ * One element of a Sobol' sequence partitioned across P = 2^q processing
+ * elements by an extra dimension (Sec. 2.5.1).  Dimension 0 of the matrices
+ * (phi_2) is the extra dimension: element p owns the points whose dimension-0
+ * coordinate lies in [p/P, (p+1)/P), i.e. the indices i = J 2^q + c_p, c_p the
+ * q-bit reversal of p.  Row r holds dimensions 1..s of the point with
+ * J = j_begin + r, so each element enumerates its own subsequence without
+ * communication; the elements' rows together are the whole sequence.
+ *   d_matrices   [s+1][m] columns (layout of qmc_sobol_matrices_wide); dimension
+ *                0 must be the identity written there
+ *   q            0 <= q < m;  p: 0 <= p < 2^q (QMC_ERR_INVALID_ARG otherwise)
+ *   j_begin, count   J = j_begin .. j_begin+count-1, all below 2^(m-q)
+ *                (QMC_ERR_RANGE otherwise)
+ *   d_seeds      [s] seeds of the output dimensions (unless NONE)
+ *   d_out_u32, d_out_f32   [count][s]
+ * Other arguments, layouts and errors as for qmc_sobol_points.
+ */
+QMC_API qmc_status qmc_sobol_points_partitioned(const uint32_t* d_matrices, uint32_t m, uint32_t s,
+                                                uint32_t q, uint64_t p, uint64_t j_begin,
+                                                uint64_t count, uint32_t scramble,
+                                                const uint32_t* d_seeds, uint32_t* d_out_u32,
+                                                float* d_out_f32, qmc_stream_t stream);
 
 /*
  * Materialised rank-1 lattice points (Eq. (R1LS), Alg. 4):
@@ -192,6 +246,26 @@ typedef enum qmc_halton_mode {
 QMC_API qmc_status qmc_halton_points(uint32_t s, uint32_t mode, const uint32_t* h_multipliers,
                                      uint64_t index_begin, uint64_t count, uint32_t* d_out_u32,
                                      float* d_out_f32, qmc_stream_t stream);
+
+/*
+ * One element of a Halton sequence partitioned across P = 2^q processing
+ * elements by its base-2 dimension (Sec. 2.5.1): element p owns the indices
+ * i = J 2^q + c_p (c_p the q-bit reversal of p), whose phi_2 lies in
+ * [p/P, (p+1)/P).  Row r holds Halton dimensions 1..s (bases 3, 5, ..) of the
+ * point with J = j_begin + r; indices are 64-bit and reduced modulo b_j^K as
+ * in qmc_halton_points (q = 0 gives the whole sequence with 64-bit indices).
+ *   s              1 <= s <= 63
+ *   h_multipliers  HOST array [s] for QMC_HALTON_LINEAR, entry j for base
+ *                  b_{j+1}: 1 <= m_j < b_{j+1}; NULL otherwise
+ *   q              0 <= q <= 63;  p: 0 <= p < 2^q (QMC_ERR_INVALID_ARG otherwise)
+ *   j_begin, count   all J below 2^(64-q) (QMC_ERR_RANGE otherwise)
+ * Other arguments, layouts and errors as for qmc_halton_points.
+ */
+QMC_API qmc_status qmc_halton_points_partitioned(uint32_t s, uint32_t mode,
+                                                 const uint32_t* h_multipliers, uint32_t q,
+                                                 uint64_t p, uint64_t j_begin, uint64_t count,
+                                                 uint32_t* d_out_u32, float* d_out_f32,
+                                                 qmc_stream_t stream);
 
 /*
  * Materialised pixel-shifted rank-1 lattice samples (Sec. 3, Eq.

@@ -36,7 +36,8 @@ EXPORTED = ["qmc_abi_version", "qmc_status_string", "qmc_sobol_matrices", "qmc_s
             "qmc_integrate_backward", "qmc_integrate_fwd_bwd", "qmc_integrate_points",
             "qmc_read_device_error", "qmc_integrate_static", "qmc_tune_integrate", "qmc_tune_clear",
             "qmc_graph_begin", "qmc_graph_end", "qmc_graph_launch", "qmc_graph_destroy",
-            "qmc_pixel_lattice_points", "qmc_halton_points"]
+            "qmc_pixel_lattice_points", "qmc_halton_points", "qmc_sobol_matrices_wide",
+            "qmc_sobol_points_wide", "qmc_sobol_points_partitioned", "qmc_halton_points_partitioned"]
 HALTON_PLAIN, HALTON_FAURE, HALTON_LINEAR = 0, 1, 2
 
 
@@ -68,6 +69,13 @@ _sigs = {
     "qmc_pixel_lattice_points": (ctypes.c_int, [_P, c_uint32, c_uint32, c_uint32, c_uint64, c_uint64, c_uint32,
                                                 _P, _P, _P]),
     "qmc_halton_points": (ctypes.c_int, [c_uint32, c_uint32, _P, c_uint64, c_uint64, _P, _P, _P]),
+    "qmc_sobol_matrices_wide": (ctypes.c_int, [c_uint32, c_uint32, _P, _P]),
+    "qmc_sobol_points_wide": (ctypes.c_int, [_P, c_uint32, c_uint32, c_uint64, c_uint64, c_uint32, _P, _P, _P,
+                                             _P]),
+    "qmc_sobol_points_partitioned": (ctypes.c_int, [_P, c_uint32, c_uint32, c_uint32, c_uint64, c_uint64,
+                                                    c_uint64, c_uint32, _P, _P, _P, _P]),
+    "qmc_halton_points_partitioned": (ctypes.c_int, [c_uint32, c_uint32, _P, c_uint32, c_uint64, c_uint64,
+                                                     c_uint64, _P, _P, _P]),
     "qmc_integrate_workspace_bytes": (c_size_t, [ctypes.POINTER(qmc_problem), c_uint32, _P]),
     "qmc_integrate": (ctypes.c_int, [ctypes.POINTER(qmc_problem), c_uint32, _P, _P, _P, _P, c_size_t, _P]),
     "qmc_integrate_backward": (ctypes.c_int, [ctypes.POINTER(qmc_problem), c_uint32, _P, _P, _P, _P, _P,
@@ -143,6 +151,26 @@ def qmc_sobol_matrices(s: int, raw_init) -> np.ndarray:
     return out
 
 
+def qmc_sobol_matrices_wide(s: int, m: int, raw_init) -> np.ndarray:
+    raw = np.ascontiguousarray(raw_init, dtype=np.uint32)
+    out = np.zeros((s, m), np.uint32)
+    _check(_lib.qmc_sobol_matrices_wide(s, m, raw.ctypes.data if raw.size else None, out.ctypes.data),
+           "qmc_sobol_matrices_wide")
+    return out
+
+
+def qmc_sobol_points_wide(matrices, m, s, index_begin, count, scramble, seeds, out_u32, out_f32, stream=None):
+    _check(_lib.qmc_sobol_points_wide(_dev(matrices), m, s, index_begin, count, scramble, _dev(seeds),
+                                      _dev(out_u32), _dev(out_f32), _stream(stream)), "qmc_sobol_points_wide")
+
+
+def qmc_sobol_points_partitioned(matrices, m, s, q, p, j_begin, count, scramble, seeds, out_u32, out_f32,
+                                 stream=None):
+    _check(_lib.qmc_sobol_points_partitioned(_dev(matrices), m, s, q, p, j_begin, count, scramble, _dev(seeds),
+                                             _dev(out_u32), _dev(out_f32), _stream(stream)),
+           "qmc_sobol_points_partitioned")
+
+
 def qmc_sobol_points(matrices, s, index_begin, count, scramble, seeds, out_u32, out_f32, stream=None):
     _check(_lib.qmc_sobol_points(_dev(matrices), s, index_begin, count, scramble, _dev(seeds), _dev(out_u32),
                                  _dev(out_f32), _stream(stream)), "qmc_sobol_points")
@@ -159,6 +187,14 @@ def qmc_halton_points(s, mode, multipliers, index_begin, count, out_u32, out_f32
     m = None if multipliers is None else np.ascontiguousarray(multipliers, dtype=np.uint32)
     _check(_lib.qmc_halton_points(s, mode, None if m is None else m.ctypes.data, index_begin, count,
                                   _dev(out_u32), _dev(out_f32), _stream(stream)), "qmc_halton_points")
+
+
+def qmc_halton_points_partitioned(s, mode, multipliers, q, p, j_begin, count, out_u32, out_f32, stream=None):
+    """multipliers: host array [s] (bases 3, 5, ..) for HALTON_LINEAR, else None."""
+    m = None if multipliers is None else np.ascontiguousarray(multipliers, dtype=np.uint32)
+    _check(_lib.qmc_halton_points_partitioned(s, mode, None if m is None else m.ctypes.data, q, p, j_begin, count,
+                                              _dev(out_u32), _dev(out_f32), _stream(stream)),
+           "qmc_halton_points_partitioned")
 
 
 def qmc_lattice_points(g, shift, s, index_begin, count, flags, out_u32, out_f32, stream=None):

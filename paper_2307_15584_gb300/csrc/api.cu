@@ -118,7 +118,7 @@ using namespace qmc;
 
 extern "C" {
 
-uint32_t qmc_abi_version(void) { return 2u; }
+uint32_t qmc_abi_version(void) { return 3u; }
 
 const char* qmc_status_string(qmc_status st) {
   switch (st) {
@@ -134,32 +134,62 @@ const char* qmc_status_string(qmc_status st) {
   return "unknown qmc_status";
 }
 
-qmc_status qmc_sobol_matrices(uint32_t s, const uint32_t* h_raw_init, uint32_t* h_matrices) {
+qmc_status qmc_sobol_matrices_wide(uint32_t s, uint32_t m, const uint32_t* h_raw_init,
+                                   uint32_t* h_matrices) {
   static const std::vector<uint32_t> polys = primitive_polynomials_deg7();
-  if (s == 0 || s > polys.size() + 1 || !h_matrices) return QMC_ERR_INVALID_ARG;
+  if (s == 0 || s > polys.size() + 1 || !h_matrices || m < 32 || m > 64) return QMC_ERR_INVALID_ARG;
   if (s > 1 && !h_raw_init) return QMC_ERR_INVALID_ARG;
   for (uint32_t j = 0; j < s; ++j) {
-    uint32_t* V = h_matrices + 32 * j;  // V[k-1] = direction integer v_k
+    uint32_t* V = h_matrices + (size_t)m * j;  // V[k-1] = first 32 digits of v_k
     if (j == 0) {
-      for (uint32_t k = 1; k <= 32; ++k) V[k - 1] = 0x80000000u >> (k - 1);
+      for (uint32_t k = 1; k <= m; ++k) V[k - 1] = k <= 32 ? 0x80000000u >> (k - 1) : 0u;
       continue;
     }
     const uint32_t p = polys[j - 1];
     uint32_t d = 0;
     while (p >> (d + 1)) ++d;
     for (uint32_t k = 1; k <= d; ++k) {
-      const uint32_t m = (uint32_t)(h_raw_init[7 * j + k - 1] & ((1ull << k) - 1)) | 1u;
-      V[k - 1] = m << (32 - k);
+      const uint32_t mk = (uint32_t)(h_raw_init[7 * j + k - 1] & ((1ull << k) - 1)) | 1u;
+      V[k - 1] = mk << (32 - k);
     }
     // Bratley-Fox form of the recurrence on direction integers:
-    // v_k = v_{k-d} ^ (v_{k-d} >> d) ^ XOR_{l=1}^{d-1} a_l v_{k-l}
-    for (uint32_t k = d + 1; k <= 32; ++k) {
+    // v_k = v_{k-d} ^ (v_{k-d} >> d) ^ XOR_{l=1}^{d-1} a_l v_{k-l}.  XOR and the
+    // right shift commute with truncation to the first 32 digits, so the
+    // truncated words obey it for every k, also beyond the 32nd column.
+    for (uint32_t k = d + 1; k <= m; ++k) {
       uint32_t v = V[k - d - 1] ^ (V[k - d - 1] >> d);
       for (uint32_t l = 1; l < d; ++l)
         if ((p >> (d - l)) & 1u) v ^= V[k - l - 1];
       V[k - 1] = v;
     }
   }
+  return QMC_OK;
+}
+
+qmc_status qmc_sobol_matrices(uint32_t s, const uint32_t* h_raw_init, uint32_t* h_matrices) {
+  return qmc_sobol_matrices_wide(s, 32, h_raw_init, h_matrices);
+}
+
+// [begin, begin + count) lies inside [0, 2^bits) (bits <= 64).
+static bool index_range_ok(uint64_t begin, uint64_t count, uint32_t bits) {
+  const uint64_t limit_m1 = bits >= 64 ? ~0ull : (1ull << bits) - 1;  // 2^bits - 1
+  if (count == 0) return bits >= 64 || begin <= limit_m1 + 1;
+  const uint64_t last = begin + (count - 1);
+  return last >= begin && last <= limit_m1;
+}
+
+// Bit reversal of the q low bits of p.
+static uint64_t reverse_bits(uint64_t p, uint32_t q) {
+  uint64_t c = 0;
+  for (uint32_t k = 0; k < q; ++k) c |= ((p >> k) & 1ull) << (q - 1 - k);
+  return c;
+}
+
+static qmc_status check_outputs(uint32_t s, uint64_t count, const void* out_u32, const void* out_f32) {
+  if (count == 0) return QMC_OK;  // nothing to write: outputs may be null (empty tensors)
+  if (count > (1ull << 62) / s) return QMC_ERR_RANGE;  // element offsets stay far below 2^64
+  if (!out_u32 && !out_f32) return QMC_ERR_INVALID_ARG;
+  if (((uintptr_t)out_u32 & 3u) || ((uintptr_t)out_f32 & 3u)) return QMC_ERR_ALIGN;
   return QMC_OK;
 }
 
@@ -188,32 +218,111 @@ qmc_status qmc_sobol_points(const uint32_t* d_matrices, uint32_t s, uint64_t ind
   a.out_f32 = d_out_f32;
   a.count = count;
   a.s = s;
-  a.index_begin = (uint32_t)index_begin;
+  a.index_begin = index_begin;
+  a.m = 32;
   a.scramble = scramble;
   return launch_sobol_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 
-qmc_status qmc_halton_points(uint32_t s, uint32_t mode, const uint32_t* h_multipliers, uint64_t index_begin,
-                             uint64_t count, uint32_t* d_out_u32, float* d_out_f32, qmc_stream_t stream) {
-  if (s == 0 || s > kHaltonMaxDims || mode > QMC_HALTON_LINEAR) return QMC_ERR_INVALID_ARG;
-  if (mode == QMC_HALTON_LINEAR && !h_multipliers) return QMC_ERR_INVALID_ARG;
-  const qmc_status st = check_points_args(1, index_begin, count, d_out_u32, d_out_f32);
+qmc_status qmc_sobol_points_wide(const uint32_t* d_matrices, uint32_t m, uint32_t s,
+                                 uint64_t index_begin, uint64_t count, uint32_t scramble,
+                                 const uint32_t* d_seeds, uint32_t* d_out_u32, float* d_out_f32,
+                                 qmc_stream_t stream) {
+  if (!d_matrices || m < 32 || m > 64 || s == 0 || s > 1024) return QMC_ERR_INVALID_ARG;
+  if (scramble > QMC_SCRAMBLE_NESTED) return QMC_ERR_INVALID_ARG;
+  if (scramble != QMC_SCRAMBLE_NONE && !d_seeds) return QMC_ERR_INVALID_ARG;
+  if (!index_range_ok(index_begin, count, m)) return QMC_ERR_RANGE;
+  const qmc_status st = check_outputs(s, count, d_out_u32, d_out_f32);
   if (st != QMC_OK || count == 0) return st;
-  HaltonArgs a{};
+  PointsArgs a{};
+  a.matrices = d_matrices;
+  a.seeds = d_seeds;
   a.out_u32 = d_out_u32;
   a.out_f32 = d_out_f32;
   a.count = count;
-  a.index_begin = (uint32_t)index_begin;
+  a.index_begin = index_begin;
   a.s = s;
+  a.m = m;
+  a.scramble = scramble;
+  return launch_sobol_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+qmc_status qmc_sobol_points_partitioned(const uint32_t* d_matrices, uint32_t m, uint32_t s,
+                                        uint32_t q, uint64_t p, uint64_t j_begin, uint64_t count,
+                                        uint32_t scramble, const uint32_t* d_seeds,
+                                        uint32_t* d_out_u32, float* d_out_f32, qmc_stream_t stream) {
+  if (!d_matrices || m < 32 || m > 64 || s == 0 || s > 1024 || q >= m) return QMC_ERR_INVALID_ARG;
+  if (p >> q) return QMC_ERR_INVALID_ARG;  // element p of 2^q
+  if (scramble > QMC_SCRAMBLE_NESTED) return QMC_ERR_INVALID_ARG;
+  if (scramble != QMC_SCRAMBLE_NONE && !d_seeds) return QMC_ERR_INVALID_ARG;
+  if (!index_range_ok(j_begin, count, m - q)) return QMC_ERR_RANGE;
+  const qmc_status st = check_outputs(s, count, d_out_u32, d_out_f32);
+  if (st != QMC_OK || count == 0) return st;
+  PointsArgs a{};
+  a.matrices = d_matrices + m;  // dimensions 1..s; dimension 0 selects the element
+  a.seeds = d_seeds;
+  a.out_u32 = d_out_u32;
+  a.out_f32 = d_out_f32;
+  a.count = count;
+  a.index_begin = j_begin;
+  a.pconst = reverse_bits(p, q);
+  a.s = s;
+  a.m = m;
+  a.col0 = q;
+  a.scramble = scramble;
+  return launch_sobol_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+// Fills the Halton arguments shared by the plain and partitioned entries;
+// output dimension j is Halton dimension dim0 + j.
+static qmc_status halton_args(uint32_t s, uint32_t dim0, uint32_t mode, const uint32_t* h_multipliers,
+                              HaltonArgs& a) {
+  if (s == 0 || dim0 + s > kHaltonMaxDims || mode > QMC_HALTON_LINEAR) return QMC_ERR_INVALID_ARG;
+  if (mode == QMC_HALTON_LINEAR && !h_multipliers) return QMC_ERR_INVALID_ARG;
+  a.s = s;
+  a.dim0 = dim0;
   a.mode = mode;
   for (uint32_t j = 0; j < s; ++j) {
-    const uint32_t b = halton_base(j);
+    const uint32_t b = halton_base(dim0 + j);
     if (mode == QMC_HALTON_LINEAR) {
       const uint32_t m = h_multipliers[j];
       if (b > 2 && (m == 0 || m >= b)) return QMC_ERR_INVALID_ARG;  // must permute the digits
       a.mult[j] = b > 2 ? m : 1u;
     }
   }
+  return QMC_OK;
+}
+
+qmc_status qmc_halton_points(uint32_t s, uint32_t mode, const uint32_t* h_multipliers, uint64_t index_begin,
+                             uint64_t count, uint32_t* d_out_u32, float* d_out_f32, qmc_stream_t stream) {
+  HaltonArgs a{};
+  qmc_status st = halton_args(s, 0, mode, h_multipliers, a);
+  if (st != QMC_OK) return st;
+  st = check_points_args(1, index_begin, count, d_out_u32, d_out_f32);
+  if (st != QMC_OK || count == 0) return st;
+  a.out_u32 = d_out_u32;
+  a.out_f32 = d_out_f32;
+  a.count = count;
+  a.index_begin = index_begin;
+  return launch_halton_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+qmc_status qmc_halton_points_partitioned(uint32_t s, uint32_t mode, const uint32_t* h_multipliers,
+                                         uint32_t q, uint64_t p, uint64_t j_begin, uint64_t count,
+                                         uint32_t* d_out_u32, float* d_out_f32, qmc_stream_t stream) {
+  if (q > 63 || (p >> q)) return QMC_ERR_INVALID_ARG;
+  HaltonArgs a{};
+  qmc_status st = halton_args(s, 1, mode, h_multipliers, a);
+  if (st != QMC_OK) return st;
+  if (!index_range_ok(j_begin, count, 64 - q)) return QMC_ERR_RANGE;
+  st = check_outputs(s, count, d_out_u32, d_out_f32);
+  if (st != QMC_OK || count == 0) return st;
+  a.out_u32 = d_out_u32;
+  a.out_f32 = d_out_f32;
+  a.count = count;
+  a.index_begin = j_begin;
+  a.q = q;
+  a.pconst = reverse_bits(p, q);
   return launch_halton_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 
@@ -257,7 +366,7 @@ qmc_status qmc_lattice_points(const uint32_t* d_g, const uint32_t* d_shift, uint
   a.out_f32 = d_out_f32;
   a.count = count;
   a.s = s;
-  a.index_begin = (uint32_t)index_begin;
+  a.index_begin = index_begin;
   a.scramble = flags;
   return launch_lattice_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }

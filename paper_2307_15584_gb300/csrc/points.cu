@@ -12,12 +12,13 @@
 // a group is point p_e = e / s, dimension j_e = e % s, the same in every group.
 //
 // Linearity over GF(2) makes the per-element cost O(1): for a group starting
-// at index G*Q (index_begin is a multiple of Q), index bits split into three
-// disjoint fields,
-//   i = (G_hi << (u + q)) | (G_in << q) | p_e,   G_in < 2^u, p_e < Q,
-// and y_j(i) = Hout_j(G_hi) ^ Hin_j[G_in] ^ lo_e.  lo_e is fixed per lane,
-// Hin is a shared-memory table of 2^u rows, Hout is recomputed once every
-// 2^u groups.  For the lattice, phi_2 of disjoint bit fields adds without
+// at enumeration index G*Q (index_begin is a multiple of Q), the bits of the
+// enumeration index J split into three disjoint fields,
+//   J = (G_hi << (u + q)) | (G_in << q) | p_e,   G_in < 2^u, p_e < Q,
+// and y_j(i) = Hout_j(G_hi) ^ Hin_j[G_in] ^ lo_e for i = (J << col0) | pconst.
+// lo_e (which also carries the fixed low part pconst) is fixed per lane, Hin
+// is a shared-memory table of 2^u rows, Hout is recomputed once every 2^u
+// groups.  G_hi takes up to 64 bits (Alg. 3's wide indices).  For the lattice, phi_2 of disjoint bit fields adds without
 // carries, so x = phi_2(G*Q) g_j + lo_e with one bit reversal per group.
 #include <cstdint>
 #include <mutex>
@@ -87,7 +88,8 @@ __device__ __forceinline__ void warp_range(uint64_t n_groups, uint64_t& g0, uint
 
 // ---------------------------------------------------------------------------
 // K1 fast path.  MODE: 0 none, 1 XOR, 2 nested.  K: 16-byte chunks per lane.
-// Shared memory: cols[s][32] (mirrored for nested), hin[2^u][s].
+// Shared memory: cols[s][m] (mirrored for nested), hin[2^u][s], pc[s].  Table
+// entries for index bits at or above m stay zero: no enumerated index sets them.
 // ---------------------------------------------------------------------------
 // TMA: full groups are staged per warp in shared memory (two tiles of
 // kStageGroups groups, u32 and f32 halves) and written by lane 0 with one bulk
@@ -100,19 +102,28 @@ __global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
   constexpr uint32_t kTileWords = kStageGroups * 128u * K;  // one output of one tile
   uint32_t* stage = smem;  // [warps][2 tiles][2 outputs][kTileWords]
   uint32_t* cols = smem + (TMA ? (kThreads / 32) * 4 * kTileWords : 0);
-  uint32_t* hin = cols + s * 32;
+  const uint32_t m = a.m;
+  uint32_t* hin = cols + s * m;
+  uint32_t* pc = hin + nin * s;
 
-  for (uint32_t idx = threadIdx.x; idx < s * 32; idx += blockDim.x) {
+  for (uint32_t idx = threadIdx.x; idx < s * m; idx += blockDim.x) {
     const uint32_t c = __ldg(a.matrices + idx);
     cols[idx] = (MODE == 2) ? __brev(c) : c;
   }
   __syncthreads();
+  const uint32_t cin = a.col0 + a.q_log2;  // column of the lowest G_in bit
   for (uint32_t idx = threadIdx.x; idx < nin * s; idx += blockDim.x) {
     const uint32_t g = idx / s, j = idx - g * s;
     uint32_t y = 0;
-    for (uint32_t k = 0; (g >> k) != 0; ++k)
-      if ((g >> k) & 1u) y ^= cols[j * 32 + a.q_log2 + k];
+    for (uint32_t k = 0; (g >> k) != 0 && cin + k < m; ++k)
+      if ((g >> k) & 1u) y ^= cols[j * m + cin + k];
     hin[idx] = y;
+  }
+  for (uint32_t j = threadIdx.x; j < s; j += blockDim.x) {
+    uint32_t y = 0;
+    for (uint32_t k = 0; k < a.col0; ++k)
+      if ((a.pconst >> k) & 1u) y ^= cols[j * m + k];
+    pc[j] = y;
   }
   __syncthreads();
 
@@ -126,9 +137,9 @@ __global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
     for (int t = 0; t < 4; ++t) {
       const uint32_t e = 4u * (lane + 32u * c) + t;
       const uint32_t p = e / s, j = e - p * s;
-      uint32_t y = 0;
-      for (uint32_t k = 0; k < a.q_log2; ++k)
-        if ((p >> k) & 1u) y ^= cols[j * 32 + k];
+      uint32_t y = pc[j];
+      for (uint32_t k = 0; k < a.q_log2 && a.col0 + k < m; ++k)
+        if ((p >> k) & 1u) y ^= cols[j * m + a.col0 + k];
       if (MODE == 1) y ^= __ldg(a.seeds + j);
       jd[4 * c + t] = j;
       lo[4 * c + t] = y;
@@ -139,8 +150,8 @@ __global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
   const uint64_t full_groups = a.count >> a.q_log2;  // groups whose Q rows all exist
   uint64_t g0, g1;
   warp_range(n_groups, g0, g1);
-  const uint32_t G_first = a.index_begin >> a.q_log2;
-  const uint32_t hi_shift = a.q_log2 + a.u_log2;
+  const uint64_t G_first = a.index_begin >> a.q_log2;
+  const uint32_t hi_col = a.col0 + a.q_log2 + a.u_log2;  // column of the lowest G_hi bit
   const uint64_t step = (uint64_t)Q * s;  // elements per group
   uint64_t off = g0 * step + 4u * lane;   // this lane's first element in group g0
 
@@ -164,15 +175,15 @@ __global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
   };
 
   for (uint64_t g = g0; g < g1; ++g, off += step) {
-    const uint32_t G = G_first + (uint32_t)g;
-    const uint32_t G_in = G & (nin - 1u);
+    const uint64_t G = G_first + g;
+    const uint32_t G_in = (uint32_t)G & (nin - 1u);
     if (g == g0 || G_in == 0) {
-      const uint32_t G_hi = G >> a.u_log2;
+      const uint64_t G_hi = G >> a.u_log2;  // below 2^(m - hi_col) for every enumerated group
 #pragma unroll
       for (int e = 0; e < 4 * K; ++e) {
         uint32_t y = 0;
         for (uint32_t k = 0; (G_hi >> k) != 0; ++k)
-          if ((G_hi >> k) & 1u) y ^= cols[jd[e] * 32 + hi_shift + k];
+          if ((G_hi >> k) & 1u) y ^= cols[jd[e] * m + hi_col + k];
         hout[e] = y;
       }
     }
@@ -229,9 +240,10 @@ __global__ void __launch_bounds__(kThreads) sobol_points_generic(PointsArgs a) {
   for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += stride) {
     const uint64_t r = f / a.s;
     const uint32_t j = (uint32_t)(f - r * a.s);
-    uint32_t i = a.index_begin + (uint32_t)r;
+    uint64_t i = ((a.index_begin + r) << a.col0) | a.pconst;  // below 2^m (checked by the caller)
+    const uint32_t* Cj = a.matrices + (uint64_t)j * a.m;
     uint32_t y = 0;
-    for (; i != 0; i &= i - 1u) y ^= __ldg(a.matrices + j * 32 + (__ffs(i) - 1));
+    for (; i != 0; i &= i - 1u) y ^= __ldg(Cj + (__ffsll((long long)i) - 1));
     if (MODE == 1) y ^= __ldg(a.seeds + j);
     if (MODE == 2) y = __brev(nested_mix(__brev(y), nested_key(__ldg(a.seeds + j))));
     store1(a.out_u32, a.out_f32, f, y);
@@ -264,7 +276,7 @@ __global__ void __launch_bounds__(kThreads) lattice_points_fast(PointsArgs a) {
   const uint64_t full_groups = a.count >> a.q_log2;
   uint64_t g0, g1;
   warp_range(n_groups, g0, g1);
-  const uint32_t G_first = a.index_begin >> a.q_log2;
+  const uint32_t G_first = (uint32_t)(a.index_begin >> a.q_log2);
   const uint64_t step = (uint64_t)Q * s;
   uint64_t off = g0 * step + 4u * lane;
   for (uint64_t g = g0; g < g1; ++g, off += step) {
@@ -296,7 +308,7 @@ __global__ void __launch_bounds__(kThreads) lattice_points_generic(PointsArgs a)
   for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += stride) {
     const uint64_t r = f / a.s;
     const uint32_t j = (uint32_t)(f - r * a.s);
-    const uint32_t k = a.index_begin + (uint32_t)r;
+    const uint32_t k = (uint32_t)a.index_begin + (uint32_t)r;
     const uint32_t phi = __brev(BACKWARD ? ~k : k);
     const uint32_t g = __ldg(a.matrices + j) | 1u;
     const uint32_t sh = a.seeds ? __ldg(a.seeds + j) : 0u;
@@ -320,11 +332,13 @@ __global__ void __launch_bounds__(kThreads) pixel_lattice_points_kernel(PixelPoi
   }
 }
 
-// Halton points: element (r, j) = phi_b(i') of index i = index_begin + r with
-// b the j-th prime; digits permuted (Faure table or linear multiplier),
-// i' = i for b = 2 (the bit reversal covers every 32-bit index), otherwise
-// i mod b^K (Alg. 1's domain limit).  Division by b through a 64-bit
-// multiply-high with the precomputed reciprocal (exact for 32-bit operands).
+// Halton points: element (r, j) = phi_b(i') of index
+// i = ((index_begin + r) << q) | pconst (q > 0: one element of a sequence
+// partitioned by its base-2 dimension, Sec. 2.5.1) with b the (dim0 + j)-th
+// prime; digits permuted (Faure table or linear multiplier), i' = i mod 2^32
+// for b = 2 (the bit reversal of the low 32 bits), otherwise i mod b^K (Alg. 1's
+// domain limit).  Division by b through a 64-bit multiply-high with the
+// precomputed reciprocal (exact for 32-bit operands).
 constexpr uint32_t kHaltonPermWords = 8896;  // sum of the first 64 primes (8893), rounded up
 struct HaltonTables {
   uint32_t base[kHaltonMaxDims];
@@ -340,14 +354,16 @@ __global__ void __launch_bounds__(kThreads) halton_points_kernel(HaltonArgs p) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += stride) {
     const uint64_t r = f / p.s;
-    const uint32_t j = (uint32_t)(f - r * p.s);
-    const uint32_t i = p.index_begin + (uint32_t)r;
+    const uint32_t jo = (uint32_t)(f - r * p.s);
+    const uint32_t j = p.dim0 + jo;
+    const uint64_t i = ((p.index_begin + r) << p.q) | p.pconst;
     const uint32_t b = g_halton.base[j];
     uint32_t v;
     if (b == 2) {
-      v = __brev(i);  // every permutation of {0, 1} that fixes 0 is the identity
+      v = __brev((uint32_t)i);  // every permutation of {0, 1} that fixes 0 is the identity
     } else {
-      uint64_t x = i % g_halton.max_power[j];
+      const uint32_t mp = g_halton.max_power[j];
+      uint64_t x = (i >> 32) ? i % mp : (uint32_t)i % mp;
       const uint64_t magic = g_halton.magic[j];
       const uint32_t poff = g_halton.perm_off[j];
       uint64_t num = 0, den = 1;
@@ -355,7 +371,7 @@ __global__ void __launch_bounds__(kThreads) halton_points_kernel(HaltonArgs p) {
         const uint64_t q = __umul64hi(x, magic);
         uint32_t d = (uint32_t)(x - q * b);
         if (p.mode == 1) d = __ldg(g_halton.perm + poff + d);
-        else if (p.mode == 2) d = (uint32_t)(((uint64_t)p.mult[j] * d) % b);
+        else if (p.mode == 2) d = (uint32_t)(((uint64_t)p.mult[jo] * d) % b);
         num = num * b + d;
         den *= b;
         x = q;
@@ -429,8 +445,20 @@ cudaError_t launch_grid_stride(KernelT kernel, uint64_t elements, cudaStream_t s
 cudaError_t launch_sobol_points(PointsArgs a, cudaStream_t stream) {
   const uint32_t K = fast_k(a.s);
   a.q_log2 = log2_exact(K ? 128u * K / a.s : 1u);
-  const bool fast = K != 0 && a.s <= 256 && (a.index_begin & ((1u << a.q_log2) - 1u)) == 0 &&
-                    aligned16(a.out_u32) && aligned16(a.out_f32);
+  bool fast = K != 0 && a.s <= 256 && (a.index_begin & ((1ull << a.q_log2) - 1u)) == 0 &&
+              aligned16(a.out_u32) && aligned16(a.out_f32);
+  // inner table of at most 16 KiB and 256 rows
+  uint32_t u = 0;
+  while (u < 8 && (2u << u) * a.s * 4u <= 16384u) ++u;
+  a.u_log2 = u;
+  // TMA bulk stores target device memory; outputs in host memory that the GPU
+  // writes directly (pinned, mapped) take the 128-bit store path.
+  bool tma = kPointsTma && device_resident(a.out_u32) && device_resident(a.out_f32);
+  const size_t table_words = (size_t)a.s * a.m + ((size_t)1 << u) * a.s + a.s;
+  const size_t stage_words = (size_t)(kThreads / 32) * 4 * kStageGroups * 128u * K;
+  const size_t optin = device_info().smem_per_block_optin;
+  if (tma && (stage_words + table_words) * sizeof(uint32_t) > optin) tma = false;
+  if (table_words * sizeof(uint32_t) > optin) fast = false;
   if (!fast) {
     switch (a.scramble) {
       case 0: return launch_grid_stride(sobol_points_generic<0>, a.count * a.s, stream, a);
@@ -438,15 +466,7 @@ cudaError_t launch_sobol_points(PointsArgs a, cudaStream_t stream) {
       default: return launch_grid_stride(sobol_points_generic<2>, a.count * a.s, stream, a);
     }
   }
-  // inner table of at most 16 KiB and 256 rows
-  uint32_t u = 0;
-  while (u < 8 && (2u << u) * a.s * 4u <= 16384u) ++u;
-  a.u_log2 = u;
-  // TMA bulk stores target device memory; outputs in host memory that the GPU
-  // writes directly (pinned, mapped) take the 128-bit store path.
-  const bool tma = kPointsTma && device_resident(a.out_u32) && device_resident(a.out_f32);
-  const size_t stage_words = tma ? (size_t)(kThreads / 32) * 4 * kStageGroups * 128u * K : 0;
-  const size_t smem = (stage_words + (size_t)a.s * 32 + ((size_t)1 << u) * a.s) * sizeof(uint32_t);
+  const size_t smem = ((tma ? stage_words : 0) + table_words) * sizeof(uint32_t);
   const uint64_t groups = (a.count + (1u << a.q_log2) - 1) >> a.q_log2;
   const bool v4 = (a.s & 3u) == 0;
 #define QMC_SOBOL_MODES(KK, V, T)                                                                       \

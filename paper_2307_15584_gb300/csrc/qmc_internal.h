@@ -21,15 +21,22 @@ struct DeviceInfo {
 // Properties of the current device (cached per device id).
 const DeviceInfo& device_info();
 
-// Arguments of the materialising kernels.
+// Arguments of the materialising kernels.  Sobol' row r is the point of index
+// i = ((index_begin + r) << col0) | pconst, evaluated with the m columns per
+// dimension of matrices (Alg. 3; m = 32 below 2^32).  col0 > 0 enumerates one
+// element of a partitioned sequence (Sec. 2.5.1): pconst < 2^col0 is its fixed
+// low index part.
 struct PointsArgs {
-  const uint32_t* matrices;  // Sobol': [s][32] columns; lattice: [s] generator words
+  const uint32_t* matrices;  // Sobol': [s][m] columns; lattice: [s] generator words
   const uint32_t* seeds;     // Sobol': scramble seeds [s]; lattice: shifts [s] (nullable)
   uint32_t* out_u32;         // [count][s] or null
   float* out_f32;            // [count][s] or null
   uint64_t count;
+  uint64_t index_begin;      // the caller checked the whole range (2^32 for the lattice)
+  uint64_t pconst;           // Sobol': low index bits below col0
   uint32_t s;
-  uint32_t index_begin;      // index_begin + count <= 2^32 was checked by the caller
+  uint32_t m;                // Sobol': columns per dimension (32 .. 64)
+  uint32_t col0;             // Sobol': first column of the enumerated index
   uint32_t scramble;         // Sobol': 0 none, 1 XOR, 2 nested; lattice: bit 0 = backward
   uint32_t q_log2;           // set by the launcher
   uint32_t u_log2;           // set by the launcher
@@ -55,8 +62,11 @@ struct HaltonArgs {
   uint32_t* out_u32;
   float* out_f32;
   uint64_t count;
-  uint32_t index_begin, s, mode;       // mode: 0 identity, 1 Faure, 2 linear
-  uint32_t mult[kHaltonMaxDims];       // linear digit scramble multipliers
+  uint64_t index_begin;                // row r: index ((index_begin + r) << q) | pconst
+  uint64_t pconst;
+  uint32_t q, dim0;                    // output dimension j is Halton dimension dim0 + j
+  uint32_t s, mode;                    // mode: 0 identity, 1 Faure, 2 linear
+  uint32_t mult[kHaltonMaxDims];       // linear digit scramble multipliers per output dimension
 };
 
 // Enqueues the Halton kernel; writes the device table first if this device has

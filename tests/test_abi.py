@@ -35,7 +35,7 @@ def test_header_symbols_exported(B):
     for name in declared:
         assert hasattr(lib, name), name
     assert sorted(B.EXPORTED) == sorted(declared)
-    assert B.qmc_abi_version() == 2
+    assert B.qmc_abi_version() == 3
     assert ctypes.sizeof(B.qmc_problem) == 64  # 4 + 3 pointers + 6 words, as in include/qmc.h
     assert "INVALID" in B.qmc_status_string(1)
 
@@ -51,6 +51,18 @@ def test_sobol_matrices_match_oracle(B, oracle):
         B.qmc_sobol_matrices(38, inputs.sobol_raw_init(38))
     with pytest.raises(B.QMCError):
         B.qmc_sobol_matrices(0, raw)
+
+
+def test_wide_sobol_matrices_match_oracle(B, oracle):
+    """Wide columns (Alg. 3): the library's truncated-word recurrence equals the
+    oracle's exact 128-bit direction numbers for every m in 32..64."""
+    raw = inputs.sobol_raw_init(37, seed=321)
+    for m in (32, 33, 52, 63, 64):
+        np.testing.assert_array_equal(B.qmc_sobol_matrices_wide(37, m, raw), oracle.sobol_matrices_wide(37, m, raw))
+    np.testing.assert_array_equal(B.qmc_sobol_matrices_wide(37, 32, raw), B.qmc_sobol_matrices(37, raw))
+    for m in (31, 65):
+        with pytest.raises(B.QMCError):
+            B.qmc_sobol_matrices_wide(4, m, raw)
 
 
 FAKE = 0x10000  # an aligned non-null "device" address: never dereferenced (calls fail validation)
@@ -82,6 +94,40 @@ def test_points_validation(B):
     # count = 0 is a no-op that needs no device
     assert L.qmc_sobol_points(FAKE, 4, 0, 0, 0, None, FAKE, None, S) == 0
     assert L.qmc_lattice_points(FAKE, None, 4, 1 << 32, 0, 0, FAKE, None, S) == 0
+
+
+def test_wide_and_partitioned_validation(B):
+    L = B._lib
+    S = None
+    U64 = (1 << 64) - 1
+    W, Pt, H = L.qmc_sobol_points_wide, L.qmc_sobol_points_partitioned, L.qmc_halton_points_partitioned
+    # columns per dimension, dimensions, scramble
+    for m in (31, 65):
+        assert W(FAKE, m, 4, 0, 16, 0, None, FAKE, None, S) == 1
+    assert W(FAKE, 64, 0, 0, 16, 0, None, FAKE, None, S) == 1
+    assert W(FAKE, 64, 4, 0, 16, 2, None, FAKE, None, S) == 1
+    # ranges end at 2^m (m = 64: at 2^64 - 1, with no wrap of begin + count)
+    assert W(FAKE, 40, 4, (1 << 40) - 8, 9, 0, None, FAKE, None, S) == 2
+    assert W(FAKE, 64, 4, U64 - 3, 5, 0, None, FAKE, None, S) == 2
+    assert W(FAKE, 64, 4, U64, 2, 0, None, FAKE, None, S) == 2
+    assert W(FAKE, 64, 1 << 10, 0, 1 << 53, 0, None, FAKE, None, S) == 2  # output offsets beyond 2^62
+    assert W(FAKE, 40, 4, 1 << 40, 0, 0, None, FAKE, None, S) == 0
+    # partition: q < m, p < 2^q, J below 2^(m-q)
+    assert Pt(FAKE, 40, 4, 40, 0, 0, 16, 0, None, FAKE, None, S) == 1
+    assert Pt(FAKE, 40, 4, 3, 8, 0, 16, 0, None, FAKE, None, S) == 1
+    assert Pt(FAKE, 40, 4, 3, 7, (1 << 37) - 4, 5, 0, None, FAKE, None, S) == 2
+    assert Pt(FAKE, 64, 4, 63, 1, 2, 1, 0, None, FAKE, None, S) == 2
+    assert Pt(FAKE, 64, 4, 3, 7, 0, 0, 0, None, FAKE, None, S) == 0
+    assert Pt(FAKE, 64, 4, 3, 7, 0, 16, 0, None, FAKE + 2, None, S) == 3
+    # Halton partition: s <= 63 output dimensions, q <= 63, p < 2^q
+    assert H(64, 0, None, 2, 0, 0, 16, FAKE, None, S) == 1
+    assert H(0, 0, None, 2, 0, 0, 16, FAKE, None, S) == 1
+    assert H(4, 0, None, 64, 0, 0, 16, FAKE, None, S) == 1
+    assert H(4, 0, None, 2, 4, 0, 16, FAKE, None, S) == 1
+    assert H(4, 2, None, 2, 0, 0, 16, FAKE, None, S) == 1
+    m3 = np.array([3, 1, 1, 1], np.uint32)  # 3 is not a unit modulo the base 3
+    assert H(4, 2, m3.ctypes.data, 2, 0, 0, 16, FAKE, None, S) == 1
+    assert H(4, 0, None, 2, 0, 1 << 62, 1, FAKE, None, S) == 2
 
 
 def _problem(B, **kw):
