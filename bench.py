@@ -54,8 +54,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="headline only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     ap.add_argument("--log2-points", type=int, default=24, help="points per GPU (2^k); 24 is the workload")
-    ap.add_argument("--only", choices=["fwd_bwd", "batched", "lattice"], default=None,
-                    help="run one integration workload alone (no headline)")
+    ap.add_argument("--only", choices=["fwd_bwd", "batched", "lattice", "points"], default=None,
+                    help="run one extra workload alone (no headline)")
     ap.add_argument("--small", action="store_true", help="reduced integration sizes (profiling)")
     return ap.parse_args()
 
@@ -397,9 +397,50 @@ def bench_lattice(dev, steps, warmup, small, sm_mhz):
     return res
 
 
+def bench_points(dev, steps, warmup, small, sm_mhz):
+    """Every materialising generator on the headline's shape (s = 32, 2^24 rows,
+    u32 + fp32, 8 B written per coordinate; 2^20 rows when small): the 32-bit
+    Sobol' headline kernel again, Sobol' with 64-bit indices at 2^40 (Alg. 3),
+    one element of a partitioned Sobol' sequence (Sec. 2.5.1), the shifted
+    rank-1 lattice, Halton (Faure) and the pixel-shifted lattice (2^20 pixels x
+    16 samples).  Each against the measured copy bandwidth."""
+    import torch
+
+    from paper_2307_15584_gb300 import binding as B
+    from paper_2307_15584_gb300 import inputs
+
+    stream = torch.cuda.current_stream()
+    s, n = S_DIMS, 1 << (20 if small else 24)
+    peak = measured_peaks()["hbm_gbs"]
+    u = torch.empty((n, s), dtype=torch.int32, device=dev)
+    f = torch.empty((n, s), dtype=torch.float32, device=dev)
+    C = B.u32_tensor(B.qmc_sobol_matrices(s, inputs.sobol_raw_init(s)), dev)
+    W = B.u32_tensor(B.qmc_sobol_matrices_wide(s + 1, 64, inputs.sobol_raw_init(s + 1)), dev)
+    sd = B.u32_tensor(inputs.scramble_seeds(s), dev)
+    g, sh = B.u32_tensor(inputs.lattice_generator(s), dev), B.u32_tensor(inputs.lattice_shift(s), dev)
+    runs = {
+        "sobol32_nested": lambda: B.qmc_sobol_points(C, s, 0, n, B.SCRAMBLE_NESTED, sd, u, f),
+        "sobol64_nested_at_2^40": lambda: B.qmc_sobol_points_wide(W, 64, s, 1 << 40, n, B.SCRAMBLE_NESTED, sd, u, f),
+        "sobol64_partition_p5_of_8": lambda: B.qmc_sobol_points_partitioned(W, 64, s, 3, 5, 1 << 37, n,
+                                                                            B.SCRAMBLE_NESTED, sd, u, f),
+        "lattice_shifted": lambda: B.qmc_lattice_points(g, sh, s, 0, n, 0, u, f),
+        "halton_faure": lambda: B.qmc_halton_points(s, B.HALTON_FAURE, None, 0, n, u, f),
+        "pixel_lattice_16spp": lambda: B.qmc_pixel_lattice_points(g, s, 1024, n // 16 // 1024 or 1, 0,
+                                                                   n // 16, 16, u, f),
+    }
+    res = {"rows": n, "s": s, "bytes_per_launch": n * s * 8}
+    for name, fn in runs.items():
+        ms = statistics.median(timed(fn, steps, warmup, stream))
+        gbs = n * s * 8 / (ms * 1e-3) / 1e9
+        res[name] = {"ms": ms, "gdims_s": n * s / (ms * 1e-3) / 1e9, "gb_s": gbs, "frac_hbm": gbs / peak}
+    del u, f
+    return res
+
+
 def run_extras(args, dev, sm_mhz):
-    which = [args.only] if args.only else ["fwd_bwd", "batched", "lattice"]
-    fns = {"fwd_bwd": bench_fwd_bwd, "batched": bench_batched, "lattice": bench_lattice}
+    which = [args.only] if args.only else ["fwd_bwd", "batched", "lattice", "points"]
+    fns = {"fwd_bwd": bench_fwd_bwd, "batched": bench_batched, "lattice": bench_lattice,
+           "points": bench_points}
     out = {}
     for name in which:
         steps = 3 if args.small else 5

@@ -17,8 +17,9 @@
 //   J = (G_hi << (u + q)) | (G_in << q) | p_e,   G_in < 2^u, p_e < Q,
 // and y_j(i) = Hout_j(G_hi) ^ Hin_j[G_in] ^ lo_e for i = (J << col0) | pconst.
 // lo_e (which also carries the fixed low part pconst) is fixed per lane, Hin
-// is a shared-memory table of 2^u rows, Hout is recomputed once every 2^u
-// groups.  G_hi takes up to 64 bits (Alg. 3's wide indices).  For the lattice, phi_2 of disjoint bit fields adds without
+// is a shared-memory table of 2^u rows, and Hout changes once every 2^u groups,
+// by the columns of the G_hi bits that flip.  G_hi takes up to 64 bits (Alg. 3's
+// wide indices).  For the lattice, phi_2 of disjoint bit fields adds without
 // carries, so x = phi_2(G*Q) g_j + lo_e with one bit reversal per group.
 #include <cstdint>
 #include <mutex>
@@ -177,13 +178,24 @@ __global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
   for (uint64_t g = g0; g < g1; ++g, off += step) {
     const uint64_t G = G_first + g;
     const uint32_t G_in = (uint32_t)G & (nin - 1u);
-    if (g == g0 || G_in == 0) {
+    if (g == g0) {
       const uint64_t G_hi = G >> a.u_log2;  // below 2^(m - hi_col) for every enumerated group
 #pragma unroll
       for (int e = 0; e < 4 * K; ++e) {
         uint32_t y = 0;
         for (uint32_t k = 0; (G_hi >> k) != 0; ++k)
           if ((G_hi >> k) & 1u) y ^= cols[jd[e] * m + hi_col + k];
+        hout[e] = y;
+      }
+    } else if (G_in == 0) {
+      // G_hi advanced by one: exactly the bits of G_hi ^ (G_hi - 1) flipped
+      // (the trailing ones and the bit above them), two on average.
+      const uint64_t G_hi = G >> a.u_log2;
+      const uint32_t nflip = (uint32_t)__ffsll((long long)G_hi);  // G_hi > 0 here
+#pragma unroll
+      for (int e = 0; e < 4 * K; ++e) {
+        uint32_t y = hout[e];
+        for (uint32_t k = 0; k < nflip; ++k) y ^= cols[jd[e] * m + hi_col + k];
         hout[e] = y;
       }
     }
@@ -317,6 +329,49 @@ __global__ void __launch_bounds__(kThreads) lattice_points_generic(PointsArgs a)
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+// Pixel-shifted lattice, coalesced path (s % 4 == 0, 16-byte aligned outputs,
+// 32 spp s <= 2^31).  A warp takes batches of 32 consecutive pixels: lane l
+// computes the shift of pixel l of the batch once (Hilbert position, then
+// phi_3), and the batch's 32 spp rows are written as consecutive 16-byte chunks,
+// each chunk's pixel shift fetched from its lane with a shuffle.
+__global__ void __launch_bounds__(kThreads) pixel_lattice_points_fast(PixelPointsArgs a) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t n_batches = (a.n_pixels + 31) >> 5;
+  uint64_t b0, b1;
+  warp_range(n_batches, b0, b1);
+  // x / d = umulhi(x, floor(2^64 / d) + 1) exactly for x < 2^32 and d > 1
+  const uint64_t mag_s = ~0ull / a.s + 1;  // s >= 4
+  const uint64_t mag_spp = a.spp > 1 ? ~0ull / a.spp + 1 : 0;
+  const uint32_t chunks_per_pixel = a.spp * (a.s >> 2);
+  for (uint64_t b = b0; b < b1; ++b) {
+    const uint64_t first = b << 5;  // batch's first pixel, relative to pixel_begin
+    const uint64_t left = a.n_pixels - first;
+    const uint32_t npx = left < 32 ? (uint32_t)left : 32u;
+    uint32_t sh = 0;
+    if (lane < npx) {
+      const uint64_t p = a.pixel_begin + first + lane;
+      sh = pixel_shift((uint32_t)(p % a.width), (uint32_t)(p / a.width), a.grid_log2);
+    }
+    const uint32_t chunks = npx * chunks_per_pixel;
+    const uint64_t off0 = first * a.spp * a.s;  // element offset of the batch
+    for (uint32_t c0 = 0; c0 < chunks; c0 += 32) {  // same trip count in every lane
+      const uint32_t c = c0 + lane;
+      const uint32_t e = 4u * c;  // element within the batch, < 2^32
+      const uint32_t row = (uint32_t)__umul64hi(e, mag_s);
+      const uint32_t j = e - row * a.s;
+      const uint32_t pl = a.spp > 1 ? (uint32_t)__umul64hi(row, mag_spp) : row;
+      const uint32_t smp = row - pl * a.spp;
+      const uint32_t shift = __shfl_sync(0xffffffffu, sh, pl & 31u);
+      if (c < chunks) {
+        const uint32_t base = __brev(smp) + shift;
+        const uint32_t v[4] = {base * (__ldg(a.g + j) | 1u), base * (__ldg(a.g + j + 1) | 1u),
+                               base * (__ldg(a.g + j + 2) | 1u), base * (__ldg(a.g + j + 3) | 1u)};
+        store4(a.out_u32, a.out_f32, off0 + e, v);
+      }
+    }
+  }
+}
+
 
 // Pixel-shifted rank-1 lattice (Sec. 3): one thread per (pixel, sample) row;
 // row r holds sample r % spp of pixel pixel_begin + r / spp.
@@ -583,6 +638,18 @@ cudaError_t launch_halton_points(const HaltonArgs& p, cudaStream_t stream) {
 
 cudaError_t launch_pixel_lattice_points(const PixelPointsArgs& a, cudaStream_t stream) {
   const DeviceInfo& dev = device_info();
+  if ((a.s & 3u) == 0 && (uint64_t)32 * a.spp * a.s <= (1ull << 31) && aligned16(a.out_u32) &&
+      aligned16(a.out_f32)) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pixel_lattice_points_fast, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    uint64_t blocks = (uint64_t)dev.sm_count * (per_sm < 1 ? 1 : per_sm);
+    const uint64_t need = (((a.n_pixels + 31) >> 5) + kThreads / 32 - 1) / (kThreads / 32);
+    if (need < blocks) blocks = need;
+    if (blocks < 1) blocks = 1;
+    pixel_lattice_points_fast<<<(unsigned)blocks, kThreads, 0, stream>>>(a);
+    return cudaGetLastError();
+  }
   uint64_t blocks = (a.n_pixels * a.spp + kThreads - 1) / kThreads;
   const uint64_t cap = (uint64_t)dev.sm_count * 8;
   if (blocks > cap) blocks = cap;

@@ -18,7 +18,10 @@ def B():
 
 
 @pytest.mark.parametrize("width,height,spp,s,begin,n", [(37, 23, 17, 6, 0, 37 * 23), (64, 64, 5, 3, 100, 700),
-                                                      (1920, 1080, 2, 16, 1920 * 1080 - 300, 300)])
+                                                      (1920, 1080, 2, 16, 1920 * 1080 - 300, 300),
+                                                      # coalesced path (s % 4 == 0): ragged batches, spp = 1
+                                                      (37, 23, 1, 4, 5, 37 * 23 - 5), (100, 70, 16, 32, 1234, 3001),
+                                                      (256, 256, 3, 8, 0, 65536), (1920, 1080, 4, 12, 777, 4099)])
 def test_pixel_lattice_points_bit_exact(B, oracle, width, height, spp, s, begin, n):
     g = inputs.lattice_generator(s, seed=13)
     u = torch.empty((n * spp, s), dtype=torch.int32, device="cuda")
