@@ -23,7 +23,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qmc_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-SOURCE_SOBOL, SOURCE_LATTICE, SOURCE_PIXEL_LATTICE = 0, 1, 2
+SOURCE_SOBOL, SOURCE_LATTICE, SOURCE_PIXEL_LATTICE, SOURCE_RANDOM_LATTICE = 0, 1, 2, 3
+RLAT_HASH, RLAT_LFSR = 0, 1
 SCRAMBLE_NONE, SCRAMBLE_XOR, SCRAMBLE_NESTED = 0, 1, 2
 F_BILINEAR2D, F_GENZ_PRODUCT_PEAK, F_GENZ_OSCILLATORY, F_GAUSSMIX4_6D = 0, 1, 2, 3
 
@@ -62,6 +63,12 @@ def lib() -> ctypes.CDLL:
             "qo_partition_index": (u64, [u32, u32, u64, u64]),
             "qo_sobol_points_partitioned": (None, [P, u32, u32, u32, u64, u64, u64, u32, P, P, P]),
             "qo_halton_u64": (u32, [u64, u32, u32, u32]),
+            "qo_splitmix64": (u64, [u64, u64]),
+            "qo_rlat_hash": (u32, [u32, u32, u32, u32, u32]),
+            "qo_lfsr_step": (u32, [u32]),
+            "qo_rlat_generator": (u32, [u32, u32, u32, u32, u32, u32]),
+            "qo_random_lattice_u32": (u32, [u32, u32, u32, u32, u32, u32, u32]),
+            "qo_random_lattice_points": (None, [u32, u32, u32, u32, u32, u64, u64, u32, P]),
             "qo_halton_points_partitioned": (None, [u32, u32, P, u32, u64, u64, u64, P]),
             "qo_sobol_u32": (u32, [P, u32]),
             "qo_nested_scramble": (u32, [u32, u32]),
@@ -231,6 +238,27 @@ def lattice_points(g, shift, begin, count, backward=False, threads=None):
 
     _chunked(count, threads, run)
     return u, f
+
+
+def random_lattice_points(kind, seed, R, s, width, n_pixels, spp, pixel_begin=0, threads=None):
+    """u32 [n_pixels * spp][s]: per-pixel random lattice samples (Alg. 4), R
+    superimposed instances."""
+    out = np.empty((n_pixels * spp, s), np.uint32)
+
+    def run(q0, n):
+        n = min(n, n_pixels - q0)
+        lib().qo_random_lattice_points(kind, seed, R, s, width, pixel_begin + q0, n, spp,
+                                       out[q0 * spp:].ctypes.data)
+
+    if n_pixels:
+        _chunked(n_pixels, threads, run)
+    return out
+
+
+def random_lattice_seeds(seed, width, n, pixel_begin=0):
+    """[n][3] per-integral (seed, px, py) rows for integrate(SOURCE_RANDOM_LATTICE)."""
+    p = np.arange(pixel_begin, pixel_begin + n, dtype=np.uint64)
+    return np.stack([np.full(n, seed, np.uint64), p % width, p // width], axis=1).astype(np.uint32)
 
 
 def integrate(source, integrand, s, counts, theta, *, C=None, g=None, scramble=0, seeds=None,

@@ -24,7 +24,15 @@
  * (up to 64-column) matrices against the Pascal closed form and Niederreiter's
  * rank criterion for the t-value of the first 2^m points, m up to 64; the
  * partitioning of Sec. 2.5.1 against brute-force selection by the extra
- * coordinate and the (t, s-1)-sequence property of each element's points.
+ * coordinate and the (t, s-1)-sequence property of each element's points;
+ * SplitMix64 against its published outputs, the LFSR against polynomial
+ * arithmetic and a primitivity test, the per-pixel random lattice against
+ * exact rational arithmetic and the Latin hypercube property of odd
+ * generators.
+ *
+ * Parity unpinned beyond those properties: the particular values of
+ * qo_rlat_hash (Alg. 4's hash_value is not defined by the paper; this
+ * library defines it from SplitMix64, whose outputs are pinned).
  *
  * Parity unpinned: the exact output bits of qo_nested_scramble.  The paper
  * names Owen scrambling but prints no algorithm; the hash below is this
@@ -38,7 +46,9 @@
 
 #define QO_EXPORT __attribute__((visibility("default")))
 
-enum { QO_SOURCE_SOBOL = 0, QO_SOURCE_LATTICE = 1, QO_SOURCE_PIXEL_LATTICE = 2 };
+enum { QO_SOURCE_SOBOL = 0, QO_SOURCE_LATTICE = 1, QO_SOURCE_PIXEL_LATTICE = 2,
+       QO_SOURCE_RANDOM_LATTICE = 3 };
+enum { QO_RLAT_HASH = 0, QO_RLAT_LFSR = 1 };
 enum { QO_SCRAMBLE_NONE = 0, QO_SCRAMBLE_XOR = 1, QO_SCRAMBLE_NESTED = 2 };
 enum {
     QO_F_BILINEAR2D = 0,
@@ -463,6 +473,89 @@ QO_EXPORT uint32_t qo_pixel_lattice_u32(uint32_t i, uint32_t g, uint32_t shift)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sec. 2.4.2 and Alg. 4: a random rank-1 lattice sequence per pixel; Sec. 3: */
+/* superimposed instances.                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number
+ * generators", 2014): output n (n = 0, 1, ..) of the generator whose state
+ * starts at z0 is mix(z0 + (n + 1) gamma), gamma = 0x9E3779B97F4A7C15, where
+ * mix applies z ^= z >> 30, z *= 0xBF58476D1CE4E5B9, z ^= z >> 27,
+ * z *= 0x94D049BB133111EB, z ^= z >> 31 (arithmetic mod 2^64). */
+QO_EXPORT uint64_t qo_splitmix64(uint64_t z0, uint64_t n)
+{
+    uint64_t z = z0 + (n + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Alg. 4's hash_value, which the paper leaves open, defined here as the high
+ * 32 bits of SplitMix64 output number
+ *   (py << 44) | (px << 24) | (k << 20) | j
+ * of the stream seeded with `seed`: one counter per pixel (px, py < 2^20),
+ * superimposed instance k < 16 and dimension j < 2^20. */
+QO_EXPORT uint32_t qo_rlat_hash(uint32_t seed, uint32_t k, uint32_t j, uint32_t px, uint32_t py)
+{
+    uint64_t counter = ((uint64_t)py << 44) | ((uint64_t)px << 24) | ((uint64_t)k << 20) | j;
+    return (uint32_t)(qo_splitmix64(seed, counter) >> 32);
+}
+
+/* One step of the linear feedback shift register of Sec. 2.4.2: the state is
+ * a polynomial of degree < 32 over GF(2) (bit k = coefficient of x^k),
+ * multiplied by x modulo the primitive polynomial x^32 + x^22 + x^2 + x + 1.
+ * A nonzero state runs through all 2^32 - 1 nonzero states. */
+QO_EXPORT uint32_t qo_lfsr_step(uint32_t state)
+{
+    uint64_t v = (uint64_t)state << 1;           /* multiply by x */
+    if ((v >> 32) & 1u) v ^= 0x100400007ull;     /* reduce: subtract (xor) the polynomial */
+    return (uint32_t)v;
+}
+
+/* Component j of the generator vector of instance k of pixel (px, py):
+ *   HASH (Alg. 4): hash_value | 1;
+ *   LFSR (Sec. 2.4.2): g_j = 2 xi_j + 1 mod 2^32 with xi_0 the instance's seed
+ *   state (the hash at the reserved dimension 2^20 - 1, replaced by 1 if 0) and
+ *   xi_{j+1} one LFSR step after xi_j, so one seed defines the whole vector. */
+QO_EXPORT uint32_t qo_rlat_generator(uint32_t kind, uint32_t seed, uint32_t k, uint32_t j,
+                                     uint32_t px, uint32_t py)
+{
+    if (kind == QO_RLAT_HASH) return qo_rlat_hash(seed, k, j, px, py) | 1u;
+    uint32_t xi = qo_rlat_hash(seed, k, (1u << 20) - 1u, px, py);
+    if (xi == 0) xi = 1;
+    for (uint32_t t = 0; t < j; ++t) xi = qo_lfsr_step(xi);
+    return (uint32_t)(((uint64_t)xi * 2u + 1u) & 0xFFFFFFFFull);
+}
+
+/* Sample t of pixel (px, py), dimension j, with R superimposed instances
+ * (Sec. 3): instance k = t mod R takes its samples i = t div R = 0, 1, ..,
+ * enumerated backwards as Alg. 4 does, x = phi_2(2^32 - 1 - i) g_j mod 1, in
+ * units of 2^-32. */
+QO_EXPORT uint32_t qo_random_lattice_u32(uint32_t kind, uint32_t seed, uint32_t R, uint32_t t,
+                                         uint32_t j, uint32_t px, uint32_t py)
+{
+    uint32_t k = t % R, i = t / R;
+    uint64_t prod = (uint64_t)qo_bit_reverse(0xFFFFFFFFu - i) *
+                    qo_rlat_generator(kind, seed, k, j, px, py);
+    return (uint32_t)(prod & 0xFFFFFFFFull);
+}
+
+/* Materialised samples: row q*spp + t holds sample t of pixel pixel_begin + q
+ * of a row-major image `width` pixels wide, s dimensions. */
+QO_EXPORT void qo_random_lattice_points(uint32_t kind, uint32_t seed, uint32_t R, uint32_t s,
+                                        uint32_t width, uint64_t pixel_begin, uint64_t n_pixels,
+                                        uint32_t spp, uint32_t* out_u32)
+{
+    for (uint64_t q = 0; q < n_pixels; ++q) {
+        uint64_t p = pixel_begin + q;
+        uint32_t px = (uint32_t)(p % width), py = (uint32_t)(p / width);
+        for (uint32_t t = 0; t < spp; ++t)
+            for (uint32_t j = 0; j < s; ++j)
+                out_u32[(q * spp + t) * s + j] = qo_random_lattice_u32(kind, seed, R, t, j, px, py);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sec. 2.6: test integrands with analytic integrals, in fp64.               */
 /* Parameters are fp32 values promoted exactly to double.                    */
 /* ------------------------------------------------------------------------ */
@@ -545,7 +638,9 @@ static void neu_add(neumaier* a, double v)
  *   source 1 (lattice): x_i = lattice point i of g[s] shifted by seeds[s]
  *     (the Cranley-Patterson rotation), backward when scramble & 1;
  *   source 2 (pixel-shifted lattice, Eq. (PixelShiftedR1LS)): seeds[0] holds
- *     the pixel's shift floor(phi_3(h) 2^32) from qo_pixel_shift.
+ *     the pixel's shift floor(phi_3(h) 2^32) from qo_pixel_shift;
+ *   source 3 (random lattice per pixel, Alg. 4 / Sec. 3): seeds[0..2] hold
+ *     (seed, px, py), scramble = kind + 256 R (R superimposed instances).
  * Coordinates are the fp32 values of the float mapping, promoted to fp64.
  * Outputs (each may be NULL except est): est = estimate; mass = (1/n) sum |f|;
  * grad[16] = (1/n) sum df/dtheta and grad_mass[16] = (1/n) sum |df/dtheta|
@@ -559,7 +654,8 @@ QO_EXPORT int qo_integrate_one(uint32_t source, uint32_t integrand, uint32_t s,
     if (s == 0 || s > 32) return -1;
     if (integrand == QO_F_BILINEAR2D && s != 2) return -1;
     if (integrand == QO_F_GAUSSMIX4_6D && s != 6) return -1;
-    if (integrand > QO_F_GAUSSMIX4_6D || source > QO_SOURCE_PIXEL_LATTICE) return -1;
+    if (integrand > QO_F_GAUSSMIX4_6D || source > QO_SOURCE_RANDOM_LATTICE) return -1;
+    if (source == QO_SOURCE_RANDOM_LATTICE && (!seeds || (scramble >> 8) == 0)) return -1;
 
     neumaier sum = {0, 0}, abs_sum = {0, 0};
     neumaier gsum[16], gabs[16];
@@ -573,8 +669,11 @@ QO_EXPORT int qo_integrate_one(uint32_t source, uint32_t integrand, uint32_t s,
                 v = randomise_sobol(qo_sobol_u32(C + 32 * j, i), scramble, seeds ? seeds[j] : 0u);
             else if (source == QO_SOURCE_LATTICE)
                 v = qo_lattice_u32(i, g[j], seeds ? seeds[j] : 0u, scramble & 1u);
-            else  /* pixel-shifted lattice: seeds[0] is the pixel's shift (qo_pixel_shift) */
+            else if (source == QO_SOURCE_PIXEL_LATTICE)  /* seeds[0]: the pixel's shift */
                 v = qo_pixel_lattice_u32(i, g[j], seeds ? seeds[0] : 0u);
+            else
+                v = qo_random_lattice_u32(scramble & 0xFFu, seeds[0], scramble >> 8, i, j,
+                                          seeds[1], seeds[2]);
             x[j] = (double)qo_map_u32_to_unifloat(v);
         }
         double f;
