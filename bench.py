@@ -402,8 +402,9 @@ def bench_points(dev, steps, warmup, small, sm_mhz):
     u32 + fp32, 8 B written per coordinate; 2^20 rows when small): the 32-bit
     Sobol' headline kernel again, Sobol' with 64-bit indices at 2^40 (Alg. 3),
     one element of a partitioned Sobol' sequence (Sec. 2.5.1), the shifted
-    rank-1 lattice, Halton (Faure) and the pixel-shifted lattice (2^20 pixels x
-    16 samples).  Each against the measured copy bandwidth."""
+    rank-1 lattice, Halton (Faure), the pixel-shifted lattice and the per-pixel
+    random lattices with 4 superimposed instances (2^20 pixels x 16 samples).
+    Each against the measured copy bandwidth."""
     import torch
 
     from paper_2307_15584_gb300 import binding as B
@@ -427,6 +428,12 @@ def bench_points(dev, steps, warmup, small, sm_mhz):
         "halton_faure": lambda: B.qmc_halton_points(s, B.HALTON_FAURE, None, 0, n, u, f),
         "pixel_lattice_16spp": lambda: B.qmc_pixel_lattice_points(g, s, 1024, n // 16 // 1024 or 1, 0,
                                                                    n // 16, 16, u, f),
+        "random_lattice_hash_x4_16spp": lambda: B.qmc_random_lattice_points(B.RLAT_HASH, 7, 4, s, 1024,
+                                                                            n // 16 // 1024 or 1, 0, n // 16, 16,
+                                                                            u, f),
+        "random_lattice_lfsr_x4_16spp": lambda: B.qmc_random_lattice_points(B.RLAT_LFSR, 7, 4, s, 1024,
+                                                                            n // 16 // 1024 or 1, 0, n // 16, 16,
+                                                                            u, f),
     }
     res = {"rows": n, "s": s, "bytes_per_launch": n * s * 8}
     for name, fn in runs.items():

@@ -65,14 +65,24 @@ typedef enum qmc_scramble {
 typedef enum qmc_source {
     QMC_SOURCE_SOBOL = 0,         /* digital (t,s)-sequence in base 2, Eq. (ts) */
     QMC_SOURCE_LATTICE = 1,       /* rank-1 lattice sequence in base 2, Eq. (R1LS) */
-    QMC_SOURCE_PIXEL_LATTICE = 2  /* pixel-shifted rank-1 lattice, Eq. (PixelShiftedR1LS):
+    QMC_SOURCE_PIXEL_LATTICE = 2, /* pixel-shifted rank-1 lattice, Eq. (PixelShiftedR1LS):
                                      integral p is pixel (x, y) = (p % image_width, p / image_width);
                                      sample i = (phi_2(i) + phi_3(h)) g mod 1 with h the pixel's
                                      position along the Hilbert curve of the smallest 2^k x 2^k
                                      grid covering the image (computed in integers: floor(phi_3
                                      2^32) is added to phi_2(i) 2^32 mod 2^32, then multiplied
                                      by g mod 2^32) */
+    QMC_SOURCE_RANDOM_LATTICE = 3 /* a random rank-1 lattice sequence per pixel (Alg. 4, Sec. 3):
+                                     integral p is pixel (x, y) as for PIXEL_LATTICE; randomize =
+                                     kind | (R << 8) (qmc_rlat_kind; R in {1,2,4,8,16} superimposed
+                                     instances); d_seeds[0] = the seed; see qmc_random_lattice_points */
 } qmc_source;
+
+/* Generator vectors of the random rank-1 lattices (Sec. 2.4.2). */
+typedef enum qmc_rlat_kind {
+    QMC_RLAT_HASH = 0,  /* g_j = hash_value(j, pixel, instance) | 1 (Alg. 4) */
+    QMC_RLAT_LFSR = 1   /* g_j = 2 xi_j + 1, xi_j the LFSR state after j steps from a per-pixel seed */
+} qmc_rlat_kind;
 
 /* Integrands with closed-form integrals (Sec. 2.6 recommends such test
  * functions).  theta layouts are per integral, fp32:
@@ -98,13 +108,15 @@ typedef struct qmc_problem {
     uint32_t source;             /* qmc_source */
     uint32_t integrand;          /* qmc_integrand */
     uint32_t s;                  /* dimension of the points = of the integrand */
-    uint32_t randomize;          /* SOBOL: qmc_scramble; LATTICE: 0 or QMC_LATTICE_BACKWARD */
+    uint32_t randomize;          /* SOBOL: qmc_scramble; LATTICE: 0 or QMC_LATTICE_BACKWARD;
+                                    RANDOM_LATTICE: kind | (instances << 8) */
     const uint32_t* d_matrices;  /* SOBOL: [s][32] generator columns (see qmc_sobol_points) */
     const uint32_t* d_g;         /* LATTICE, PIXEL_LATTICE: [s] generator words, low bit forced
                                     to 1 (PIXEL_LATTICE takes no seeds and no randomize flags) */
     const uint32_t* d_seeds;     /* SOBOL: scramble seeds; LATTICE: Cranley-Patterson shifts
                                     (units of 2^-32).  [s], or [n_integrals][s] when
-                                    seeds_per_integral = 1.  NULL: no randomisation/shift. */
+                                    seeds_per_integral = 1.  NULL: no randomisation/shift.
+                                    RANDOM_LATTICE: [1], the seed of hash_value (required). */
     uint32_t seeds_per_integral; /* 0 or 1 */
     uint32_t chunk;              /* samples per work item: a power of two in [32, 8192];
                                     0 = the tuned value for this problem class, else 4096 */
@@ -113,8 +125,9 @@ typedef struct qmc_problem {
                                     host does not pass counts to qmc_integrate_workspace_bytes */
     uint32_t with_gradient;      /* 1: size the workspace for qmc_integrate_backward and
                                     qmc_integrate_fwd_bwd (17 partial sums per work item) */
-    uint32_t image_width;        /* PIXEL_LATTICE: pixels per image row (>= 1); the image has
-                                    ceil(n_integrals / image_width) rows.  Ignored otherwise. */
+    uint32_t image_width;        /* PIXEL_LATTICE, RANDOM_LATTICE: pixels per image row (>= 1);
+                                    the image has ceil(n_integrals / image_width) rows (both
+                                    sides at most 2^20 for RANDOM_LATTICE).  Ignored otherwise. */
 } qmc_problem;
 
 /* ABI revision of this header (bumped on any incompatible change). */
@@ -266,6 +279,35 @@ QMC_API qmc_status qmc_halton_points_partitioned(uint32_t s, uint32_t mode,
                                                  uint64_t p, uint64_t j_begin, uint64_t count,
                                                  uint32_t* d_out_u32, float* d_out_f32,
                                                  qmc_stream_t stream);
+
+/*
+ * Materialised per-pixel random rank-1 lattice samples (Alg. 4, Sec. 2.4.2,
+ * Sec. 3): every pixel (x, y) of a row-major image_width x image_height image
+ * draws its own generator vectors g^(k), k < instances, and sample t of the
+ * pixel is
+ *   x_j(t) = phi_2(2^32 - 1 - i) g_j^(k) mod 1,  k = t mod R, i = t div R
+ * (backwards, so that no pixel starts at the common origin; R superimposed
+ * instances hide the rare bad generator vector).  Generator components:
+ *   QMC_RLAT_HASH  g_j = hash_value(j) | 1, hash_value = the high 32 bits of
+ *                  SplitMix64 output c = y 2^44 + x 2^24 + k 2^20 + j of the
+ *                  stream seeded with `seed` (Steele, Lea, Flood 2014)
+ *   QMC_RLAT_LFSR  g_j = 2 xi_j + 1 mod 2^32: xi_0 = hash_value at the reserved
+ *                  dimension 2^20 - 1 (1 if that is 0), xi_{j+1} = xi_j times x
+ *                  modulo x^32 + x^22 + x^2 + x + 1 over GF(2)
+ *   kind           qmc_rlat_kind
+ *   instances      R in {1, 2, 4, 8, 16}
+ *   s              1 <= s <= 1024
+ *   image_width, image_height   1 .. 2^20 each
+ *   pixel_begin, n_pixels   pixels pixel_begin .. pixel_begin+n_pixels-1 of the
+ *                  image (QMC_ERR_RANGE beyond it); spp >= 1 samples each
+ *   outputs        [n_pixels * spp][s]: row q*spp + t is sample t of pixel
+ *                  pixel_begin + q; u32 (units of 2^-32) and/or fp32
+ * Other conventions as for qmc_sobol_points (alignment, count 0 no-op).
+ */
+QMC_API qmc_status qmc_random_lattice_points(uint32_t kind, uint32_t seed, uint32_t instances, uint32_t s,
+                                             uint32_t image_width, uint32_t image_height,
+                                             uint64_t pixel_begin, uint64_t n_pixels, uint32_t spp,
+                                             uint32_t* d_out_u32, float* d_out_f32, qmc_stream_t stream);
 
 /*
  * Materialised pixel-shifted rank-1 lattice samples (Sec. 3, Eq.

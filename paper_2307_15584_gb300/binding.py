@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "QMC_OK", 1: "QMC_ERR_INVALID_ARG", 2: "QMC_ERR_RANGE", 3: "Q
                 4: "QMC_ERR_CUDA", 5: "QMC_ERR_TIMEOUT", 6: "QMC_ERR_UNSUPPORTED", 7: "QMC_ERR_WORKSPACE"}
 SCRAMBLE_NONE, SCRAMBLE_XOR, SCRAMBLE_NESTED = 0, 1, 2
 LATTICE_BACKWARD = 1
-SOURCE_SOBOL, SOURCE_LATTICE, SOURCE_PIXEL_LATTICE = 0, 1, 2
+SOURCE_SOBOL, SOURCE_LATTICE, SOURCE_PIXEL_LATTICE, SOURCE_RANDOM_LATTICE = 0, 1, 2, 3
+RLAT_HASH, RLAT_LFSR = 0, 1
 F_BILINEAR2D, F_GENZ_PRODUCT_PEAK, F_GENZ_OSCILLATORY, F_GAUSSMIX4_6D = 0, 1, 2, 3
 
 EXPORTED = ["qmc_abi_version", "qmc_status_string", "qmc_sobol_matrices", "qmc_sobol_points",
@@ -37,7 +38,8 @@ EXPORTED = ["qmc_abi_version", "qmc_status_string", "qmc_sobol_matrices", "qmc_s
             "qmc_read_device_error", "qmc_integrate_static", "qmc_tune_integrate", "qmc_tune_clear",
             "qmc_graph_begin", "qmc_graph_end", "qmc_graph_launch", "qmc_graph_destroy",
             "qmc_pixel_lattice_points", "qmc_halton_points", "qmc_sobol_matrices_wide",
-            "qmc_sobol_points_wide", "qmc_sobol_points_partitioned", "qmc_halton_points_partitioned"]
+            "qmc_sobol_points_wide", "qmc_sobol_points_partitioned", "qmc_halton_points_partitioned",
+            "qmc_random_lattice_points"]
 HALTON_PLAIN, HALTON_FAURE, HALTON_LINEAR = 0, 1, 2
 
 
@@ -70,6 +72,8 @@ _sigs = {
                                                 _P, _P, _P]),
     "qmc_halton_points": (ctypes.c_int, [c_uint32, c_uint32, _P, c_uint64, c_uint64, _P, _P, _P]),
     "qmc_sobol_matrices_wide": (ctypes.c_int, [c_uint32, c_uint32, _P, _P]),
+    "qmc_random_lattice_points": (ctypes.c_int, [c_uint32, c_uint32, c_uint32, c_uint32, c_uint32, c_uint32,
+                                                 c_uint64, c_uint64, c_uint32, _P, _P, _P]),
     "qmc_sobol_points_wide": (ctypes.c_int, [_P, c_uint32, c_uint32, c_uint64, c_uint64, c_uint32, _P, _P, _P,
                                              _P]),
     "qmc_sobol_points_partitioned": (ctypes.c_int, [_P, c_uint32, c_uint32, c_uint32, c_uint64, c_uint64,
@@ -187,6 +191,18 @@ def qmc_halton_points(s, mode, multipliers, index_begin, count, out_u32, out_f32
     m = None if multipliers is None else np.ascontiguousarray(multipliers, dtype=np.uint32)
     _check(_lib.qmc_halton_points(s, mode, None if m is None else m.ctypes.data, index_begin, count,
                                   _dev(out_u32), _dev(out_f32), _stream(stream)), "qmc_halton_points")
+
+
+def qmc_random_lattice_points(kind, seed, instances, s, image_width, image_height, pixel_begin, n_pixels, spp,
+                              out_u32, out_f32, stream=None):
+    _check(_lib.qmc_random_lattice_points(kind, seed, instances, s, image_width, image_height, pixel_begin,
+                                          n_pixels, spp, _dev(out_u32), _dev(out_f32), _stream(stream)),
+           "qmc_random_lattice_points")
+
+
+def rlat_randomize(kind: int, instances: int) -> int:
+    """qmc_problem.randomize of QMC_SOURCE_RANDOM_LATTICE."""
+    return kind | (instances << 8)
 
 
 def qmc_halton_points_partitioned(s, mode, multipliers, q, p, j_begin, count, out_u32, out_f32, stream=None):

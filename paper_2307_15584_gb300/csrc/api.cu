@@ -387,9 +387,15 @@ uint32_t ilog2(uint32_t v) {
   return l;
 }
 
+// kind (QMC_RLAT_HASH or _LFSR) in the low byte, 1, 2, 4, 8 or 16 instances above.
+bool rlat_randomize_ok(uint32_t r) {
+  const uint32_t kind = r & 0xFFu, inst = r >> 8;
+  return kind <= QMC_RLAT_LFSR && inst >= 1 && inst <= 16 && (inst & (inst - 1)) == 0;
+}
+
 qmc_status validate_problem(const qmc_problem* p, bool need_source) {
   if (!p) return QMC_ERR_INVALID_ARG;
-  if (p->integrand > QMC_F_GAUSSMIX4_6D || p->source > QMC_SOURCE_PIXEL_LATTICE) return QMC_ERR_INVALID_ARG;
+  if (p->integrand > QMC_F_GAUSSMIX4_6D || p->source > QMC_SOURCE_RANDOM_LATTICE) return QMC_ERR_INVALID_ARG;
   const uint32_t s = p->s;
   if (p->integrand == QMC_F_BILINEAR2D && s != 2) return QMC_ERR_INVALID_ARG;
   if (p->integrand == QMC_F_GAUSSMIX4_6D && s != 6) return QMC_ERR_INVALID_ARG;
@@ -406,8 +412,11 @@ qmc_status validate_problem(const qmc_problem* p, bool need_source) {
       if (p->randomize != QMC_SCRAMBLE_NONE && !p->d_seeds) return QMC_ERR_INVALID_ARG;
     } else if (p->source == QMC_SOURCE_LATTICE) {
       if (!p->d_g || (p->randomize & ~QMC_LATTICE_BACKWARD)) return QMC_ERR_INVALID_ARG;
-    } else {  // pixel-shifted lattice: generator words and an image width, nothing else
+    } else if (p->source == QMC_SOURCE_PIXEL_LATTICE) {  // generator words and an image width
       if (!p->d_g || p->randomize != 0 || p->image_width == 0) return QMC_ERR_INVALID_ARG;
+    } else {  // random lattice per pixel: kind | (instances << 8), the seed, an image width
+      if (!rlat_randomize_ok(p->randomize) || !p->d_seeds) return QMC_ERR_INVALID_ARG;
+      if (p->image_width == 0 || p->image_width > (1u << 20)) return QMC_ERR_INVALID_ARG;
     }
   }
   return QMC_OK;
@@ -462,6 +471,11 @@ qmc_status prepare(const qmc_problem* p, uint32_t n, const uint32_t* d_counts, c
     a.image_width = p->image_width;
     a.grid_log2 = image_grid_log2(n, p->image_width);
   }
+  if (p->source == QMC_SOURCE_RANDOM_LATTICE) {
+    if (((uint64_t)n + p->image_width - 1) / p->image_width > (1u << 20)) return QMC_ERR_INVALID_ARG;
+    a.image_width = p->image_width;
+    a.rlat_log2 = ilog2(p->randomize >> 8);
+  }
   // work split: explicit values, else the tuner's record for this problem class, else defaults
   uint32_t chunk = p->chunk, block = p->block;
   if (chunk == 0 || block == 0) {
@@ -494,6 +508,33 @@ qmc_status prepare(const qmc_problem* p, uint32_t n, const uint32_t* d_counts, c
 qmc_status finish(cudaError_t e) { return e == cudaSuccess ? QMC_OK : QMC_ERR_CUDA; }
 
 }  // namespace
+
+qmc_status qmc_random_lattice_points(uint32_t kind, uint32_t seed, uint32_t instances, uint32_t s,
+                                     uint32_t image_width, uint32_t image_height, uint64_t pixel_begin,
+                                     uint64_t n_pixels, uint32_t spp, uint32_t* d_out_u32, float* d_out_f32,
+                                     qmc_stream_t stream) {
+  if (!rlat_randomize_ok(kind | (instances << 8)) || instances > 16) return QMC_ERR_INVALID_ARG;
+  if (s == 0 || s > 1024 || spp == 0) return QMC_ERR_INVALID_ARG;
+  if (image_width == 0 || image_height == 0 || image_width > (1u << 20) || image_height > (1u << 20))
+    return QMC_ERR_INVALID_ARG;
+  const uint64_t pixels = (uint64_t)image_width * image_height;
+  if (pixel_begin > pixels || n_pixels > pixels - pixel_begin) return QMC_ERR_RANGE;
+  if (n_pixels == 0) return QMC_OK;
+  const qmc_status st = check_outputs(s, n_pixels * spp, d_out_u32, d_out_f32);
+  if (st != QMC_OK) return st;
+  RandomPointsArgs a{};
+  a.out_u32 = d_out_u32;
+  a.out_f32 = d_out_f32;
+  a.pixel_begin = pixel_begin;
+  a.n_pixels = n_pixels;
+  a.spp = spp;
+  a.s = s;
+  a.width = image_width;
+  a.kind = kind;
+  a.seed = seed;
+  a.r_log2 = ilog2(instances);
+  return launch_random_lattice_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
 
 size_t qmc_integrate_workspace_bytes(const qmc_problem* p, uint32_t n_integrals,
                                      const uint32_t* h_counts) {

@@ -289,6 +289,48 @@ struct PixelLatticeSource {
   }
 };
 
+// Random rank-1 lattice per pixel (Alg. 4, Sec. 3): integral p is pixel
+// (p % width, p / width).  Sample t of an item lives in lane t mod 32 (items
+// start at multiples of the chunk, a multiple of 32), so with R | 32 instances
+// every lane keeps one instance k = lane mod R for the whole item and derives
+// its generator vector once per item; point i = t div R of that instance is
+// phi_2(2^32 - 1 - i) g mod 1.
+template <int S, int KIND>
+struct RandomLatticeSource {
+  uint32_t start, seed, r_log2;
+  uint32_t g[S];
+
+  static size_t smem_bytes(uint32_t, uint32_t) { return 0; }
+
+  __device__ void kernel_setup(const IntegrateArgs& a, uint32_t*) {
+    seed = __ldg(a.seeds);
+    r_log2 = a.rlat_log2;
+  }
+
+  __device__ void item_setup(const IntegrateArgs& a, uint32_t p, uint32_t st) {
+    start = st;
+    const uint32_t px = p % a.image_width, py = p / a.image_width;
+    const uint32_t k = threadIdx.x & ((1u << r_log2) - 1u);
+    if (KIND == QMC_RLAT_HASH) {
+#pragma unroll
+      for (int j = 0; j < S; ++j) g[j] = rlat_hash(seed, k, j, px, py) | 1u;
+    } else {
+      uint32_t xi = rlat_lfsr_seed(seed, k, px, py);
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        g[j] = 2u * xi + 1u;
+        xi = lfsr_step(xi);
+      }
+    }
+  }
+
+  __device__ __forceinline__ void point(uint32_t, uint32_t il, bool, float* x) const {
+    const uint32_t phi = __brev(~((start + il) >> r_log2));
+#pragma unroll
+    for (int j = 0; j < S; ++j) x[j] = unifloat_x2p32(phi * g[j]);
+  }
+};
+
 // Unfused comparison path: coordinates read back from HBM.
 template <int S>
 struct PointsSource {
@@ -796,6 +838,10 @@ cudaError_t launch_main_fn(const IntegrateArgs& a, uint32_t block, cudaStream_t 
   constexpr int S = Integrand<FN>::S;
   if (a.points) return launch_main_t<PointsSource<S>, FN, GRAD>(a, block, stream);
   if (a.source == QMC_SOURCE_PIXEL_LATTICE) return launch_main_t<PixelLatticeSource<S>, FN, GRAD>(a, block, stream);
+  if (a.source == QMC_SOURCE_RANDOM_LATTICE)
+    return (a.randomize & 0xFFu) == QMC_RLAT_HASH
+               ? launch_main_t<RandomLatticeSource<S, QMC_RLAT_HASH>, FN, GRAD>(a, block, stream)
+               : launch_main_t<RandomLatticeSource<S, QMC_RLAT_LFSR>, FN, GRAD>(a, block, stream);
   if (a.source == QMC_SOURCE_LATTICE)
     return (a.randomize & QMC_LATTICE_BACKWARD) ? launch_main_t<LatticeSource<S, true>, FN, GRAD>(a, block, stream)
                                                 : launch_main_t<LatticeSource<S, false>, FN, GRAD>(a, block, stream);

@@ -636,6 +636,116 @@ cudaError_t launch_halton_points(const HaltonArgs& p, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+namespace {
+
+// Generator component j of instance k of pixel (px, py), for one chunk of
+// consecutive dimensions j0 .. j0+N-1 (LFSR: stepped from the pixel's seed state).
+template <int KIND, int N>
+__device__ __forceinline__ void rlat_generators(uint32_t seed, uint32_t k, uint32_t j0, uint32_t px,
+                                                uint32_t py, uint32_t (&g)[N]) {
+  if (KIND == QMC_RLAT_HASH) {
+#pragma unroll
+    for (int q = 0; q < N; ++q) g[q] = rlat_hash(seed, k, j0 + q, px, py) | 1u;
+  } else {
+    uint32_t xi = rlat_lfsr_seed(seed, k, px, py);
+    for (uint32_t u = 0; u < j0; ++u) xi = lfsr_step(xi);
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      g[q] = 2u * xi + 1u;
+      xi = lfsr_step(xi);
+    }
+  }
+}
+
+// Coalesced path (s % 4 == 0, 16-byte aligned outputs, 32 spp s <= 2^31): as
+// pixel_lattice_points_fast, a warp takes batches of 32 pixels whose
+// coordinates its lanes hold; each 16-byte chunk (one sample, four consecutive
+// dimensions) derives its four generator components and multiplies.
+template <int KIND>
+__global__ void __launch_bounds__(kThreads) random_lattice_points_fast(RandomPointsArgs a) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t n_batches = (a.n_pixels + 31) >> 5;
+  uint64_t b0, b1;
+  warp_range(n_batches, b0, b1);
+  const uint64_t mag_s = ~0ull / a.s + 1;  // s >= 4
+  const uint64_t mag_spp = a.spp > 1 ? ~0ull / a.spp + 1 : 0;
+  const uint32_t chunks_per_pixel = a.spp * (a.s >> 2);
+  const uint32_t kmask = (1u << a.r_log2) - 1u;
+  for (uint64_t b = b0; b < b1; ++b) {
+    const uint64_t first = b << 5;
+    const uint64_t left = a.n_pixels - first;
+    const uint32_t npx = left < 32 ? (uint32_t)left : 32u;
+    const uint64_t p = a.pixel_begin + first + (lane < npx ? lane : 0u);
+    const uint32_t pxl = (uint32_t)(p % a.width), pyl = (uint32_t)(p / a.width);
+    const uint32_t chunks = npx * chunks_per_pixel;
+    const uint64_t off0 = first * a.spp * a.s;
+    for (uint32_t c0 = 0; c0 < chunks; c0 += 32) {  // same trip count in every lane
+      const uint32_t c = c0 + lane;
+      const uint32_t e = 4u * c;
+      const uint32_t row = (uint32_t)__umul64hi(e, mag_s);
+      const uint32_t j = e - row * a.s;
+      const uint32_t pl = a.spp > 1 ? (uint32_t)__umul64hi(row, mag_spp) : row;
+      const uint32_t t = row - pl * a.spp;
+      const uint32_t px = __shfl_sync(0xffffffffu, pxl, pl & 31u);
+      const uint32_t py = __shfl_sync(0xffffffffu, pyl, pl & 31u);
+      if (c < chunks) {
+        uint32_t g[4];
+        rlat_generators<KIND, 4>(a.seed, t & kmask, j, px, py, g);
+        const uint32_t phi = __brev(~(t >> a.r_log2));  // phi_2(2^32 - 1 - i), Alg. 4
+        const uint32_t v[4] = {phi * g[0], phi * g[1], phi * g[2], phi * g[3]};
+        store4(a.out_u32, a.out_f32, off0 + e, v);
+      }
+    }
+  }
+}
+
+// Generic path: one element per thread.
+template <int KIND>
+__global__ void __launch_bounds__(kThreads) random_lattice_points_generic(RandomPointsArgs a) {
+  const uint64_t total = a.n_pixels * a.spp * a.s;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += stride) {
+    const uint64_t row = f / a.s;
+    const uint32_t j = (uint32_t)(f - row * a.s);
+    const uint64_t q = row / a.spp;
+    const uint32_t t = (uint32_t)(row - q * a.spp);
+    const uint64_t p = a.pixel_begin + q;
+    uint32_t g[1];
+    rlat_generators<KIND, 1>(a.seed, t & ((1u << a.r_log2) - 1u), j, (uint32_t)(p % a.width),
+                             (uint32_t)(p / a.width), g);
+    store1(a.out_u32, a.out_f32, f, __brev(~(t >> a.r_log2)) * g[0]);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_random_lattice_points(const RandomPointsArgs& a, cudaStream_t stream) {
+  const DeviceInfo& dev = device_info();
+  const bool hash = a.kind == QMC_RLAT_HASH;
+  if ((a.s & 3u) == 0 && (uint64_t)32 * a.spp * a.s <= (1ull << 31) && aligned16(a.out_u32) &&
+      aligned16(a.out_f32)) {
+    const auto kernel = hash ? random_lattice_points_fast<QMC_RLAT_HASH> : random_lattice_points_fast<QMC_RLAT_LFSR>;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    uint64_t blocks = (uint64_t)dev.sm_count * (per_sm < 1 ? 1 : per_sm);
+    const uint64_t need = (((a.n_pixels + 31) >> 5) + kThreads / 32 - 1) / (kThreads / 32);
+    if (need < blocks) blocks = need;
+    if (blocks < 1) blocks = 1;
+    kernel<<<(unsigned)blocks, kThreads, 0, stream>>>(a);
+    return cudaGetLastError();
+  }
+  uint64_t blocks = (a.n_pixels * a.spp * a.s + kThreads - 1) / kThreads;
+  const uint64_t cap = (uint64_t)dev.sm_count * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  if (hash)
+    random_lattice_points_generic<QMC_RLAT_HASH><<<(unsigned)blocks, kThreads, 0, stream>>>(a);
+  else
+    random_lattice_points_generic<QMC_RLAT_LFSR><<<(unsigned)blocks, kThreads, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pixel_lattice_points(const PixelPointsArgs& a, cudaStream_t stream) {
   const DeviceInfo& dev = device_info();
   if ((a.s & 3u) == 0 && (uint64_t)32 * a.spp * a.s <= (1ull << 31) && aligned16(a.out_u32) &&

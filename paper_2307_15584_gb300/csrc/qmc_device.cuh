@@ -101,6 +101,35 @@ __device__ __forceinline__ uint32_t pixel_shift(uint32_t px, uint32_t py, uint32
   return radinv3_u32(hilbert_position(px, py, k));
 }
 
+// --- Random rank-1 lattices per pixel (Alg. 4, Sec. 2.4.2) -------------------
+// Alg. 4 names a hash_value of (dimension, pixel) without defining it.  Here it
+// is the high word of SplitMix64 (Steele, Lea, Flood 2014) output number
+// c = py*2^44 + px*2^24 + k*2^20 + j of the stream seeded with `seed`, i.e.
+// the finaliser applied to seed + (c+1) * 0x9E3779B97F4A7C15.
+__device__ __forceinline__ uint32_t rlat_hash(uint32_t seed, uint32_t k, uint32_t j, uint32_t px,
+                                              uint32_t py) {
+  const uint64_t c = ((uint64_t)py << 44) | ((uint64_t)px << 24) | ((uint64_t)k << 20) | j;
+  uint64_t z = (uint64_t)seed + (c + 1ull) * 0x9E3779B97F4A7C15ull;
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (uint32_t)(z >> 32);
+}
+
+// Galois LFSR of Sec. 2.4.2: the state times x modulo x^32 + x^22 + x^2 + x + 1.
+__device__ __forceinline__ uint32_t lfsr_step(uint32_t st) {
+  return (st << 1) ^ (0x00400007u & (0u - (st >> 31)));
+}
+
+// Seed state of the LFSR generator of instance k of a pixel: the hash at the
+// reserved dimension 2^20 - 1 (never zero: 0 maps to 1).
+__device__ __forceinline__ uint32_t rlat_lfsr_seed(uint32_t seed, uint32_t k, uint32_t px, uint32_t py) {
+  const uint32_t x0 = rlat_hash(seed, k, (1u << 20) - 1u, px, py);
+  return x0 ? x0 : 1u;
+}
+
 // ---------------------------------------------------------------------------
 // Compensated fp32 summation (Sec. 2.5.1 names Kahan's algorithm; this is
 // the Neumaier variant, whose error term is exact for either operand order).

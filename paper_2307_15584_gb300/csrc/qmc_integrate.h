@@ -27,6 +27,7 @@ struct IntegrateArgs {
   uint32_t chunk_log2;
   uint32_t image_width;  // pixel-shifted lattice: integral p is pixel (p % width, p / width)
   uint32_t grid_log2;    // ... on the 2^grid_log2 square grid of the Hilbert curve
+  uint32_t rlat_log2;    // random lattice: log2 of the superimposed instances (kind in randomize)
   uint32_t n;
   const uint32_t* counts;
   const float* theta;

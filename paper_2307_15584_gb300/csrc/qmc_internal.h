@@ -53,6 +53,17 @@ struct PixelPointsArgs {
 
 cudaError_t launch_pixel_lattice_points(const PixelPointsArgs& a, cudaStream_t stream);
 
+// Arguments of the per-pixel random lattice points (Alg. 4, Sec. 3).
+struct RandomPointsArgs {
+  uint32_t* out_u32;  // [n_pixels * spp][s] or null
+  float* out_f32;     // [n_pixels * spp][s] or null
+  uint64_t pixel_begin, n_pixels;
+  uint32_t spp, s, width;
+  uint32_t kind, seed, r_log2;  // qmc_rlat_kind, hash seed, log2 of the instance count
+};
+
+cudaError_t launch_random_lattice_points(const RandomPointsArgs& a, cudaStream_t stream);
+
 // Radical inversion in prime bases (Sec. 2.2).  The per-base constants (the
 // first 64 primes, their domain limits, division reciprocals and Faure tables)
 // never change; points.cu writes them once per device into a device table.

@@ -190,3 +190,26 @@ def test_runtime_validation(B):
     # forward+backward tuning needs a target and a loss buffer
     assert L.qmc_tune_integrate(ctypes.byref(p), 4, FAKE, FAKE, None, FAKE, FAKE, None, FAKE, 1 << 20, None,
                                 ctypes.byref(best)) == 1
+
+
+def test_random_lattice_validation(B):
+    L = B._lib
+    S = None
+    R = L.qmc_random_lattice_points
+    for bad in ((2, 7, 4, 8, 64, 64, 0, 16, 4), (0, 7, 3, 8, 64, 64, 0, 16, 4), (0, 7, 32, 8, 64, 64, 0, 16, 4),
+                (0, 7, 0, 8, 64, 64, 0, 16, 4), (0, 7, 4, 0, 64, 64, 0, 16, 4), (0, 7, 4, 1025, 64, 64, 0, 16, 4),
+                (0, 7, 4, 8, (1 << 20) + 1, 1, 0, 16, 4), (0, 7, 4, 8, 64, 64, 0, 16, 0)):
+        assert R(*bad, FAKE, None, S) == 1, bad
+    assert R(0, 7, 4, 8, 64, 64, 4090, 7, 4, FAKE, None, S) == 2  # beyond the image
+    assert R(0, 7, 4, 8, 64, 64, 4096, 0, 4, FAKE, None, S) == 0  # empty range: no launch
+    assert R(0, 7, 4, 8, 64, 64, 0, 16, 4, FAKE + 2, None, S) == 3
+    ref = ctypes.byref
+    ws = 1 << 20
+    base = dict(source=B.SOURCE_RANDOM_LATTICE, randomize=B.rlat_randomize(B.RLAT_HASH, 4), image_width=64,
+                seeds_per_integral=False)
+    for bad in (dict(randomize=B.rlat_randomize(2, 4)), dict(randomize=B.rlat_randomize(0, 3)),
+                dict(randomize=B.rlat_randomize(0, 32)), dict(seeds=None), dict(image_width=0),
+                dict(image_width=(1 << 20) + 1)):
+        kw = dict(base)
+        kw.update(bad)
+        assert L.qmc_integrate(ref(_problem(B, **kw)), 4, FAKE, FAKE, FAKE, ws, 1 << 30, None) == 1, bad
