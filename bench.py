@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--only", choices=["fwd_bwd", "batched", "lattice", "points"], default=None,
                     help="run one extra workload alone (no headline)")
     ap.add_argument("--small", action="store_true", help="reduced integration sizes (profiling)")
+    ap.add_argument("--plan", choices=["window", "partition"], default="window",
+                    help="per-rank work: a contiguous index window, or one element of the sequence "
+                         "partitioned by its phi_2 dimension across the ranks (Sec. 2.5.1)")
     return ap.parse_args()
 
 
@@ -70,6 +73,15 @@ def dist_env():
 def rank_window(rank: int, world: int, n: int = N_POINTS):
     """Index window of one rank: rank r materialises indices [r n, (r+1) n)."""
     return rank * n, n
+
+
+def rank_partition(rank: int, world: int):
+    """Element of the partitioned sequence that a rank enumerates (Sec. 2.5.1):
+    (q, p) with P = 2^q = world and p = rank; element p owns the indices
+    J 2^q + (q-bit reversal of p)."""
+    if world < 1 or world & (world - 1) or not 0 <= rank < world:
+        raise ValueError("the partition plan needs a power-of-two number of ranks")
+    return world.bit_length() - 1, rank
 
 
 # ------------------------------------------------------------------ peaks, clocks, profiles
@@ -476,14 +488,24 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream()
 
     begin, count = rank_window(rank, world, 1 << args.log2_points)
-    C = B.qmc_sobol_matrices(S_DIMS, inputs.sobol_raw_init(S_DIMS))
     seeds = inputs.scramble_seeds(S_DIMS)
+    if args.plan == "window":
+        C = B.qmc_sobol_matrices(S_DIMS, inputs.sobol_raw_init(S_DIMS))
+    else:  # dimensions 1..s of the wide matrices; dimension 0 selects the rank's element
+        q, p = rank_partition(rank, world)
+        C = B.qmc_sobol_matrices_wide(S_DIMS + 1, 64, inputs.sobol_raw_init(S_DIMS + 1))
     Cd, sd = B.u32_tensor(C, dev), B.u32_tensor(seeds, dev)
     out_u = torch.empty((count, S_DIMS), dtype=torch.int32, device=dev)
     out_f = torch.empty((count, S_DIMS), dtype=torch.float32, device=dev)
 
+    def launch(u, f):
+        if args.plan == "window":
+            B.qmc_sobol_points(Cd, S_DIMS, begin, count, B.SCRAMBLE_NESTED, sd, u, f)
+        else:
+            B.qmc_sobol_points_partitioned(Cd, 64, S_DIMS, q, p, 0, count, B.SCRAMBLE_NESTED, sd, u, f)
+
     def step():
-        B.qmc_sobol_points(Cd, S_DIMS, begin, count, B.SCRAMBLE_NESTED, sd, out_u, out_f)
+        launch(out_u, out_f)
 
     for _ in range(args.warmup):
         step()
@@ -529,7 +551,7 @@ def run_ours(args, world, rank, local):
     def e2e_direct():  # the kernel writes the points straight into pinned host memory (NVLink-C2C)
         Cd.copy_(h_C, non_blocking=True)
         sd.copy_(h_s, non_blocking=True)
-        B.qmc_sobol_points(Cd, S_DIMS, begin, count, B.SCRAMBLE_NESTED, sd, h_u.data_ptr(), h_f.data_ptr())
+        launch(h_u.data_ptr(), h_f.data_ptr())
 
     e2e_copy_ms = statistics.median(timed(e2e_step, 3, 1, stream))
     e2e_direct_ms = statistics.median(timed(e2e_direct, 3, 1, stream))
@@ -552,6 +574,9 @@ def run_ours(args, world, rank, local):
         "config": {"workload": f"materialised scrambled Sobol: s={S_DIMS} dims, {count} indices per GPU, nested "
                                f"scramble, u32+fp32 outputs [{count}][{S_DIMS}] each", "s": S_DIMS,
                    "points_per_gpu": count, "scramble": "nested", "outputs": "u32+f32",
+                   "plan": ("contiguous index window per GPU" if args.plan == "window"
+                            else f"element {rank} of P = {world} of the sequence partitioned by its phi_2 "
+                                 "dimension"),
                    "l2": "outputs (4 GiB per step) exceed the 129 MB L2; no flush needed"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": profile_traffic("sobol_points_fast<1,2>"),

@@ -87,22 +87,72 @@ __device__ __forceinline__ void warp_range(uint64_t n_groups, uint64_t& g0, uint
   g1 = n_groups * (w + 1) / W;
 }
 
+// Per-warp staging of full groups for TMA bulk stores: two tiles of
+// kStageGroups groups (u32 and f32 halves) in shared memory; lane 0 sends a
+// full tile with one bulk store per output, and the warp refills a tile once
+// the copy engine has read it.  Calls are warp-uniform.
+template <int K>
+struct WarpStager {
+  static constexpr uint32_t kTileWords = kStageGroups * 128u * K;  // one output of one tile
+  static constexpr uint32_t kWarpWords = 4 * kTileWords;           // [2 tiles][2 outputs]
+  uint32_t* base;
+  uint32_t tile, staged;
+  uint64_t tile_off;  // global element offset of the tile's first group
+
+  __device__ explicit WarpStager(uint32_t* warp_base) : base(warp_base), tile(0), staged(0), tile_off(0) {}
+
+  // chunk c (elements 4 (lane + 32 c) .. +3) of the group being staged
+  __device__ __forceinline__ void put(uint32_t lane, int c, const uint32_t (&v)[4]) {
+    uint32_t* t = base + tile * 2 * kTileWords + staged * 128u * K + 4u * (lane + 32u * c);
+    *reinterpret_cast<uint4*>(t) = make_uint4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4*>(t + kTileWords) =
+        make_float4(map_u32_to_unifloat(v[0]), map_u32_to_unifloat(v[1]), map_u32_to_unifloat(v[2]),
+                    map_u32_to_unifloat(v[3]));
+  }
+
+  // the group at element offset off (this lane's first element) is complete;
+  // `last`: no further full group of this warp follows
+  __device__ __forceinline__ void group_done(uint32_t lane, uint64_t off, bool last, uint32_t* out_u32,
+                                             float* out_f32) {
+    if (staged == 0) tile_off = off - 4u * lane;
+    if (++staged == kStageGroups || last) flush(lane, out_u32, out_f32);
+  }
+
+  __device__ __forceinline__ void flush(uint32_t lane, uint32_t* out_u32, float* out_f32) {
+    fence_smem_to_async();
+    __syncwarp();
+    if (lane == 0) {
+      const uint32_t bytes = staged * 128u * K * 4u;
+      const uint32_t* t = base + tile * 2 * kTileWords;
+      if (out_u32) bulk_store(out_u32 + tile_off, t, bytes);
+      if (out_f32) bulk_store(out_f32 + tile_off, t + kTileWords, bytes);
+      bulk_commit();
+      bulk_wait_read_1();  // the other tile's previous copy has read its source
+    }
+    __syncwarp();
+    tile ^= 1u;
+    staged = 0;
+  }
+
+  // every bulk store of this warp has completed before the kernel ends
+  __device__ __forceinline__ void finish(uint32_t lane) {
+    if (lane == 0) bulk_wait_all();
+  }
+};
+
 // ---------------------------------------------------------------------------
 // K1 fast path.  MODE: 0 none, 1 XOR, 2 nested.  K: 16-byte chunks per lane.
 // Shared memory: cols[s][m] (mirrored for nested), hin[2^u][s], pc[s].  Table
 // entries for index bits at or above m stay zero: no enumerated index sets them.
 // ---------------------------------------------------------------------------
-// TMA: full groups are staged per warp in shared memory (two tiles of
-// kStageGroups groups, u32 and f32 halves) and written by lane 0 with one bulk
-// store per output; the warp refills a tile once the copy engine has read it.
+// TMA: full groups go through a WarpStager (bulk stores from shared memory).
 template <int K, int MODE, bool V4, bool TMA>  // V4: s % 4 == 0, chunks hold 4 consecutive dimensions
 __global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
   extern __shared__ __align__(128) uint32_t smem[];
   const uint32_t s = a.s;
   const uint32_t nin = 1u << a.u_log2;
-  constexpr uint32_t kTileWords = kStageGroups * 128u * K;  // one output of one tile
-  uint32_t* stage = smem;  // [warps][2 tiles][2 outputs][kTileWords]
-  uint32_t* cols = smem + (TMA ? (kThreads / 32) * 4 * kTileWords : 0);
+  // [warps][WarpStager words], then the tables
+  uint32_t* cols = smem + (TMA ? (kThreads / 32) * WarpStager<K>::kWarpWords : 0);
   const uint32_t m = a.m;
   uint32_t* hin = cols + s * m;
   uint32_t* pc = hin + nin * s;
@@ -156,24 +206,7 @@ __global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
   const uint64_t step = (uint64_t)Q * s;  // elements per group
   uint64_t off = g0 * step + 4u * lane;   // this lane's first element in group g0
 
-  uint32_t* my_stage = stage + (threadIdx.x >> 5) * 4 * kTileWords;
-  uint32_t tile = 0, staged = 0;
-  uint64_t tile_off = 0;  // global element offset of the tile's first group
-  auto flush = [&]() {   // send the staged groups of the current tile (warp-uniform call)
-    fence_smem_to_async();
-    __syncwarp();
-    if (lane == 0) {
-      const uint32_t bytes = staged * 128u * K * 4u;
-      const uint32_t* t = my_stage + tile * 2 * kTileWords;
-      if (a.out_u32) bulk_store(a.out_u32 + tile_off, t, bytes);
-      if (a.out_f32) bulk_store(a.out_f32 + tile_off, t + kTileWords, bytes);
-      bulk_commit();
-      bulk_wait_read_1();  // the other tile's previous copy has read its source
-    }
-    __syncwarp();
-    tile ^= 1u;
-    staged = 0;
-  };
+  WarpStager<K> stager(smem + (threadIdx.x >> 5) * WarpStager<K>::kWarpWords);
 
   for (uint64_t g = g0; g < g1; ++g, off += step) {
     const uint64_t G = G_first + g;
@@ -219,15 +252,10 @@ __global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
       }
       const uint64_t o = off + 128u * c;
       if (g < full_groups) {
-        if (TMA) {
-          uint32_t* t = my_stage + tile * 2 * kTileWords + staged * 128u * K + 4u * (lane + 32u * c);
-          *reinterpret_cast<uint4*>(t) = make_uint4(v[0], v[1], v[2], v[3]);
-          *reinterpret_cast<float4*>(t + kTileWords) =
-              make_float4(map_u32_to_unifloat(v[0]), map_u32_to_unifloat(v[1]), map_u32_to_unifloat(v[2]),
-                          map_u32_to_unifloat(v[3]));
-        } else {
+        if (TMA)
+          stager.put(lane, c, v);
+        else
           store4(a.out_u32, a.out_f32, o, v);
-        }
       } else {  // ragged last group: per-element row test
         const uint64_t rows_left = a.count - (g << a.q_log2);
         const uint32_t e0 = 4u * (lane + 32u * c);
@@ -236,12 +264,10 @@ __global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
           if ((uint64_t)((e0 + t) / s) < rows_left) store1(a.out_u32, a.out_f32, o + t, v[t]);
       }
     }
-    if (TMA && g < full_groups) {
-      if (staged == 0) tile_off = off - 4u * lane;
-      if (++staged == kStageGroups || g + 1 == g1 || g + 1 == full_groups) flush();
-    }
+    if (TMA && g < full_groups)
+      stager.group_done(lane, off, g + 1 == g1 || g + 1 == full_groups, a.out_u32, a.out_f32);
   }
-  if (TMA && lane == 0) bulk_wait_all();  // writes complete before the kernel ends
+  if (TMA) stager.finish(lane);
 }
 
 // K1 generic path: one element per thread, columns read through the cache.
@@ -266,9 +292,11 @@ __global__ void __launch_bounds__(kThreads) sobol_points_generic(PointsArgs a) {
 // K2: rank-1 lattice.  BACKWARD follows Alg. 4: phi_2(~k) = ~phi_2(k), so
 // x = shift - g - phi_2(k) g (mod 2^32).
 // ---------------------------------------------------------------------------
-template <int K, bool BACKWARD>
+template <int K, bool BACKWARD, bool TMA>
 __global__ void __launch_bounds__(kThreads) lattice_points_fast(PointsArgs a) {
+  extern __shared__ __align__(128) uint32_t smem[];
   const uint32_t lane = threadIdx.x & 31u;
+  WarpStager<K> stager(smem + (threadIdx.x >> 5) * WarpStager<K>::kWarpWords);
   const uint32_t s = a.s;
   const uint32_t Q = 1u << a.q_log2;
   uint32_t gj[4 * K], lo[4 * K];
@@ -301,7 +329,10 @@ __global__ void __launch_bounds__(kThreads) lattice_points_fast(PointsArgs a) {
         v[t] = BACKWARD ? lo[4 * c + t] - phib * gj[4 * c + t] : phib * gj[4 * c + t] + lo[4 * c + t];
       const uint64_t o = off + 128u * c;
       if (g < full_groups) {
-        store4(a.out_u32, a.out_f32, o, v);
+        if (TMA)
+          stager.put(lane, c, v);
+        else
+          store4(a.out_u32, a.out_f32, o, v);
       } else {  // ragged last group: per-element row test
         const uint64_t rows_left = a.count - (g << a.q_log2);
         const uint32_t e0 = 4u * (lane + 32u * c);
@@ -310,7 +341,10 @@ __global__ void __launch_bounds__(kThreads) lattice_points_fast(PointsArgs a) {
           if ((uint64_t)((e0 + t) / s) < rows_left) store1(a.out_u32, a.out_f32, o + t, v[t]);
       }
     }
+    if (TMA && g < full_groups)
+      stager.group_done(lane, off, g + 1 == g1 || g + 1 == full_groups, a.out_u32, a.out_f32);
   }
+  if (TMA) stager.finish(lane);
 }
 
 template <bool BACKWARD>
@@ -772,17 +806,25 @@ cudaError_t launch_lattice_points(PointsArgs a, cudaStream_t stream) {
   const bool backward = (a.scramble & 1u) != 0;
   const uint32_t K = fast_k(a.s);
   a.q_log2 = log2_exact(K ? 128u * K / a.s : 1u);
-  const bool fast = K != 0 && (a.index_begin & ((1u << a.q_log2) - 1u)) == 0 && aligned16(a.out_u32) &&
+  const bool fast = K != 0 && (a.index_begin & ((1ull << a.q_log2) - 1u)) == 0 && aligned16(a.out_u32) &&
                     aligned16(a.out_f32);
   if (!fast) {
     return backward ? launch_grid_stride(lattice_points_generic<true>, a.count * a.s, stream, a)
                     : launch_grid_stride(lattice_points_generic<false>, a.count * a.s, stream, a);
   }
   const uint64_t groups = (a.count + (1u << a.q_log2) - 1) >> a.q_log2;
-#define QMC_LATTICE_CASE(KK)                                                                 \
-  case KK:                                                                                   \
-    return backward ? launch_persistent(lattice_points_fast<KK, true>, groups, 0, stream, a) \
-                    : launch_persistent(lattice_points_fast<KK, false>, groups, 0, stream, a);
+  // TMA bulk stores for device-memory outputs whose staging tiles fit (K <= 3)
+  const size_t stage = (size_t)(kThreads / 32) * 4 * kStageGroups * 128u * K * sizeof(uint32_t);
+  const bool tma = kPointsTma && device_resident(a.out_u32) && device_resident(a.out_f32) &&
+                   stage <= device_info().smem_per_block_optin;
+  const size_t smem = tma ? stage : 0;
+#define QMC_LATTICE_CASE(KK)                                                                                 \
+  case KK:                                                                                                   \
+    if (tma)                                                                                                 \
+      return backward ? launch_persistent(lattice_points_fast<KK, true, kPointsTma>, groups, smem, stream, a)  \
+                      : launch_persistent(lattice_points_fast<KK, false, kPointsTma>, groups, smem, stream, a); \
+    return backward ? launch_persistent(lattice_points_fast<KK, true, false>, groups, 0, stream, a)          \
+                    : launch_persistent(lattice_points_fast<KK, false, false>, groups, 0, stream, a);
   switch (K) {
     QMC_LATTICE_CASE(1)
     QMC_LATTICE_CASE(2)
