@@ -514,16 +514,19 @@ QO_EXPORT uint32_t qo_lfsr_step(uint32_t state)
 
 /* Component j of the generator vector of instance k of pixel (px, py):
  *   HASH (Alg. 4): hash_value | 1;
- *   LFSR (Sec. 2.4.2): g_j = 2 xi_j + 1 mod 2^32 with xi_0 the instance's seed
- *   state (the hash at the reserved dimension 2^20 - 1, replaced by 1 if 0) and
- *   xi_{j+1} one LFSR step after xi_j, so one seed defines the whole vector. */
+ *   LFSR (Sec. 2.4.2): g_j = 2 xi_j + 1 mod 2^32, where the LFSR serves as the
+ *   pseudo-random number generator of 32-bit numbers xi: xi_0 is the instance's
+ *   seed state (the hash at the reserved dimension 2^20 - 1, replaced by 1 if 0)
+ *   and xi_{j+1} the state 32 steps after xi_j, so that every number holds 32
+ *   fresh register bits (one step alone only shifts the state, which would make
+ *   g_{j+1} nearly 2 g_j).  One seed defines the whole vector. */
 QO_EXPORT uint32_t qo_rlat_generator(uint32_t kind, uint32_t seed, uint32_t k, uint32_t j,
                                      uint32_t px, uint32_t py)
 {
     if (kind == QO_RLAT_HASH) return qo_rlat_hash(seed, k, j, px, py) | 1u;
     uint32_t xi = qo_rlat_hash(seed, k, (1u << 20) - 1u, px, py);
     if (xi == 0) xi = 1;
-    for (uint32_t t = 0; t < j; ++t) xi = qo_lfsr_step(xi);
+    for (uint64_t t = 0; t < 32ull * j; ++t) xi = qo_lfsr_step(xi);
     return (uint32_t)(((uint64_t)xi * 2u + 1u) & 0xFFFFFFFFull);
 }
 

@@ -298,13 +298,21 @@ struct PixelLatticeSource {
 template <int S, int KIND>
 struct RandomLatticeSource {
   uint32_t start, seed, r_log2;
+  const uint32_t* jump;  // LFSR: the 32-step jump table in shared memory
   uint32_t g[S];
 
-  static size_t smem_bytes(uint32_t, uint32_t) { return 0; }
+  static size_t smem_bytes(uint32_t, uint32_t) {
+    return KIND == QMC_RLAT_LFSR ? kLfsrJumpWords * sizeof(uint32_t) : 0;
+  }
 
-  __device__ void kernel_setup(const IntegrateArgs& a, uint32_t*) {
+  __device__ void kernel_setup(const IntegrateArgs& a, uint32_t* smem) {
     seed = __ldg(a.seeds);
     r_log2 = a.rlat_log2;
+    jump = smem;
+    if (KIND == QMC_RLAT_LFSR) {
+      lfsr_jump_table_fill(smem);
+      __syncthreads();
+    }
   }
 
   __device__ void item_setup(const IntegrateArgs& a, uint32_t p, uint32_t st) {
@@ -319,7 +327,7 @@ struct RandomLatticeSource {
 #pragma unroll
       for (int j = 0; j < S; ++j) {
         g[j] = 2u * xi + 1u;
-        xi = lfsr_step(xi);
+        xi = lfsr_jump32(jump, xi);
       }
     }
   }
@@ -852,16 +860,6 @@ cudaError_t launch_main_fn(const IntegrateArgs& a, uint32_t block, cudaStream_t 
 }
 
 }  // namespace
-
-size_t integrate_smem_bytes(uint32_t source, uint32_t integrand, uint32_t s, uint32_t chunk_log2,
-                            bool points) {
-  if (points || source == QMC_SOURCE_LATTICE) return 0;
-  switch (integrand) {
-    case QMC_F_BILINEAR2D: return SobolSource<2, 0>::smem_bytes(s, chunk_log2);
-    case QMC_F_GAUSSMIX4_6D: return SobolSource<6, 0>::smem_bytes(s, chunk_log2);
-    default: return SobolSource<16, 0>::smem_bytes(s, chunk_log2);
-  }
-}
 
 cudaError_t launch_integrate(const IntegrateArgs& a, uint32_t block, bool grad, cudaStream_t stream) {
   const uint32_t n_blocks = (uint32_t)(((uint64_t)a.n + kScanBlock) / kScanBlock);  // covers entry n

@@ -672,21 +672,46 @@ cudaError_t launch_halton_points(const HaltonArgs& p, cudaStream_t stream) {
 
 namespace {
 
+// LFSR jump tables of the materialising kernels: level b advances a state by
+// 32 * 2^b steps (b < kJumpLevels), each level the square of the one below, so a
+// chunk reaches dimension j0 in popcount(j0) jumps.
+constexpr uint32_t kJumpLevels = 5;
+
+template <int KIND>
+__device__ __forceinline__ void rlat_jump_tables_fill(uint32_t* jump) {
+  if (KIND != QMC_RLAT_LFSR) return;
+  lfsr_jump_table_fill(jump);
+  __syncthreads();
+  for (uint32_t b = 1; b < kJumpLevels; ++b) {
+    const uint32_t* lower = jump + (b - 1) * kLfsrJumpWords;
+    for (uint32_t e = threadIdx.x; e < kLfsrJumpWords; e += blockDim.x) {
+      const uint32_t v = (e & 255u) << (8u * (e >> 8));
+      jump[b * kLfsrJumpWords + e] = lfsr_jump32(lower, lfsr_jump32(lower, v));
+    }
+    __syncthreads();
+  }
+}
+
 // Generator component j of instance k of pixel (px, py), for one chunk of
-// consecutive dimensions j0 .. j0+N-1 (LFSR: stepped from the pixel's seed state).
+// consecutive dimensions j0 .. j0+N-1 (LFSR: 32 register steps per dimension
+// from the pixel's seed state, taken through the jump tables).
 template <int KIND, int N>
 __device__ __forceinline__ void rlat_generators(uint32_t seed, uint32_t k, uint32_t j0, uint32_t px,
-                                                uint32_t py, uint32_t (&g)[N]) {
+                                                uint32_t py, const uint32_t* jump, uint32_t (&g)[N]) {
   if (KIND == QMC_RLAT_HASH) {
 #pragma unroll
     for (int q = 0; q < N; ++q) g[q] = rlat_hash(seed, k, j0 + q, px, py) | 1u;
   } else {
     uint32_t xi = rlat_lfsr_seed(seed, k, px, py);
-    for (uint32_t u = 0; u < j0; ++u) xi = lfsr_step(xi);
+#pragma unroll
+    for (uint32_t b = 0; b + 1 < kJumpLevels; ++b)
+      if ((j0 >> b) & 1u) xi = lfsr_jump32(jump + b * kLfsrJumpWords, xi);
+    for (uint32_t u = 0; u < (j0 >> (kJumpLevels - 1)); ++u)
+      xi = lfsr_jump32(jump + (kJumpLevels - 1) * kLfsrJumpWords, xi);
 #pragma unroll
     for (int q = 0; q < N; ++q) {
       g[q] = 2u * xi + 1u;
-      xi = lfsr_step(xi);
+      xi = lfsr_jump32(jump, xi);
     }
   }
 }
@@ -697,6 +722,8 @@ __device__ __forceinline__ void rlat_generators(uint32_t seed, uint32_t k, uint3
 // dimensions) derives its four generator components and multiplies.
 template <int KIND>
 __global__ void __launch_bounds__(kThreads) random_lattice_points_fast(RandomPointsArgs a) {
+  __shared__ uint32_t jump[KIND == QMC_RLAT_LFSR ? kJumpLevels * kLfsrJumpWords : 1];
+  rlat_jump_tables_fill<KIND>(jump);
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t n_batches = (a.n_pixels + 31) >> 5;
   uint64_t b0, b1;
@@ -724,7 +751,7 @@ __global__ void __launch_bounds__(kThreads) random_lattice_points_fast(RandomPoi
       const uint32_t py = __shfl_sync(0xffffffffu, pyl, pl & 31u);
       if (c < chunks) {
         uint32_t g[4];
-        rlat_generators<KIND, 4>(a.seed, t & kmask, j, px, py, g);
+        rlat_generators<KIND, 4>(a.seed, t & kmask, j, px, py, jump, g);
         const uint32_t phi = __brev(~(t >> a.r_log2));  // phi_2(2^32 - 1 - i), Alg. 4
         const uint32_t v[4] = {phi * g[0], phi * g[1], phi * g[2], phi * g[3]};
         store4(a.out_u32, a.out_f32, off0 + e, v);
@@ -736,6 +763,8 @@ __global__ void __launch_bounds__(kThreads) random_lattice_points_fast(RandomPoi
 // Generic path: one element per thread.
 template <int KIND>
 __global__ void __launch_bounds__(kThreads) random_lattice_points_generic(RandomPointsArgs a) {
+  __shared__ uint32_t jump[KIND == QMC_RLAT_LFSR ? kJumpLevels * kLfsrJumpWords : 1];
+  rlat_jump_tables_fill<KIND>(jump);
   const uint64_t total = a.n_pixels * a.spp * a.s;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += stride) {
@@ -746,7 +775,7 @@ __global__ void __launch_bounds__(kThreads) random_lattice_points_generic(Random
     const uint64_t p = a.pixel_begin + q;
     uint32_t g[1];
     rlat_generators<KIND, 1>(a.seed, t & ((1u << a.r_log2) - 1u), j, (uint32_t)(p % a.width),
-                             (uint32_t)(p / a.width), g);
+                             (uint32_t)(p / a.width), jump, g);
     store1(a.out_u32, a.out_f32, f, __brev(~(t >> a.r_log2)) * g[0]);
   }
 }

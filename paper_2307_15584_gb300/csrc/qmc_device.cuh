@@ -123,6 +123,25 @@ __device__ __forceinline__ uint32_t lfsr_step(uint32_t st) {
   return (st << 1) ^ (0x00400007u & (0u - (st >> 31)));
 }
 
+// The LFSR yields one 32-bit number per 32 register steps.  Advancing a state by
+// 32 steps multiplies it by x^32 modulo the polynomial, a linear map over GF(2),
+// so it is the XOR of four byte-indexed tables (the multi-digit table idea of
+// Sec. 2.2 carried over to GF(2)): T[b][v] = (v << 8b) advanced 32 steps.
+constexpr uint32_t kLfsrJumpWords = 1024;  // [4][256]
+
+// Block-cooperative fill of T; the caller synchronises the block afterwards.
+__device__ __forceinline__ void lfsr_jump_table_fill(uint32_t* T) {
+  for (uint32_t e = threadIdx.x; e < kLfsrJumpWords; e += blockDim.x) {
+    uint32_t v = (e & 255u) << (8u * (e >> 8));
+    for (int t = 0; t < 32; ++t) v = lfsr_step(v);
+    T[e] = v;
+  }
+}
+
+__device__ __forceinline__ uint32_t lfsr_jump32(const uint32_t* T, uint32_t xi) {
+  return T[xi & 255u] ^ T[256u + ((xi >> 8) & 255u)] ^ T[512u + ((xi >> 16) & 255u)] ^ T[768u + (xi >> 24)];
+}
+
 // Seed state of the LFSR generator of instance k of a pixel: the hash at the
 // reserved dimension 2^20 - 1 (never zero: 0 maps to 1).
 __device__ __forceinline__ uint32_t rlat_lfsr_seed(uint32_t seed, uint32_t k, uint32_t px, uint32_t py) {

@@ -61,7 +61,4 @@ WsLayout workspace_layout(uint32_t n, uint64_t capacity_items, uint32_t values_p
 
 cudaError_t launch_integrate(const IntegrateArgs& a, uint32_t block, bool grad, cudaStream_t stream);
 
-size_t integrate_smem_bytes(uint32_t source, uint32_t integrand, uint32_t s, uint32_t chunk_log2,
-                            bool points);
-
 }  // namespace qmc

@@ -55,6 +55,7 @@ def _key(seed: int, tag: int) -> np.uint64:
 # stream tags (distinct streams per purpose)
 _T_DIRECTION, _T_SCRAMBLE, _T_LATTICE_G, _T_LATTICE_SHIFT = 1, 2, 3, 4
 _T_GENZ, _T_THETA, _T_COUNTS, _T_PIXEL, _T_TARGET = 5, 6, 7, 8, 9
+_T_IMAGE = 10
 
 
 def sobol_raw_init(s: int, seed: int = DEFAULT_SEED) -> np.ndarray:
@@ -105,6 +106,28 @@ def log_uniform_counts(n: int, lo: int = 1, hi: int = 65536, seed: int = DEFAULT
     u = uniform01(_key(seed, _T_COUNTS), np.arange(n, dtype=np.uint64))
     c = np.floor(np.exp(u * math.log(hi)))
     return np.clip(c, lo, hi).astype(np.uint32)
+
+
+def gaussmix_theta_image(width: int, height: int, seed: int = DEFAULT_SEED) -> np.ndarray:
+    """fp32 [height * width][16]: mixture parameters that vary smoothly over an image
+    (row-major pixels), so that neighbouring pixels have nearly equal integrals
+    and an estimator's error image shows its spatial structure.  Component c has a
+    seeded weight w_c ~ U[0.2,1], width sigma_c ~ U[0.08,0.25], and means
+    mu_c = 0.5 + 0.35 sin(2 pi (f_c x / width + p_c)), nu_c = 0.5 + 0.35 sin(2 pi
+    (g_c y / height + q_c)) with seeded frequencies f_c, g_c ~ U[0.5,2.5] and phases."""
+    r = uniform01(_key(seed, _T_IMAGE), np.arange(24, dtype=np.uint64)).reshape(4, 6)
+    w = 0.2 + 0.8 * r[:, 0]
+    sg = 0.08 + 0.17 * r[:, 1]
+    f, g = 0.5 + 2.0 * r[:, 2], 0.5 + 2.0 * r[:, 3]
+    x = (np.arange(width, dtype=np.float64) + 0.5) / width
+    y = (np.arange(height, dtype=np.float64) + 0.5) / height
+    th = np.empty((height, width, 4, 4), np.float64)
+    for c in range(4):
+        th[:, :, c, 0] = w[c]
+        th[:, :, c, 1] = 0.5 + 0.35 * np.sin(2 * np.pi * (f[c] * x[None, :] + r[c, 4]))
+        th[:, :, c, 2] = 0.5 + 0.35 * np.sin(2 * np.pi * (g[c] * y[:, None] + r[c, 5]))
+        th[:, :, c, 3] = sg[c]
+    return th.reshape(height * width, 16).astype(np.float32)
 
 
 def gaussmix_target(theta_star: np.ndarray) -> np.ndarray:

@@ -1,0 +1,25 @@
+"""Host-side helpers of bench.py: the closed-form integrals it reports errors
+against agree with the oracle's (CPU only)."""
+import numpy as np
+
+import bench
+from paper_2307_15584_gb300 import inputs
+
+
+def test_genz_closed_forms_match_oracle(oracle):
+    for fam, fn in (("product_peak", oracle.exact_genz_product_peak), ("oscillatory", oracle.exact_genz_oscillatory)):
+        for k in range(4):
+            for s in (1, 6, 16):
+                t = inputs.genz_params(fam, s, k)
+                assert abs(bench.genz_exact(fam, t, s) - fn(t, s)) <= 1e-12 * max(1.0, abs(fn(t, s)))
+
+
+def test_mixture_closed_form_matches_oracle(oracle):
+    theta = inputs.gaussmix_theta(64, seed=5)
+    exact = inputs.gaussmix_target(theta)
+    for p in range(64):
+        assert abs(exact[p] - oracle.exact_gaussmix(theta[p])) <= 1e-12 * abs(exact[p])
+
+
+def test_rms_rel_err():
+    assert abs(bench.rms_rel_err(np.array([1.1, 0.9]), np.array([1.0, 1.0])) - 0.1) < 1e-15

@@ -99,15 +99,29 @@ def test_random_lattice_closed_form(oracle, kind, R):
 
 
 def test_hash_and_lfsr_generators(oracle):
-    """HASH: g_j = hash_value | 1.  LFSR: g_j = 2 xi_j + 1 with xi_j = x^j xi_0
-    modulo the LFSR polynomial, xi_0 the instance's seed state."""
+    """HASH: g_j = hash_value | 1.  LFSR: g_j = 2 xi_j + 1 with xi_j = x^(32 j) xi_0
+    modulo the LFSR polynomial (32 register steps per number), xi_0 the instance's
+    seed state."""
     L = oracle.lib()
     for (seed, k, px, py) in [(1, 0, 0, 0), (99, 3, 1919, 1079), (123456789, 2, 17, 5)]:
         xi0 = L.qo_rlat_hash(seed, k, (1 << 20) - 1, px, py) or 1
         for j in range(40):
             assert L.qo_rlat_generator(0, seed, k, j, px, py) == L.qo_rlat_hash(seed, k, j, px, py) | 1
-            xi = _gf2_mulmod(xi0, _gf2_pow_x(j))
+            xi = _gf2_mulmod(xi0, _gf2_pow_x(32 * j))
             assert L.qo_rlat_generator(1, seed, k, j, px, py) == (2 * xi + 1) % (1 << 32)
+
+
+def test_lfsr_generator_components_are_not_shifts_of_each_other(oracle):
+    """With 32 register steps per number, consecutive components are unrelated
+    words.  After a single step (a shift by one bit, plus the taps) every pair
+    would have |g_{j+1} - 2 g_j| < 2^24 (mod 2^32); unrelated words land there
+    with probability 2^-7, about 3.5 of these 448 pairs."""
+    L = oracle.lib()
+    near = 0
+    for px in range(64):
+        g = [L.qo_rlat_generator(1, 7, 0, j, px, 3) for j in range(8)]
+        near += sum(1 for a, b in zip(g, g[1:]) if min((b - 2 * a) % (1 << 32), (2 * a - b) % (1 << 32)) < 1 << 24)
+    assert near <= 20
 
 
 def test_backward_enumeration_puts_the_origin_last(oracle):
