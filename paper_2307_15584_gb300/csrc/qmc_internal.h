@@ -78,6 +78,9 @@ struct HaltonArgs {
   uint32_t q, dim0;                    // output dimension j is Halton dimension dim0 + j
   uint32_t s, mode;                    // mode: 0 identity, 1 Faure, 2 linear
   uint32_t mult[kHaltonMaxDims];       // linear digit scramble multipliers per output dimension
+  // set by the launcher: shared-memory layout
+  uint32_t tile_rows, stage_stride, stage_words;
+  uint32_t table_off[kHaltonMaxDims];
 };
 
 // Enqueues the Halton kernel; writes the device table first if this device has
