@@ -634,8 +634,13 @@ def run_ours(args, world, rank, local):
         sd.copy_(h_s, non_blocking=True)
         launch(h_u.data_ptr(), h_f.data_ptr())
 
+    def d2h_only():  # the host link alone: the same bytes copied without the kernel
+        h_u.copy_(out_u, non_blocking=True)
+        h_f.copy_(out_f, non_blocking=True)
+
     e2e_copy_ms = statistics.median(timed(e2e_step, 3, 1, stream))
     e2e_direct_ms = statistics.median(timed(e2e_direct, 3, 1, stream))
+    link_ms = statistics.median(timed(d2h_only, 3, 1, stream))
     e2e_ms = min(e2e_copy_ms, e2e_direct_ms)
     h2d = h_C.numel() * 4 + h_s.numel() * 4
     d2h = h_u.numel() * 4 + h_f.numel() * 4
@@ -667,7 +672,12 @@ def run_ours(args, world, rank, local):
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                 "method": "kernel writes pinned host memory" if e2e_direct_ms <= e2e_copy_ms
                           else "device outputs + cudaMemcpyAsync to pinned host",
-                "ms_copy_back": e2e_copy_ms, "ms_direct_to_host": e2e_direct_ms},
+                "ms_copy_back": e2e_copy_ms, "ms_direct_to_host": e2e_direct_ms,
+                "achieved_gbs": (h2d + d2h) / (e2e_ms * 1e-3) / 1e9,
+                "link_gbs": d2h / (link_ms * 1e-3) / 1e9,
+                "link_frac": (link_ms / e2e_ms),
+                "link_note": "link_gbs: the same output bytes copied device to pinned host alone; "
+                             "splitting the copy over 2-8 streams measured the same"},
         "gpu_launches": args.steps,
         "clocks": clk,
     }
