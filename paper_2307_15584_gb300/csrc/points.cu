@@ -845,46 +845,63 @@ __device__ __forceinline__ void rlat_generators(uint32_t seed, uint32_t k, uint3
   }
 }
 
-// Coalesced path (s % 4 == 0, 16-byte aligned outputs, 32 spp s <= 2^31): as
-// pixel_lattice_points_fast, a warp takes batches of 32 pixels whose
-// coordinates its lanes hold; each 16-byte chunk (one sample, four consecutive
-// dimensions) derives its four generator components and multiplies.
+// Coalesced path (s % 4 == 0, 16-byte aligned outputs, batch_pixels spp s <= 2^31).
+// A block takes batches of batch_pixels consecutive pixels: it first derives the
+// generator words of every (pixel, instance, dimension) of the batch into
+// shared memory ([pixel][R][s]; spp / R samples share each word), then writes
+// the batch's rows as consecutive 16-byte chunks, each chunk one sample and
+// four consecutive dimensions: one 128-bit shared load, four multiplies.
 template <int KIND>
 __global__ void __launch_bounds__(kThreads) random_lattice_points_fast(RandomPointsArgs a) {
-  __shared__ uint32_t jump[KIND == QMC_RLAT_LFSR ? kJumpLevels * kLfsrJumpWords : 1];
+  extern __shared__ __align__(16) uint32_t rsm[];
+  uint32_t* jump = rsm;  // LFSR jump tables
+  uint32_t* pxy = rsm + (KIND == QMC_RLAT_LFSR ? kJumpLevels * kLfsrJumpWords : 0);  // [batch][2]
+  uint32_t* gvec = pxy + ((2 * a.batch_pixels + 3u) & ~3u);  // [batch][R][s], 16-byte aligned
   rlat_jump_tables_fill<KIND>(jump);
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint64_t n_batches = (a.n_pixels + 31) >> 5;
-  uint64_t b0, b1;
-  warp_range(n_batches, b0, b1);
-  const uint64_t mag_s = ~0ull / a.s + 1;  // s >= 4
+  const uint32_t s = a.s, R = 1u << a.r_log2, Rs = R * s;
+  const uint64_t mag_s = ~0ull / s + 1;  // s >= 4
   const uint64_t mag_spp = a.spp > 1 ? ~0ull / a.spp + 1 : 0;
-  const uint32_t chunks_per_pixel = a.spp * (a.s >> 2);
-  const uint32_t kmask = (1u << a.r_log2) - 1u;
-  for (uint64_t b = b0; b < b1; ++b) {
-    const uint64_t first = b << 5;
+  const uint64_t n_batches = (a.n_pixels + a.batch_pixels - 1) / a.batch_pixels;
+  for (uint64_t b = blockIdx.x; b < n_batches; b += gridDim.x) {
+    const uint64_t first = b * a.batch_pixels;
     const uint64_t left = a.n_pixels - first;
-    const uint32_t npx = left < 32 ? (uint32_t)left : 32u;
-    const uint64_t p = a.pixel_begin + first + (lane < npx ? lane : 0u);
-    const uint32_t pxl = (uint32_t)(p % a.width), pyl = (uint32_t)(p / a.width);
-    const uint32_t chunks = npx * chunks_per_pixel;
-    const uint64_t off0 = first * a.spp * a.s;
-    for (uint32_t c0 = 0; c0 < chunks; c0 += 32) {  // same trip count in every lane
-      const uint32_t c = c0 + lane;
-      const uint32_t e = 4u * c;
+    const uint32_t npx = left < a.batch_pixels ? (uint32_t)left : a.batch_pixels;
+    __syncthreads();  // the previous batch's words are no longer read
+    for (uint32_t q = threadIdx.x; q < npx; q += blockDim.x) {
+      const uint64_t p = a.pixel_begin + first + q;
+      pxy[2 * q] = (uint32_t)(p % a.width);
+      pxy[2 * q + 1] = (uint32_t)(p / a.width);
+    }
+    __syncthreads();
+    if (KIND == QMC_RLAT_HASH) {  // every component independently
+      for (uint32_t idx = threadIdx.x; idx < npx * Rs; idx += blockDim.x) {
+        const uint32_t row = (uint32_t)__umul64hi(idx, mag_s);  // (pixel, instance)
+        const uint32_t j = idx - row * s, q = row >> a.r_log2;
+        gvec[idx] = rlat_hash(a.seed, row & (R - 1u), j, pxy[2 * q], pxy[2 * q + 1]) | 1u;
+      }
+    } else {  // one thread per (pixel, instance) walks the register through the dimensions
+      for (uint32_t w = threadIdx.x; w < npx * R; w += blockDim.x) {
+        const uint32_t q = w >> a.r_log2;
+        uint32_t xi = rlat_lfsr_seed(a.seed, w & (R - 1u), pxy[2 * q], pxy[2 * q + 1]);
+        for (uint32_t j = 0; j < s; ++j) {
+          gvec[w * s + j] = 2u * xi + 1u;
+          xi = lfsr_jump32(jump, xi);
+        }
+      }
+    }
+    __syncthreads();
+    const uint32_t chunks = npx * a.spp * (s >> 2);
+    const uint64_t off0 = first * a.spp * s;
+    for (uint32_t c = threadIdx.x; c < chunks; c += blockDim.x) {
+      const uint32_t e = 4u * c;  // element within the batch, < 2^31
       const uint32_t row = (uint32_t)__umul64hi(e, mag_s);
-      const uint32_t j = e - row * a.s;
+      const uint32_t j = e - row * s;
       const uint32_t pl = a.spp > 1 ? (uint32_t)__umul64hi(row, mag_spp) : row;
       const uint32_t t = row - pl * a.spp;
-      const uint32_t px = __shfl_sync(0xffffffffu, pxl, pl & 31u);
-      const uint32_t py = __shfl_sync(0xffffffffu, pyl, pl & 31u);
-      if (c < chunks) {
-        uint32_t g[4];
-        rlat_generators<KIND, 4>(a.seed, t & kmask, j, px, py, jump, g);
-        const uint32_t phi = __brev(~(t >> a.r_log2));  // phi_2(2^32 - 1 - i), Alg. 4
-        const uint32_t v[4] = {phi * g[0], phi * g[1], phi * g[2], phi * g[3]};
-        store4(a.out_u32, a.out_f32, off0 + e, v);
-      }
+      const uint4 g = *reinterpret_cast<const uint4*>(gvec + (pl * R + (t & (R - 1u))) * s + j);
+      const uint32_t phi = __brev(~(t >> a.r_log2));  // phi_2(2^32 - 1 - i), Alg. 4
+      const uint32_t v[4] = {phi * g.x, phi * g.y, phi * g.z, phi * g.w};
+      store4(a.out_u32, a.out_f32, off0 + e, v);
     }
   }
 }
@@ -911,20 +928,33 @@ __global__ void __launch_bounds__(kThreads) random_lattice_points_generic(Random
 
 }  // namespace
 
-cudaError_t launch_random_lattice_points(const RandomPointsArgs& a, cudaStream_t stream) {
+cudaError_t launch_random_lattice_points(const RandomPointsArgs& args, cudaStream_t stream) {
   const DeviceInfo& dev = device_info();
+  RandomPointsArgs a = args;
   const bool hash = a.kind == QMC_RLAT_HASH;
-  if ((a.s & 3u) == 0 && (uint64_t)32 * a.spp * a.s <= (1ull << 31) && aligned16(a.out_u32) &&
-      aligned16(a.out_f32)) {
+  const uint64_t Rs = (uint64_t)a.s << a.r_log2;
+  // batch: up to 48 KiB of generator words (at least one pixel), at most 256 pixels
+  uint64_t pixels = (48u * 1024u / 4u) / Rs;
+  if (pixels > 256) pixels = 256;
+  if (pixels < 1) pixels = 1;
+  a.batch_pixels = (uint32_t)pixels;
+  const size_t smem =
+      ((hash ? 0 : (size_t)kJumpLevels * kLfsrJumpWords) + ((2 * pixels + 3) & ~3ull) + pixels * Rs) * sizeof(uint32_t);
+  if ((a.s & 3u) == 0 && pixels * a.spp * a.s <= (1ull << 31) && aligned16(a.out_u32) && aligned16(a.out_f32) &&
+      smem <= dev.smem_per_block_optin) {
     const auto kernel = hash ? random_lattice_points_fast<QMC_RLAT_HASH> : random_lattice_points_fast<QMC_RLAT_LFSR>;
+    if (smem > 48 * 1024) {
+      const cudaError_t ea = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (ea != cudaSuccess) return ea;
+    }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
     if (e != cudaSuccess) return e;
     uint64_t blocks = (uint64_t)dev.sm_count * (per_sm < 1 ? 1 : per_sm);
-    const uint64_t need = (((a.n_pixels + 31) >> 5) + kThreads / 32 - 1) / (kThreads / 32);
-    if (need < blocks) blocks = need;
+    const uint64_t batches = (a.n_pixels + pixels - 1) / pixels;
+    if (batches < blocks) blocks = batches;
     if (blocks < 1) blocks = 1;
-    kernel<<<(unsigned)blocks, kThreads, 0, stream>>>(a);
+    kernel<<<(unsigned)blocks, kThreads, smem, stream>>>(a);
     return cudaGetLastError();
   }
   uint64_t blocks = (a.n_pixels * a.spp * a.s + kThreads - 1) / kThreads;

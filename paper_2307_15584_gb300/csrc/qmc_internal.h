@@ -60,6 +60,7 @@ struct RandomPointsArgs {
   uint64_t pixel_begin, n_pixels;
   uint32_t spp, s, width;
   uint32_t kind, seed, r_log2;  // qmc_rlat_kind, hash seed, log2 of the instance count
+  uint32_t batch_pixels;        // set by the launcher: pixels per shared-memory batch
 };
 
 cudaError_t launch_random_lattice_points(const RandomPointsArgs& a, cudaStream_t stream);
