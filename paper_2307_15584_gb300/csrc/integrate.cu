@@ -508,7 +508,7 @@ struct Integrand<QMC_F_GAUSSMIX4_6D> {
       for (int d = 0; d < 6; ++d) {
         const float diff = __fmaf_rn(X[d], 0x1p-32f, (d & 1) ? -nu[c] : -mu[c]);  // x - m, one rounding
         q = __fmaf_rn(diff, diff, q);
-        if constexpr (SUMS) {
+        if constexpr (SUMS) {  // the differences themselves: sum x - 3 mu would cancel near the mean
           if (d & 1) so = __fadd_rn(so, diff); else se = __fadd_rn(se, diff);
         }
       }
@@ -557,9 +557,13 @@ struct Integrand<QMC_F_GAUSSMIX4_6D> {
     return f;
   }
 
-  // f and df/dtheta (theta order w, mu, nu, sigma per component)
+  // f and the per-sample factors of df/dtheta (theta order w, mu, nu, sigma per
+  // component): gq[4c..4c+3] = (G_c, sum_even (x_d - mu_c), sum_odd (x_d - nu_c),
+  // q_c), so that df/dw = G, df/dmu = (w / sigma^2) G se, df/dnu = (w / sigma^2)
+  // G so, df/dsigma = (w / sigma^3) G q.  The constant factors multiply the
+  // item's sums once (grad_scale) instead of every sample.
   template <bool EXACT>
-  __device__ __forceinline__ float eval_grad(const float* x, float* g, float& err) const {
+  __device__ __forceinline__ float eval_grad(const float* x, float* gq, float& err) const {
     float f = 0.0f;
     err = 0.0f;
 #pragma unroll
@@ -567,15 +571,20 @@ struct Integrand<QMC_F_GAUSSMIX4_6D> {
       float q, t, se = 0.0f, so = 0.0f;
       const float G = gauss<EXACT, true>(x, c, q, t, se, so);
       const float wG = __fmul_rn(w[c], G);
-      const float wg2 = __fmul_rn(wG, is2[c]);
       f = __fadd_rn(f, wG);
       err = __fmaf_rn(fabsf(wG), t, err);
-      g[4 * c + 0] = G;
-      g[4 * c + 1] = __fmul_rn(wg2, se);
-      g[4 * c + 2] = __fmul_rn(wg2, so);
-      g[4 * c + 3] = __fmul_rn(__fmul_rn(wG, is3[c]), q);
+      gq[4 * c + 0] = G;
+      gq[4 * c + 1] = se;
+      gq[4 * c + 2] = so;
+      gq[4 * c + 3] = q;
     }
     return f;
+  }
+
+  // factor of value v (1..16, theta order) that eval_grad's sums leave out
+  __device__ __forceinline__ float grad_scale(int v) const {
+    const int c = (v - 1) >> 2, k = (v - 1) & 3;
+    return k == 0 ? 1.0f : k == 3 ? __fmul_rn(w[c], is3[c]) : __fmul_rn(w[c], is2[c]);
   }
 };
 
@@ -639,12 +648,18 @@ __device__ __forceinline__ void run_item(const Src& src, const F& f, uint32_t le
       src.point(r, il, valid, x);
       float err;
       if constexpr (GRAD) {
-        float g[16];
-        const float v = f.template eval_grad<EXACT>(x, g, err);
+        float gq[16];
+        const float v = f.template eval_grad<EXACT>(x, gq, err);
         if (valid) {
           blk[0] = __fadd_rn(blk[0], v);
 #pragma unroll
-          for (int k = 0; k < 16; ++k) blk[1 + k] = __fadd_rn(blk[1 + k], g[k]);
+          for (int c = 0; c < 4; ++c) {
+            const float G = gq[4 * c];
+            blk[1 + 4 * c] = __fadd_rn(blk[1 + 4 * c], G);
+            blk[2 + 4 * c] = __fmaf_rn(G, gq[4 * c + 1], blk[2 + 4 * c]);
+            blk[3 + 4 * c] = __fmaf_rn(G, gq[4 * c + 2], blk[3 + 4 * c]);
+            blk[4 + 4 * c] = __fmaf_rn(G, gq[4 * c + 3], blk[4 + 4 * c]);
+          }
           if constexpr (F::kAdaptive && !EXACT) e2 = __fmaf_rn(err, err, e2);
         }
       } else {
@@ -709,9 +724,13 @@ __global__ void __launch_bounds__(256) integrate_main(IntegrateArgs a) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const Comp c = warp_comp_sum(acc[v].comp());
+      float k = 1.0f;
+      if constexpr (GRAD) {
+        if (v > 0) k = f.grad_scale(v);
+      }
       if (lane == (uint32_t)(v & 31)) {
-        out[2 * v] = c.sum;
-        out[2 * v + 1] = c.err;
+        out[2 * v] = __fmul_rn(c.sum, k);
+        out[2 * v + 1] = __fmul_rn(c.err, k);
       }
     }
     next = __shfl_sync(0xffffffffu, next, 0);
