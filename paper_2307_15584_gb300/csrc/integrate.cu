@@ -671,7 +671,14 @@ __device__ __forceinline__ void run_item(const Src& src, const F& f, uint32_t le
       }
     }
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v].add(blk[v]);
+    for (int v = 0; v < NV; ++v) {
+      // The estimate keeps the compensated sum.  The parameter gradients are
+      // held to a tolerance relative to the mean absolute derivative, which a
+      // plain sum of the lane's block sums meets with a wide margin (about
+      // (kBlock - 1 + blocks) unit roundoffs of the sum of absolute terms).
+      if (v == 0) acc[v].add(blk[v]);
+      else acc[v].s = __fadd_rn(acc[v].s, blk[v]);
+    }
   }
 }
 
