@@ -162,15 +162,17 @@ __global__ void __launch_bounds__(kScanThreads) scan_write(IntegrateArgs a) {
 // ---------------------------------------------------------------------------
 template <int S, int SCR>  // SCR: 0 none, 1 XOR, 2 nested
 struct SobolSource {
+  static constexpr int kRow = (S + 3) & ~3;  // table row stride: whole 128-bit words
   const uint32_t* cols;  // shared: [s][32], mirrored when nested
-  const uint32_t* tab;   // shared: [C/32][S], y(32 r)
+  const uint32_t* tab;   // shared: [C/32][kRow], y(32 r)
   uint32_t s;
   uint32_t lane_y[S];    // y(lane)
   uint32_t yl[S];        // y(start) ^ y(lane) (^ seed for XOR)
   NestedKey key[S];
 
+  // the columns first (a multiple of 32 words keeps the table 16-byte aligned)
   static size_t smem_bytes(uint32_t s, uint32_t chunk_log2) {
-    return ((size_t)s * 32 + ((size_t)1 << (chunk_log2 - 5)) * S) * sizeof(uint32_t);
+    return ((size_t)s * 32 + ((size_t)1 << (chunk_log2 - 5)) * kRow) * sizeof(uint32_t);
   }
 
   __device__ void kernel_setup(const IntegrateArgs& a, uint32_t* smem) {
@@ -183,8 +185,8 @@ struct SobolSource {
     }
     __syncthreads();
     const uint32_t rows = 1u << (a.chunk_log2 - 5);
-    for (uint32_t i = threadIdx.x; i < rows * S; i += blockDim.x) {
-      const uint32_t r = i / S, j = i - r * S;
+    for (uint32_t i = threadIdx.x; i < rows * kRow; i += blockDim.x) {
+      const uint32_t r = i / kRow, j = i - r * kRow;
       uint32_t y = 0;
       if (j < s)
         for (uint32_t b = 0; (r >> b) != 0; ++b)
@@ -221,7 +223,12 @@ struct SobolSource {
   }
 
   __device__ __forceinline__ void point(uint32_t r, uint32_t /*il*/, bool /*valid*/, float* x) const {
-    const uint32_t* row = tab + r * S;
+    uint32_t row[kRow];
+#pragma unroll
+    for (int q = 0; q < kRow / 4; ++q) {  // 128-bit shared loads
+      const uint4 w = reinterpret_cast<const uint4*>(tab + r * kRow)[q];
+      row[4 * q] = w.x, row[4 * q + 1] = w.y, row[4 * q + 2] = w.z, row[4 * q + 3] = w.w;
+    }
 #pragma unroll
     for (int j = 0; j < S; ++j) {
       uint32_t y = row[j] ^ yl[j];
