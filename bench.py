@@ -138,7 +138,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-POINTS_SOURCES = ["points.cu", "qmc_device.cuh", "qmc_internal.h"]
+POINTS_SOURCES = ["sobol_points.cu", "points_common.cuh", "qmc_device.cuh", "qmc_internal.h"]
 INTEGRATE_SOURCES = ["integrate.cu", "qmc_device.cuh", "qmc_integrate.h", "qmc_internal.h"]
 KERNEL_SOURCES = {"sobol_points_fast<1,2>": POINTS_SOURCES}
 

@@ -1,0 +1,375 @@
+// lattice_points.cu -- materialised rank-1 lattice points (HBM-write bound):
+//   lattice_points_*          Eq. (R1LS) / Alg. 4: x_j(k) = phi_2(k) g_j + shift_j mod 2^32,
+//                             forward or backward;
+//   pixel_lattice_points_*    Sec. 3, Eq. (PixelShiftedR1LS): one phi_3 shift per pixel
+//                             along the Hilbert curve;
+//   random_lattice_points_*   Alg. 4, Sec. 2.4.2, Sec. 3: a random generator vector per
+//                             pixel (hashed or LFSR) and superimposed instances.
+// Layouts as in sobol_points.cu: rows [count][s] u32/f32, coalesced 16-byte chunks;
+// phi_2 of disjoint index bit fields adds without carries, so the rank-1 lattice
+// takes x = phi_2(G*Q) g_j + lo_e with one bit reversal per group.
+#include <cstdint>
+
+#include "points_common.cuh"
+
+namespace qmc {
+
+namespace {
+using namespace pts;
+
+// ---------------------------------------------------------------------------
+// K2: rank-1 lattice.  BACKWARD follows Alg. 4: phi_2(~k) = ~phi_2(k), so
+// x = shift - g - phi_2(k) g (mod 2^32).
+// ---------------------------------------------------------------------------
+template <int K, bool BACKWARD, bool TMA>
+__global__ void __launch_bounds__(kThreads) lattice_points_fast(PointsArgs a) {
+  extern __shared__ __align__(128) uint32_t smem[];
+  const uint32_t lane = threadIdx.x & 31u;
+  WarpStager<K> stager(smem + (threadIdx.x >> 5) * WarpStager<K>::kWarpWords);
+  const uint32_t s = a.s;
+  const uint32_t Q = 1u << a.q_log2;
+  uint32_t gj[4 * K], lo[4 * K];
+#pragma unroll
+  for (int c = 0; c < K; ++c)
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const uint32_t e = 4u * (lane + 32u * c) + t;
+      const uint32_t p = e / s, j = e - p * s;
+      const uint32_t g = __ldg(a.matrices + j) | 1u;  // generator words
+      const uint32_t sh = a.seeds ? __ldg(a.seeds + j) : 0u;
+      const uint32_t phi_p = __brev(p);
+      gj[4 * c + t] = g;
+      lo[4 * c + t] = BACKWARD ? sh - g - phi_p * g : phi_p * g + sh;
+    }
+  const uint64_t n_groups = (a.count + Q - 1) >> a.q_log2;
+  const uint64_t full_groups = a.count >> a.q_log2;
+  uint64_t g0, g1;
+  warp_range(n_groups, g0, g1);
+  const uint32_t G_first = (uint32_t)(a.index_begin >> a.q_log2);
+  const uint64_t step = (uint64_t)Q * s;
+  uint64_t off = g0 * step + 4u * lane;
+  for (uint64_t g = g0; g < g1; ++g, off += step) {
+    const uint32_t phib = __brev((G_first + (uint32_t)g) << a.q_log2);
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      uint32_t v[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        v[t] = BACKWARD ? lo[4 * c + t] - phib * gj[4 * c + t] : phib * gj[4 * c + t] + lo[4 * c + t];
+      const uint64_t o = off + 128u * c;
+      if (g < full_groups) {
+        if (TMA)
+          stager.put(lane, c, v);
+        else
+          store4(a.out_u32, a.out_f32, o, v);
+      } else {  // ragged last group: per-element row test
+        const uint64_t rows_left = a.count - (g << a.q_log2);
+        const uint32_t e0 = 4u * (lane + 32u * c);
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if ((uint64_t)((e0 + t) / s) < rows_left) store1(a.out_u32, a.out_f32, o + t, v[t]);
+      }
+    }
+    if (TMA && g < full_groups)
+      stager.group_done(lane, off, g + 1 == g1 || g + 1 == full_groups, a.out_u32, a.out_f32);
+  }
+  if (TMA) stager.finish(lane);
+}
+
+template <bool BACKWARD>
+__global__ void __launch_bounds__(kThreads) lattice_points_generic(PointsArgs a) {
+  const uint64_t total = a.count * a.s;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += stride) {
+    const uint64_t r = f / a.s;
+    const uint32_t j = (uint32_t)(f - r * a.s);
+    const uint32_t k = (uint32_t)a.index_begin + (uint32_t)r;
+    const uint32_t phi = __brev(BACKWARD ? ~k : k);
+    const uint32_t g = __ldg(a.matrices + j) | 1u;
+    const uint32_t sh = a.seeds ? __ldg(a.seeds + j) : 0u;
+    store1(a.out_u32, a.out_f32, f, phi * g + sh);
+  }
+}
+
+// Pixel-shifted lattice, coalesced path (s % 4 == 0, 16-byte aligned outputs,
+// 32 spp s <= 2^31).  A warp takes batches of 32 consecutive pixels: lane l
+// computes the shift of pixel l of the batch once (Hilbert position, then
+// phi_3), and the batch's 32 spp rows are written as consecutive 16-byte chunks,
+// each chunk's pixel shift fetched from its lane with a shuffle.
+__global__ void __launch_bounds__(kThreads) pixel_lattice_points_fast(PixelPointsArgs a) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t n_batches = (a.n_pixels + 31) >> 5;
+  uint64_t b0, b1;
+  warp_range(n_batches, b0, b1);
+  // x / d = umulhi(x, floor(2^64 / d) + 1) exactly for x < 2^32 and d > 1
+  const uint64_t mag_s = ~0ull / a.s + 1;  // s >= 4
+  const uint64_t mag_spp = a.spp > 1 ? ~0ull / a.spp + 1 : 0;
+  const uint32_t chunks_per_pixel = a.spp * (a.s >> 2);
+  for (uint64_t b = b0; b < b1; ++b) {
+    const uint64_t first = b << 5;  // batch's first pixel, relative to pixel_begin
+    const uint64_t left = a.n_pixels - first;
+    const uint32_t npx = left < 32 ? (uint32_t)left : 32u;
+    uint32_t sh = 0;
+    if (lane < npx) {
+      const uint64_t p = a.pixel_begin + first + lane;
+      sh = pixel_shift((uint32_t)(p % a.width), (uint32_t)(p / a.width), a.grid_log2);
+    }
+    const uint32_t chunks = npx * chunks_per_pixel;
+    const uint64_t off0 = first * a.spp * a.s;  // element offset of the batch
+    for (uint32_t c0 = 0; c0 < chunks; c0 += 32) {  // same trip count in every lane
+      const uint32_t c = c0 + lane;
+      const uint32_t e = 4u * c;  // element within the batch, < 2^32
+      const uint32_t row = (uint32_t)__umul64hi(e, mag_s);
+      const uint32_t j = e - row * a.s;
+      const uint32_t pl = a.spp > 1 ? (uint32_t)__umul64hi(row, mag_spp) : row;
+      const uint32_t smp = row - pl * a.spp;
+      const uint32_t shift = __shfl_sync(0xffffffffu, sh, pl & 31u);
+      if (c < chunks) {
+        const uint32_t base = __brev(smp) + shift;
+        const uint32_t v[4] = {base * (__ldg(a.g + j) | 1u), base * (__ldg(a.g + j + 1) | 1u),
+                               base * (__ldg(a.g + j + 2) | 1u), base * (__ldg(a.g + j + 3) | 1u)};
+        store4(a.out_u32, a.out_f32, off0 + e, v);
+      }
+    }
+  }
+}
+
+
+// Pixel-shifted rank-1 lattice (Sec. 3): one thread per (pixel, sample) row;
+// row r holds sample r % spp of pixel pixel_begin + r / spp.
+__global__ void __launch_bounds__(kThreads) pixel_lattice_points_kernel(PixelPointsArgs a) {
+  const uint64_t rows = a.n_pixels * a.spp;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride) {
+    const uint64_t p = a.pixel_begin + r / a.spp;
+    const uint32_t i = (uint32_t)(r % a.spp);
+    const uint32_t shift = pixel_shift((uint32_t)(p % a.width), (uint32_t)(p / a.width), a.grid_log2);
+    const uint32_t base = __brev(i) + shift;
+    for (uint32_t j = 0; j < a.s; ++j) store1(a.out_u32, a.out_f32, r * a.s + j, base * (__ldg(a.g + j) | 1u));
+  }
+}
+
+
+// LFSR jump tables of the materialising kernels: level b advances a state by
+// 32 * 2^b steps (b < kJumpLevels), each level the square of the one below, so a
+// chunk reaches dimension j0 in popcount(j0) jumps.
+constexpr uint32_t kJumpLevels = 5;
+
+template <int KIND>
+__device__ __forceinline__ void rlat_jump_tables_fill(uint32_t* jump) {
+  if (KIND != QMC_RLAT_LFSR) return;
+  lfsr_jump_table_fill(jump);
+  __syncthreads();
+  for (uint32_t b = 1; b < kJumpLevels; ++b) {
+    const uint32_t* lower = jump + (b - 1) * kLfsrJumpWords;
+    for (uint32_t e = threadIdx.x; e < kLfsrJumpWords; e += blockDim.x) {
+      const uint32_t v = (e & 255u) << (8u * (e >> 8));
+      jump[b * kLfsrJumpWords + e] = lfsr_jump32(lower, lfsr_jump32(lower, v));
+    }
+    __syncthreads();
+  }
+}
+
+// Generator component j of instance k of pixel (px, py), for one chunk of
+// consecutive dimensions j0 .. j0+N-1 (LFSR: 32 register steps per dimension
+// from the pixel's seed state, taken through the jump tables).
+template <int KIND, int N>
+__device__ __forceinline__ void rlat_generators(uint32_t seed, uint32_t k, uint32_t j0, uint32_t px,
+                                                uint32_t py, const uint32_t* jump, uint32_t (&g)[N]) {
+  if (KIND == QMC_RLAT_HASH) {
+#pragma unroll
+    for (int q = 0; q < N; ++q) g[q] = rlat_hash(seed, k, j0 + q, px, py) | 1u;
+  } else {
+    uint32_t xi = rlat_lfsr_seed(seed, k, px, py);
+#pragma unroll
+    for (uint32_t b = 0; b + 1 < kJumpLevels; ++b)
+      if ((j0 >> b) & 1u) xi = lfsr_jump32(jump + b * kLfsrJumpWords, xi);
+    for (uint32_t u = 0; u < (j0 >> (kJumpLevels - 1)); ++u)
+      xi = lfsr_jump32(jump + (kJumpLevels - 1) * kLfsrJumpWords, xi);
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      g[q] = 2u * xi + 1u;
+      xi = lfsr_jump32(jump, xi);
+    }
+  }
+}
+
+// Coalesced path (s % 4 == 0, 16-byte aligned outputs, batch_pixels spp s <= 2^31).
+// A block takes batches of batch_pixels consecutive pixels: it first derives the
+// generator words of every (pixel, instance, dimension) of the batch into
+// shared memory ([pixel][R][s]; spp / R samples share each word), then writes
+// the batch's rows as consecutive 16-byte chunks, each chunk one sample and
+// four consecutive dimensions: one 128-bit shared load, four multiplies.
+template <int KIND>
+__global__ void __launch_bounds__(kThreads) random_lattice_points_fast(RandomPointsArgs a) {
+  extern __shared__ __align__(16) uint32_t rsm[];
+  uint32_t* jump = rsm;  // LFSR jump tables
+  uint32_t* pxy = rsm + (KIND == QMC_RLAT_LFSR ? kJumpLevels * kLfsrJumpWords : 0);  // [batch][2]
+  uint32_t* gvec = pxy + ((2 * a.batch_pixels + 3u) & ~3u);  // [batch][R][s], 16-byte aligned
+  rlat_jump_tables_fill<KIND>(jump);
+  const uint32_t s = a.s, R = 1u << a.r_log2, Rs = R * s;
+  const uint64_t mag_s = ~0ull / s + 1;  // s >= 4
+  const uint64_t mag_spp = a.spp > 1 ? ~0ull / a.spp + 1 : 0;
+  const uint64_t n_batches = (a.n_pixels + a.batch_pixels - 1) / a.batch_pixels;
+  for (uint64_t b = blockIdx.x; b < n_batches; b += gridDim.x) {
+    const uint64_t first = b * a.batch_pixels;
+    const uint64_t left = a.n_pixels - first;
+    const uint32_t npx = left < a.batch_pixels ? (uint32_t)left : a.batch_pixels;
+    __syncthreads();  // the previous batch's words are no longer read
+    for (uint32_t q = threadIdx.x; q < npx; q += blockDim.x) {
+      const uint64_t p = a.pixel_begin + first + q;
+      pxy[2 * q] = (uint32_t)(p % a.width);
+      pxy[2 * q + 1] = (uint32_t)(p / a.width);
+    }
+    __syncthreads();
+    if (KIND == QMC_RLAT_HASH) {  // every component independently
+      for (uint32_t idx = threadIdx.x; idx < npx * Rs; idx += blockDim.x) {
+        const uint32_t row = (uint32_t)__umul64hi(idx, mag_s);  // (pixel, instance)
+        const uint32_t j = idx - row * s, q = row >> a.r_log2;
+        gvec[idx] = rlat_hash(a.seed, row & (R - 1u), j, pxy[2 * q], pxy[2 * q + 1]) | 1u;
+      }
+    } else {  // one thread per (pixel, instance) walks the register through the dimensions
+      for (uint32_t w = threadIdx.x; w < npx * R; w += blockDim.x) {
+        const uint32_t q = w >> a.r_log2;
+        uint32_t xi = rlat_lfsr_seed(a.seed, w & (R - 1u), pxy[2 * q], pxy[2 * q + 1]);
+        for (uint32_t j = 0; j < s; ++j) {
+          gvec[w * s + j] = 2u * xi + 1u;
+          xi = lfsr_jump32(jump, xi);
+        }
+      }
+    }
+    __syncthreads();
+    const uint32_t chunks = npx * a.spp * (s >> 2);
+    const uint64_t off0 = first * a.spp * s;
+    for (uint32_t c = threadIdx.x; c < chunks; c += blockDim.x) {
+      const uint32_t e = 4u * c;  // element within the batch, < 2^31
+      const uint32_t row = (uint32_t)__umul64hi(e, mag_s);
+      const uint32_t j = e - row * s;
+      const uint32_t pl = a.spp > 1 ? (uint32_t)__umul64hi(row, mag_spp) : row;
+      const uint32_t t = row - pl * a.spp;
+      const uint4 g = *reinterpret_cast<const uint4*>(gvec + (pl * R + (t & (R - 1u))) * s + j);
+      const uint32_t phi = __brev(~(t >> a.r_log2));  // phi_2(2^32 - 1 - i), Alg. 4
+      const uint32_t v[4] = {phi * g.x, phi * g.y, phi * g.z, phi * g.w};
+      store4(a.out_u32, a.out_f32, off0 + e, v);
+    }
+  }
+}
+
+// Generic path: one element per thread.
+template <int KIND>
+__global__ void __launch_bounds__(kThreads) random_lattice_points_generic(RandomPointsArgs a) {
+  __shared__ uint32_t jump[KIND == QMC_RLAT_LFSR ? kJumpLevels * kLfsrJumpWords : 1];
+  rlat_jump_tables_fill<KIND>(jump);
+  const uint64_t total = a.n_pixels * a.spp * a.s;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += stride) {
+    const uint64_t row = f / a.s;
+    const uint32_t j = (uint32_t)(f - row * a.s);
+    const uint64_t q = row / a.spp;
+    const uint32_t t = (uint32_t)(row - q * a.spp);
+    const uint64_t p = a.pixel_begin + q;
+    uint32_t g[1];
+    rlat_generators<KIND, 1>(a.seed, t & ((1u << a.r_log2) - 1u), j, (uint32_t)(p % a.width),
+                             (uint32_t)(p / a.width), jump, g);
+    store1(a.out_u32, a.out_f32, f, __brev(~(t >> a.r_log2)) * g[0]);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_random_lattice_points(const RandomPointsArgs& args, cudaStream_t stream) {
+  const DeviceInfo& dev = device_info();
+  RandomPointsArgs a = args;
+  const bool hash = a.kind == QMC_RLAT_HASH;
+  const uint64_t Rs = (uint64_t)a.s << a.r_log2;
+  // batch: up to 48 KiB of generator words (at least one pixel), at most 256 pixels
+  uint64_t pixels = (48u * 1024u / 4u) / Rs;
+  if (pixels > 256) pixels = 256;
+  if (pixels < 1) pixels = 1;
+  a.batch_pixels = (uint32_t)pixels;
+  const size_t smem =
+      ((hash ? 0 : (size_t)kJumpLevels * kLfsrJumpWords) + ((2 * pixels + 3) & ~3ull) + pixels * Rs) * sizeof(uint32_t);
+  if ((a.s & 3u) == 0 && pixels * a.spp * a.s <= (1ull << 31) && aligned16(a.out_u32) && aligned16(a.out_f32) &&
+      smem <= dev.smem_per_block_optin) {
+    const auto kernel = hash ? random_lattice_points_fast<QMC_RLAT_HASH> : random_lattice_points_fast<QMC_RLAT_LFSR>;
+    if (smem > 48 * 1024) {
+      const cudaError_t ea = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (ea != cudaSuccess) return ea;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    uint64_t blocks = (uint64_t)dev.sm_count * (per_sm < 1 ? 1 : per_sm);
+    const uint64_t batches = (a.n_pixels + pixels - 1) / pixels;
+    if (batches < blocks) blocks = batches;
+    if (blocks < 1) blocks = 1;
+    kernel<<<(unsigned)blocks, kThreads, smem, stream>>>(a);
+    return cudaGetLastError();
+  }
+  uint64_t blocks = (a.n_pixels * a.spp * a.s + kThreads - 1) / kThreads;
+  const uint64_t cap = (uint64_t)dev.sm_count * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  if (hash)
+    random_lattice_points_generic<QMC_RLAT_HASH><<<(unsigned)blocks, kThreads, 0, stream>>>(a);
+  else
+    random_lattice_points_generic<QMC_RLAT_LFSR><<<(unsigned)blocks, kThreads, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pixel_lattice_points(const PixelPointsArgs& a, cudaStream_t stream) {
+  const DeviceInfo& dev = device_info();
+  if ((a.s & 3u) == 0 && (uint64_t)32 * a.spp * a.s <= (1ull << 31) && aligned16(a.out_u32) &&
+      aligned16(a.out_f32)) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pixel_lattice_points_fast, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    uint64_t blocks = (uint64_t)dev.sm_count * (per_sm < 1 ? 1 : per_sm);
+    const uint64_t need = (((a.n_pixels + 31) >> 5) + kThreads / 32 - 1) / (kThreads / 32);
+    if (need < blocks) blocks = need;
+    if (blocks < 1) blocks = 1;
+    pixel_lattice_points_fast<<<(unsigned)blocks, kThreads, 0, stream>>>(a);
+    return cudaGetLastError();
+  }
+  uint64_t blocks = (a.n_pixels * a.spp + kThreads - 1) / kThreads;
+  const uint64_t cap = (uint64_t)dev.sm_count * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  pixel_lattice_points_kernel<<<(unsigned)blocks, kThreads, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lattice_points(PointsArgs a, cudaStream_t stream) {
+  const bool backward = (a.scramble & 1u) != 0;
+  const uint32_t K = fast_k(a.s);
+  a.q_log2 = log2_exact(K ? 128u * K / a.s : 1u);
+  const bool fast = K != 0 && (a.index_begin & ((1ull << a.q_log2) - 1u)) == 0 && aligned16(a.out_u32) &&
+                    aligned16(a.out_f32);
+  if (!fast) {
+    return backward ? launch_grid_stride(lattice_points_generic<true>, a.count * a.s, stream, a)
+                    : launch_grid_stride(lattice_points_generic<false>, a.count * a.s, stream, a);
+  }
+  const uint64_t groups = (a.count + (1u << a.q_log2) - 1) >> a.q_log2;
+  // TMA bulk stores for device-memory outputs whose staging tiles fit (K <= 3)
+  const size_t stage = (size_t)(kThreads / 32) * 4 * kStageGroups * 128u * K * sizeof(uint32_t);
+  const bool tma = kPointsTma && device_resident(a.out_u32) && device_resident(a.out_f32) &&
+                   stage <= device_info().smem_per_block_optin;
+  const size_t smem = tma ? stage : 0;
+#define QMC_LATTICE_CASE(KK)                                                                                 \
+  case KK:                                                                                                   \
+    if (tma)                                                                                                 \
+      return backward ? launch_persistent(lattice_points_fast<KK, true, kPointsTma>, groups, smem, stream, a)  \
+                      : launch_persistent(lattice_points_fast<KK, false, kPointsTma>, groups, smem, stream, a); \
+    return backward ? launch_persistent(lattice_points_fast<KK, true, false>, groups, 0, stream, a)          \
+                    : launch_persistent(lattice_points_fast<KK, false, false>, groups, 0, stream, a);
+  switch (K) {
+    QMC_LATTICE_CASE(1)
+    QMC_LATTICE_CASE(2)
+    QMC_LATTICE_CASE(3)
+    QMC_LATTICE_CASE(4)
+    default: return cudaErrorInvalidValue;
+  }
+#undef QMC_LATTICE_CASE
+}
+
+}  // namespace qmc
