@@ -425,11 +425,19 @@ struct Integrand<QMC_F_GENZ_PRODUCT_PEAK> {
   __device__ __forceinline__ float eval(const float* x, float& err) const {
     err = 0.0f;
     float prod = 1.0f;
+    if (s == 16) {  // every dimension (a warp-uniform branch: no per-dimension test)
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      if ((uint32_t)j < s) {
+      for (int j = 0; j < 16; ++j) {
         const float d = __fmaf_rn(x[j], 0x1p-32f, -u[j]);  // x - u, one rounding
         prod = __fmul_rn(prod, __fadd_rn(__fmaf_rn(d, d, ch[j]), cl[j]));
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if ((uint32_t)j < s) {
+          const float d = __fmaf_rn(x[j], 0x1p-32f, -u[j]);
+          prod = __fmul_rn(prod, __fadd_rn(__fmaf_rn(d, d, ch[j]), cl[j]));
+        }
       }
     }
     return __frcp_rn(prod);
@@ -456,8 +464,7 @@ struct Integrand<QMC_F_GENZ_OSCILLATORY> {
     err = 0.0f;
     float B = 0.0f;
 #pragma unroll
-    for (int j = 0; j < 16; ++j)
-      if ((uint32_t)j < s) B = __fmaf_rn(a[j], x[j], B);
+    for (int j = 0; j < 16; ++j) B = __fmaf_rn(a[j], x[j], B);  // a_j = 0 beyond s adds exactly 0
     float sb, cb;
     sincosf(B, &sb, &cb);
     return __fmaf_rn(c0, cb, -__fmul_rn(s0, sb));
