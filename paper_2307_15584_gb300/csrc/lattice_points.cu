@@ -203,11 +203,16 @@ __device__ __forceinline__ void rlat_generators(uint32_t seed, uint32_t k, uint3
 template <int KIND>
 __global__ void __launch_bounds__(kThreads) random_lattice_points_fast(RandomPointsArgs a) {
   extern __shared__ __align__(16) uint32_t rsm[];
-  uint32_t* jump = rsm;  // LFSR jump tables
-  uint32_t* pxy = rsm + (KIND == QMC_RLAT_LFSR ? kJumpLevels * kLfsrJumpWords : 0);  // [batch][2]
-  uint32_t* gvec = pxy + ((2 * a.batch_pixels + 3u) & ~3u);  // [batch][R][s], 16-byte aligned
-  rlat_jump_tables_fill<KIND>(jump);
-  const uint32_t s = a.s, R = 1u << a.r_log2, Rs = R * s;
+  uint32_t* jump = rsm;  // LFSR: the 32-step jump table (the walk below needs no other level)
+  uint32_t* pxy = rsm + (KIND == QMC_RLAT_LFSR ? kLfsrJumpWords : 0);  // [batch][2]
+  // generator words [batch][R][stride]: a row stride of s + 4 keeps rows 16-byte aligned and
+  // spreads the LFSR walk's per-thread rows over the banks (4-way instead of 32-way conflicts)
+  uint32_t* gvec = pxy + ((2 * a.batch_pixels + 3u) & ~3u);
+  if (KIND == QMC_RLAT_LFSR) {
+    lfsr_jump_table_fill(jump);
+    __syncthreads();
+  }
+  const uint32_t s = a.s, R = 1u << a.r_log2, Rs = R * s, stride = s + 4u;
   const uint64_t mag_s = ~0ull / s + 1;  // s >= 4
   const uint64_t mag_spp = a.spp > 1 ? ~0ull / a.spp + 1 : 0;
   const uint64_t n_batches = (a.n_pixels + a.batch_pixels - 1) / a.batch_pixels;
@@ -226,14 +231,14 @@ __global__ void __launch_bounds__(kThreads) random_lattice_points_fast(RandomPoi
       for (uint32_t idx = threadIdx.x; idx < npx * Rs; idx += blockDim.x) {
         const uint32_t row = (uint32_t)__umul64hi(idx, mag_s);  // (pixel, instance)
         const uint32_t j = idx - row * s, q = row >> a.r_log2;
-        gvec[idx] = rlat_hash(a.seed, row & (R - 1u), j, pxy[2 * q], pxy[2 * q + 1]) | 1u;
+        gvec[row * stride + j] = rlat_hash(a.seed, row & (R - 1u), j, pxy[2 * q], pxy[2 * q + 1]) | 1u;
       }
     } else {  // one thread per (pixel, instance) walks the register through the dimensions
       for (uint32_t w = threadIdx.x; w < npx * R; w += blockDim.x) {
         const uint32_t q = w >> a.r_log2;
         uint32_t xi = rlat_lfsr_seed(a.seed, w & (R - 1u), pxy[2 * q], pxy[2 * q + 1]);
         for (uint32_t j = 0; j < s; ++j) {
-          gvec[w * s + j] = 2u * xi + 1u;
+          gvec[w * stride + j] = 2u * xi + 1u;
           xi = lfsr_jump32(jump, xi);
         }
       }
@@ -247,7 +252,7 @@ __global__ void __launch_bounds__(kThreads) random_lattice_points_fast(RandomPoi
       const uint32_t j = e - row * s;
       const uint32_t pl = a.spp > 1 ? (uint32_t)__umul64hi(row, mag_spp) : row;
       const uint32_t t = row - pl * a.spp;
-      const uint4 g = *reinterpret_cast<const uint4*>(gvec + (pl * R + (t & (R - 1u))) * s + j);
+      const uint4 g = *reinterpret_cast<const uint4*>(gvec + (pl * R + (t & (R - 1u))) * stride + j);
       const uint32_t phi = __brev(~(t >> a.r_log2));  // phi_2(2^32 - 1 - i), Alg. 4
       const uint32_t v[4] = {phi * g.x, phi * g.y, phi * g.z, phi * g.w};
       store4(a.out_u32, a.out_f32, off0 + e, v);
@@ -281,14 +286,14 @@ cudaError_t launch_random_lattice_points(const RandomPointsArgs& args, cudaStrea
   const DeviceInfo& dev = device_info();
   RandomPointsArgs a = args;
   const bool hash = a.kind == QMC_RLAT_HASH;
-  const uint64_t Rs = (uint64_t)a.s << a.r_log2;
+  const uint64_t Rrow = (uint64_t)(a.s + 4) << a.r_log2;  // words per pixel (padded rows)
   // batch: up to 48 KiB of generator words (at least one pixel), at most 256 pixels
-  uint64_t pixels = (48u * 1024u / 4u) / Rs;
+  uint64_t pixels = (48u * 1024u / 4u) / Rrow;
   if (pixels > 256) pixels = 256;
   if (pixels < 1) pixels = 1;
   a.batch_pixels = (uint32_t)pixels;
   const size_t smem =
-      ((hash ? 0 : (size_t)kJumpLevels * kLfsrJumpWords) + ((2 * pixels + 3) & ~3ull) + pixels * Rs) * sizeof(uint32_t);
+      ((hash ? 0 : (size_t)kLfsrJumpWords) + ((2 * pixels + 3) & ~3ull) + pixels * Rrow) * sizeof(uint32_t);
   if ((a.s & 3u) == 0 && pixels * a.spp * a.s <= (1ull << 31) && aligned16(a.out_u32) && aligned16(a.out_f32) &&
       smem <= dev.smem_per_block_optin) {
     const auto kernel = hash ? random_lattice_points_fast<QMC_RLAT_HASH> : random_lattice_points_fast<QMC_RLAT_LFSR>;
