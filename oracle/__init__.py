@@ -26,7 +26,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 SOURCE_SOBOL, SOURCE_LATTICE, SOURCE_PIXEL_LATTICE, SOURCE_RANDOM_LATTICE = 0, 1, 2, 3
 RLAT_HASH, RLAT_LFSR = 0, 1
 SCRAMBLE_NONE, SCRAMBLE_XOR, SCRAMBLE_NESTED = 0, 1, 2
-F_BILINEAR2D, F_GENZ_PRODUCT_PEAK, F_GENZ_OSCILLATORY, F_GAUSSMIX4_6D = 0, 1, 2, 3
+F_BILINEAR2D, F_GENZ_PRODUCT_PEAK, F_GENZ_OSCILLATORY, F_GAUSSMIX4_6D, F_SCENE4D = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:

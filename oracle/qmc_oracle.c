@@ -28,7 +28,9 @@
  * SplitMix64 against its published outputs, the LFSR against polynomial
  * arithmetic and a primitivity test, the per-pixel random lattice against
  * exact rational arithmetic and the Latin hypercube property of odd
- * generators.
+ * generators.  The procedural scene: its light-square integral against a closed form
+ * (itself checked by quadrature), its fp32 visibility and checker decisions
+ * against fp64 geometry.
  *
  * Parity unpinned beyond those properties: the particular values of
  * qo_rlat_hash (Alg. 4's hash_value is not defined by the paper; this
@@ -54,7 +56,8 @@ enum {
     QO_F_BILINEAR2D = 0,
     QO_F_GENZ_PRODUCT_PEAK = 1,
     QO_F_GENZ_OSCILLATORY = 2,
-    QO_F_GAUSSMIX4_6D = 3
+    QO_F_GAUSSMIX4_6D = 3,
+    QO_F_SCENE4D = 4
 };
 
 /* ------------------------------------------------------------------------ */
@@ -635,6 +638,48 @@ static void neu_add(neumaier* a, double v)
     a->s = t;
 }
 
+/* ------------------------------------------------------------------------ */
+/* A procedural scene standing in for Fig. 1's rendering: the irradiance that */
+/* a square area light delivers through a spherical occluder onto a          */
+/* checkerboard ground plane, seen orthographically from above.              */
+/* ------------------------------------------------------------------------ */
+
+/* The scene function of a 4-D sample (x0, x1: position in the pixel's footprint
+ * on the plane z = 0; x2, x3: position on the light), theta[16] =
+ *   (fx, fy, fw, fh,  cx, cy, h, side,  Le,  ox, oy, oz, rho,  freq, 0, 0):
+ * P = (fx + fw x0, fy + fh x1, 0); L = (cx + side (x2 - 1/2), cy + side (x3 - 1/2), h),
+ * a light facing down; occluder = sphere (ox, oy, oz) of radius rho inside the
+ * slab 0 < z < h.  f = albedo(P) V(P, L) Le side^2 h^2 / |L - P|^4 (the geometry
+ * term cos cos / d^2 of two facing horizontal surfaces times the light's area),
+ * albedo 0.8 or 0.2 by the parity of floor(freq P_x) + floor(freq P_y).
+ * The two decisions -- the checker cell and whether the segment P-L meets the
+ * sphere (the discriminant of |P + t (L - P) - O|^2 = rho^2 is >= 0; with the
+ * sphere inside the slab every meeting lies inside the segment) -- are taken in
+ * fp32 with each operation rounded separately in the order written here, the
+ * precision the GPU takes them in; the shading value is fp64. */
+static double f_scene(const double* x, const float* th)
+{
+    float u0 = (float)x[0], u1 = (float)x[1], u2 = (float)x[2], u3 = (float)x[3];  /* exact */
+    float Px = th[0] + th[2] * u0;
+    float Py = th[1] + th[3] * u1;
+    float Lx = th[4] + th[7] * (u2 - 0.5f);
+    float Ly = th[5] + th[7] * (u3 - 0.5f);
+    float Dx = Lx - Px, Dy = Ly - Py, Dz = th[6];
+    float Ex = Px - th[9], Ey = Py - th[10], Ez = -th[11];
+    float DE = (Dx * Ex + Dy * Ey) + Dz * Ez;
+    float DD = (Dx * Dx + Dy * Dy) + Dz * Dz;
+    float EE = (Ex * Ex + Ey * Ey) + Ez * Ez;
+    float disc = DE * DE - DD * (EE - th[12] * th[12]);
+    if (!(disc < 0.0f)) return 0.0;  /* the sphere blocks the light */
+    int cell = ((int)floorf(Px * th[13]) + (int)floorf(Py * th[13])) & 1;
+    double albedo = cell ? 0.8 : 0.2;
+    double px = (double)th[0] + (double)th[2] * x[0], py = (double)th[1] + (double)th[3] * x[1];
+    double lx = (double)th[4] + (double)th[7] * (x[2] - 0.5), ly = (double)th[5] + (double)th[7] * (x[3] - 0.5);
+    double h = th[6];
+    double d2 = (lx - px) * (lx - px) + (ly - py) * (ly - py) + h * h;
+    return albedo * (double)th[8] * (double)th[7] * (double)th[7] * h * h / (d2 * d2);
+}
+
 /* QMC estimate (1/n) sum_{i<n} f(x_i; theta) of one integral.
  *   source 0 (Sobol'): x_i = Sobol' point i of C[s][32] randomised by
  *     `scramble` with seeds[s];
@@ -657,7 +702,8 @@ QO_EXPORT int qo_integrate_one(uint32_t source, uint32_t integrand, uint32_t s,
     if (s == 0 || s > 32) return -1;
     if (integrand == QO_F_BILINEAR2D && s != 2) return -1;
     if (integrand == QO_F_GAUSSMIX4_6D && s != 6) return -1;
-    if (integrand > QO_F_GAUSSMIX4_6D || source > QO_SOURCE_RANDOM_LATTICE) return -1;
+    if (integrand == QO_F_SCENE4D && s != 4) return -1;
+    if (integrand > QO_F_SCENE4D || source > QO_SOURCE_RANDOM_LATTICE) return -1;
     if (source == QO_SOURCE_RANDOM_LATTICE && (!seeds || (scramble >> 8) == 0)) return -1;
 
     neumaier sum = {0, 0}, abs_sum = {0, 0};
@@ -684,6 +730,7 @@ QO_EXPORT int qo_integrate_one(uint32_t source, uint32_t integrand, uint32_t s,
         case QO_F_BILINEAR2D: f = f_bilinear(x); break;
         case QO_F_GENZ_PRODUCT_PEAK: f = f_genz_product_peak(x, s, theta); break;
         case QO_F_GENZ_OSCILLATORY: f = f_genz_oscillatory(x, s, theta); break;
+        case QO_F_SCENE4D: f = f_scene(x, theta); break;
         default: f = f_gaussmix(x, theta, grad ? df : NULL); break;
         }
         neu_add(&sum, f);
@@ -714,6 +761,7 @@ QO_EXPORT double qo_integrand(uint32_t integrand, uint32_t s, const double* x,
     case QO_F_BILINEAR2D: return f_bilinear(x);
     case QO_F_GENZ_PRODUCT_PEAK: return f_genz_product_peak(x, s, theta);
     case QO_F_GENZ_OSCILLATORY: return f_genz_oscillatory(x, s, theta);
+    case QO_F_SCENE4D: return f_scene(x, theta);
     default: return f_gaussmix(x, theta, grad);
     }
 }

@@ -130,6 +130,25 @@ def gaussmix_theta_image(width: int, height: int, seed: int = DEFAULT_SEED) -> n
     return th.reshape(height * width, 16).astype(np.float32)
 
 
+def scene_theta(width: int, height: int, freq: float = 8.0, occluder: bool = True) -> np.ndarray:
+    """fp32 [height * width][16]: per-pixel parameters of the procedural scene
+    (row-major pixels): the pixel's footprint on the ground plane (the image
+    covers [0, width/height] x [0, 1], square pixels), then the scene shared by
+    all pixels -- a square light of side 0.3 and radiance 1 at height 1 above the
+    image centre, a sphere of radius 0.12 centred at 35 % of that height, offset
+    towards the origin, and a checkerboard of `freq` cells per unit length."""
+    aspect = width / height
+    p = np.arange(width * height)
+    th = np.zeros((width * height, 16), np.float64)
+    th[:, 0] = (p % width) / height
+    th[:, 1] = (p // width) / height
+    th[:, 2] = th[:, 3] = 1.0 / height
+    th[:, 4:9] = [0.5 * aspect, 0.5, 1.0, 0.3, 1.0]
+    th[:, 9:13] = [0.45 * aspect, 0.45, 0.35, 0.12 if occluder else 0.0]
+    th[:, 13] = freq
+    return th.astype(np.float32)
+
+
 def gaussmix_target(theta_star: np.ndarray) -> np.ndarray:
     """Synthetic target image: the exact integral of the mixture at parameters theta_star.
 
