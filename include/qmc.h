@@ -91,12 +91,25 @@ typedef enum qmc_rlat_kind {
  *   GENZ_OSCILLATORY    1 <= s <= 16, theta = a[s], u[s]: cos(2 pi u_1 + sum_j a_j x_j)
  *   GAUSSMIX4_6D        s = 6, theta[16] = 4 x (w, mu, nu, sigma):
  *                       sum_c w_c exp(-sum_d (x_d - m_{c,d})^2 / (2 sigma_c^2)),
- *                       m_{c,d} = mu_c for even d, nu_c for odd d. */
+ *                       m_{c,d} = mu_c for even d, nu_c for odd d.
+ *   SCENE4D             s = 4, theta[16] = (fx, fy, fw, fh, cx, cy, h, side, Le,
+ *                       ox, oy, oz, rho, freq, 0, 0): a procedural scene (a Fig. 1
+ *                       substitute; no closed form): P = (fx + fw x0, fy + fh x1, 0)
+ *                       on a checkerboard plane (albedo 0.8 / 0.2 by the parity of
+ *                       floor(freq P_x) + floor(freq P_y)), L = (cx + side (x2 - 1/2),
+ *                       cy + side (x3 - 1/2), h) on a square light facing down,
+ *                       f = albedo V Le side^2 h^2 / |L - P|^4 with V = 0 when the
+ *                       segment P-L meets the sphere (ox, oy, oz; rho) lying inside
+ *                       0 < z < h.  The checker and occlusion decisions are taken in
+ *                       fp32 with every operation rounded in the order of the
+ *                       definition (no fused multiply-add), so they are reproducible
+ *                       on any IEEE machine. */
 typedef enum qmc_integrand {
     QMC_F_BILINEAR2D = 0,
     QMC_F_GENZ_PRODUCT_PEAK = 1,
     QMC_F_GENZ_OSCILLATORY = 2,
-    QMC_F_GAUSSMIX4_6D = 3
+    QMC_F_GAUSSMIX4_6D = 3,
+    QMC_F_SCENE4D = 4
 } qmc_integrand;
 
 /* One batch of integrals that share a point source and an integrand

@@ -30,7 +30,7 @@ SCRAMBLE_NONE, SCRAMBLE_XOR, SCRAMBLE_NESTED = 0, 1, 2
 LATTICE_BACKWARD = 1
 SOURCE_SOBOL, SOURCE_LATTICE, SOURCE_PIXEL_LATTICE, SOURCE_RANDOM_LATTICE = 0, 1, 2, 3
 RLAT_HASH, RLAT_LFSR = 0, 1
-F_BILINEAR2D, F_GENZ_PRODUCT_PEAK, F_GENZ_OSCILLATORY, F_GAUSSMIX4_6D = 0, 1, 2, 3
+F_BILINEAR2D, F_GENZ_PRODUCT_PEAK, F_GENZ_OSCILLATORY, F_GAUSSMIX4_6D, F_SCENE4D = 0, 1, 2, 3, 4
 
 EXPORTED = ["qmc_abi_version", "qmc_status_string", "qmc_sobol_matrices", "qmc_sobol_points",
             "qmc_lattice_points", "qmc_integrate_workspace_bytes", "qmc_integrate",

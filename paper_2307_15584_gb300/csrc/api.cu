@@ -395,10 +395,11 @@ bool rlat_randomize_ok(uint32_t r) {
 
 qmc_status validate_problem(const qmc_problem* p, bool need_source) {
   if (!p) return QMC_ERR_INVALID_ARG;
-  if (p->integrand > QMC_F_GAUSSMIX4_6D || p->source > QMC_SOURCE_RANDOM_LATTICE) return QMC_ERR_INVALID_ARG;
+  if (p->integrand > QMC_F_SCENE4D || p->source > QMC_SOURCE_RANDOM_LATTICE) return QMC_ERR_INVALID_ARG;
   const uint32_t s = p->s;
   if (p->integrand == QMC_F_BILINEAR2D && s != 2) return QMC_ERR_INVALID_ARG;
   if (p->integrand == QMC_F_GAUSSMIX4_6D && s != 6) return QMC_ERR_INVALID_ARG;
+  if (p->integrand == QMC_F_SCENE4D && s != 4) return QMC_ERR_INVALID_ARG;
   if ((p->integrand == QMC_F_GENZ_PRODUCT_PEAK || p->integrand == QMC_F_GENZ_OSCILLATORY) &&
       (s == 0 || s > 16))
     return QMC_ERR_INVALID_ARG;
@@ -448,7 +449,8 @@ qmc_status prepare(const qmc_problem* p, uint32_t n, const uint32_t* d_counts, c
   if (st != QMC_OK) return st;
   if (!d_counts) return QMC_ERR_INVALID_ARG;
   if (p->integrand != QMC_F_BILINEAR2D && !d_theta) return QMC_ERR_INVALID_ARG;
-  if (p->integrand == QMC_F_GAUSSMIX4_6D && !aligned16(d_theta)) return QMC_ERR_ALIGN;
+  if ((p->integrand == QMC_F_GAUSSMIX4_6D || p->integrand == QMC_F_SCENE4D) && !aligned16(d_theta))
+    return QMC_ERR_ALIGN;
   if (!ws || ((uintptr_t)ws & 255u)) return QMC_ERR_WORKSPACE;
   const uint32_t vpi = values_per_item(p, grad);
   const WsLayout L0 = workspace_layout(n, 0, vpi);
@@ -489,9 +491,9 @@ qmc_status prepare(const qmc_problem* p, uint32_t n, const uint32_t* d_counts, c
   a.n = n;
   a.counts = d_counts;
   a.theta = d_theta;
-  a.theta_stride = p->integrand == QMC_F_GAUSSMIX4_6D ? 16u
-                   : p->integrand == QMC_F_BILINEAR2D  ? 0u
-                                                       : 2u * p->s;
+  a.theta_stride = (p->integrand == QMC_F_GAUSSMIX4_6D || p->integrand == QMC_F_SCENE4D) ? 16u
+                   : p->integrand == QMC_F_BILINEAR2D                                    ? 0u
+                                                                                         : 2u * p->s;
   a.hdr = reinterpret_cast<WsHeader*>(base + L.header);
   a.item_off = reinterpret_cast<uint32_t*>(base + L.item_off);
   a.row_off = nullptr;
