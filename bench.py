@@ -496,16 +496,18 @@ def error_spectrum_low_ratio(err: np.ndarray, band: float = 0.125) -> float:
 
 
 def bench_samplers(dev, steps, warmup, small, sm_mhz):
-    """Fig. 1 substitute (Sec. 3): a 1920x1080 image (480x270 when small) whose
-    pixel integrands are 6-D Gaussian mixtures varying smoothly over the image,
+    """Fig. 1 substitute (Sec. 3): two 1920x1080 images (480x270 when small),
     estimated at 4 / 16 / 64 / 256 samples per pixel by the samplers the paper
     compares, all through the fused integrator: nested-scrambled Sobol' with
-    per-pixel seeds and with one seed vector shared by every pixel, the
-    pixel-shifted rank-1 lattice (Eq. (PixelShiftedR1LS)), and per-pixel random
-    lattices (Alg. 4) with hashed generator vectors, one or four superimposed
-    instances, and LFSR generator vectors with four instances.  Per sampler and
-    rate: the RMS relative error against the closed-form integrals, the
-    low-frequency share of the error image's power spectrum, and the time."""
+    per-pixel seeds (and, on the first image, one seed vector shared by every
+    pixel), the pixel-shifted rank-1 lattice (Eq. (PixelShiftedR1LS)), and
+    per-pixel random lattices (Alg. 4) with hashed generator vectors, one or four
+    superimposed instances, and LFSR generator vectors with four instances.
+    Image one: 6-D Gaussian mixtures varying smoothly over the image (errors
+    against the closed forms).  Image two: a procedural scene with checker edges
+    and a soft shadow (errors against a 16384-spp reference).  Per sampler and
+    rate: the RMS error, the low-frequency share of the error image's power
+    spectrum, and the time."""
     import torch
 
     from paper_2307_15584_gb300 import binding as B
@@ -536,23 +538,61 @@ def bench_samplers(dev, steps, warmup, small, sm_mhz):
                                                  seeds=seed, image_width=W),
     }
     est = torch.empty(n, dtype=torch.float64, device=dev)
-    res = {"image": [W, H], "integrand": "gaussmix, smooth over the image", "spp": [4, 16, 64, 256],
-           "metrics": "rms_rel_err vs closed form; low_freq_ratio = error power below 1/8 cycle/pixel "
-                      "over mean power (white noise 1)"}
-    for name, prob in problems.items():
-        entry = {"rms_rel_err": [], "low_freq_ratio": [], "ms": []}
-        for spp in res["spp"]:
-            counts = np.full(n, spp, np.uint32)
-            cd = B.u32_tensor(counts, dev)
-            ws = B.alloc_workspace(prob, n, counts, dev)
-            ms = statistics.median(timed(lambda: B.qmc_integrate(prob, n, cd, thd, est, ws), steps, warmup, stream))
-            err = ((est.cpu().numpy() - exact) / exact).reshape(H, W)
-            entry["rms_rel_err"].append(float(np.sqrt(np.mean(err * err))))
-            entry["low_freq_ratio"].append(error_spectrum_low_ratio(err))
-            entry["ms"].append(ms)
-            del ws
-        entry["gsamples_s_at_256spp"] = n * 256 / (entry["ms"][-1] * 1e-3) / 1e9
-        res[name] = entry
+
+    def compare(problems, theta_d, reference, relative):
+        out = {}
+        for name, prob in problems.items():
+            entry = {"rms_err": [], "low_freq_ratio": [], "ms": []}
+            for spp in (4, 16, 64, 256):
+                counts = np.full(n, spp, np.uint32)
+                cd = B.u32_tensor(counts, dev)
+                ws = B.alloc_workspace(prob, n, counts, dev)
+                ms = statistics.median(timed(lambda: B.qmc_integrate(prob, n, cd, theta_d, est, ws), steps, warmup,
+                                             stream))
+                diff = est.cpu().numpy() - reference
+                err = (diff / reference if relative else diff / np.abs(reference).mean()).reshape(H, W)
+                entry["rms_err"].append(float(np.sqrt(np.mean(err * err))))
+                entry["low_freq_ratio"].append(error_spectrum_low_ratio(err))
+                entry["ms"].append(ms)
+                del ws
+            entry["gsamples_s_at_256spp"] = n * 256 / (entry["ms"][-1] * 1e-3) / 1e9
+            out[name] = entry
+        return out
+
+    res = {"image": [W, H], "spp": [4, 16, 64, 256],
+           "metrics": "rms_err; low_freq_ratio = error power below 1/8 cycle/pixel over mean power (white noise 1)"}
+    res["mixture"] = {"integrand": "gaussmix, smooth over the image", "reference": "closed form",
+                      "error": "relative per pixel", **compare(problems, thd, exact, True)}
+
+    # the procedural scene: discontinuous (checker edges, the shadow of a sphere), no closed form;
+    # the reference is per-pixel nested-scrambled Sobol' at 16384 samples per pixel
+    theta_s = torch.from_numpy(inputs.scene_theta(W, H)).to(dev)
+    C4 = B.u32_tensor(B.qmc_sobol_matrices(4, inputs.sobol_raw_init(4)), dev)
+    pp4 = B.u32_tensor(inputs.pixel_seeds(n, 4), dev)
+    g4 = B.u32_tensor(inputs.lattice_generator(4), dev)
+    Fs = B.F_SCENE4D
+    ref_prob = B.make_problem(B.SOURCE_SOBOL, Fs, 4, B.SCRAMBLE_NESTED, matrices=C4,
+                              seeds=B.u32_tensor(inputs.pixel_seeds(n, 4, seed=inputs.DEFAULT_SEED + 7), dev),
+                              seeds_per_integral=True)
+    ref_counts = np.full(n, 1 << 14, np.uint32)
+    ref_ws = B.alloc_workspace(ref_prob, n, ref_counts, dev)
+    B.qmc_integrate(ref_prob, n, B.u32_tensor(ref_counts, dev), theta_s, est, ref_ws)
+    reference = est.cpu().numpy().copy()
+    del ref_ws
+    scene = {
+        "sobol_nested_per_pixel": B.make_problem(B.SOURCE_SOBOL, Fs, 4, B.SCRAMBLE_NESTED, matrices=C4, seeds=pp4,
+                                                 seeds_per_integral=True),
+        "pixel_shifted_lattice": B.make_problem(B.SOURCE_PIXEL_LATTICE, Fs, 4, 0, g=g4, image_width=W),
+        "random_lattice_hash": B.make_problem(B.SOURCE_RANDOM_LATTICE, Fs, 4, B.rlat_randomize(B.RLAT_HASH, 1),
+                                              seeds=seed, image_width=W),
+        "random_lattice_hash_x4": B.make_problem(B.SOURCE_RANDOM_LATTICE, Fs, 4, B.rlat_randomize(B.RLAT_HASH, 4),
+                                                 seeds=seed, image_width=W),
+        "random_lattice_lfsr_x4": B.make_problem(B.SOURCE_RANDOM_LATTICE, Fs, 4, B.rlat_randomize(B.RLAT_LFSR, 4),
+                                                 seeds=seed, image_width=W),
+    }
+    res["scene"] = {"integrand": "checkerboard under a square light, shadow of a sphere (discontinuous)",
+                    "reference": "nested-scrambled Sobol', 16384 spp per pixel",
+                    "error": "per pixel, relative to the image's mean", **compare(scene, theta_s, reference, False)}
     return res
 
 
