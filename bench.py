@@ -139,7 +139,14 @@ class ClockSampler:
 
 
 POINTS_SOURCES = ["sobol_points.cu", "points_common.cuh", "qmc_device.cuh", "qmc_internal.h"]
-INTEGRATE_SOURCES = ["integrate.cu", "qmc_device.cuh", "qmc_integrate.h", "qmc_internal.h"]
+INTEGRATE_COMMON = ["integrate_kernel.cuh", "qmc_device.cuh", "qmc_integrate.h", "qmc_internal.h"]
+
+
+def integrate_sources(key: str) -> list[str]:
+    """Sources of the fused kernel a profile figure belongs to: its integrand's
+    translation unit and the shared kernel header."""
+    unit = "integrate_gaussmix.cu" if "gaussmix" in key else "integrate_genz.cu"
+    return [unit] + INTEGRATE_COMMON
 KERNEL_SOURCES = {"sobol_points_fast<1,2>": POINTS_SOURCES}
 
 
@@ -167,7 +174,7 @@ def issue_roofline(samples_per_s: float, key: str, sm_mhz):
     """Instruction-issue roofline of a fused integration kernel: thread-instructions
     per sample (ncu, committed in profiles/inst_per_sample.txt) x samples/s against
     SMs x schedulers x 32 lanes x SM clock."""
-    ips = _profile_value("inst_per_sample.txt", key, INTEGRATE_SOURCES)
+    ips = _profile_value("inst_per_sample.txt", key, integrate_sources(key))
     clock = sm_mhz or measured_peaks()["sm_max_mhz"]
     peak = SMS * SCHEDULERS_PER_SM * WARP * clock * 1e6 / 1e9  # Ginst/s
     if ips is None:

@@ -61,4 +61,10 @@ WsLayout workspace_layout(uint32_t n, uint64_t capacity_items, uint32_t values_p
 
 cudaError_t launch_integrate(const IntegrateArgs& a, uint32_t block, bool grad, cudaStream_t stream);
 
+// Persistent integration kernel of one integrand family (integrate_<name>.cu).
+cudaError_t launch_integrand_bilinear(const IntegrateArgs& a, uint32_t block, cudaStream_t stream);
+cudaError_t launch_integrand_genz(const IntegrateArgs& a, uint32_t block, cudaStream_t stream);
+cudaError_t launch_integrand_gaussmix(const IntegrateArgs& a, uint32_t block, bool grad, cudaStream_t stream);
+cudaError_t launch_integrand_scene(const IntegrateArgs& a, uint32_t block, cudaStream_t stream);
+
 }  // namespace qmc
