@@ -193,14 +193,12 @@ static qmc_status check_outputs(uint32_t s, uint64_t count, const void* out_u32,
   return QMC_OK;
 }
 
+// Arguments of the 32-bit-index point entries: the range ends at 2^32 at most.
 static qmc_status check_points_args(uint32_t s, uint64_t index_begin, uint64_t count,
                                     const void* out_u32, const void* out_f32) {
   if (s == 0 || s > 1024) return QMC_ERR_INVALID_ARG;
-  if (index_begin > (1ull << 32) || count > (1ull << 32) - index_begin) return QMC_ERR_RANGE;
-  if (count == 0) return QMC_OK;  // nothing to write: outputs may be null (empty tensors)
-  if (!out_u32 && !out_f32) return QMC_ERR_INVALID_ARG;
-  if (((uintptr_t)out_u32 & 3u) || ((uintptr_t)out_f32 & 3u)) return QMC_ERR_ALIGN;
-  return QMC_OK;
+  if (!index_range_ok(index_begin, count, 32)) return QMC_ERR_RANGE;
+  return check_outputs(s, count, out_u32, out_f32);
 }
 
 qmc_status qmc_sobol_points(const uint32_t* d_matrices, uint32_t s, uint64_t index_begin,
