@@ -83,6 +83,7 @@ def lib() -> ctypes.CDLL:
             "qo_pixel_lattice_u32": (u32, [u32, u32, u32]),
             "qo_integrate_one": (i32, [u32, u32, u32, u32, P, P, P, u32, P, P, P, P, P]),
             "qo_integrand": (dbl, [u32, u32, P, P, P]),
+            "qo_integrate_partitioned": (i32, [u32, u32, u32, P, u32, u32, u64, P, u32, P, P, P, P, P]),
             "qo_gaussmix_f64": (dbl, [P, P]),
             "qo_exact_genz_product_peak": (dbl, [u32, P]),
             "qo_exact_genz_oscillatory": (dbl, [u32, P]),
@@ -294,6 +295,41 @@ def integrate(source, integrand, s, counts, theta, *, C=None, g=None, scramble=0
             raise ValueError("oracle rejected the problem")
 
     # largest integrals first so the pool stays busy
+    order = np.argsort(-counts.astype(np.int64), kind="stable")
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(one, order.tolist()))
+    return {"est": est, "mass": mass, "grad": grad, "grad_mass": gmass}
+
+
+def integrate_partitioned(integrand, s, counts, theta, C, q, elements, *, scramble=0, seeds=None,
+                          with_grad=False, threads=None):
+    """Estimates of element elements[k] of the Sobol' sequence partitioned across
+    2^q elements by dimension 0 of the wide matrices C [s+1][m] (Sec. 2.5.1),
+    with counts[k] samples each.  theta [n][P]; seeds None, [s] or [n][s]."""
+    counts = np.ascontiguousarray(counts, dtype=np.uint32).reshape(-1)
+    n = counts.size
+    theta = np.ascontiguousarray(theta, dtype=np.float32).reshape(n, -1)
+    C = np.ascontiguousarray(C, dtype=np.uint32)
+    m = C.shape[1]
+    elements = np.asarray(elements, dtype=np.uint64).reshape(-1)
+    if seeds is not None:
+        seeds = np.asarray(seeds, dtype=np.uint32)
+        if seeds.ndim == 1:
+            seeds = np.tile(seeds.reshape(1, s), (n, 1))
+        seeds = np.ascontiguousarray(seeds.reshape(n, -1))
+    est, mass = np.zeros(n), np.zeros(n)
+    grad = np.zeros((n, 16)) if with_grad else None
+    gmass = np.zeros((n, 16)) if with_grad else None
+
+    def one(k):
+        rc = lib().qo_integrate_partitioned(
+            integrand, s, scramble, _p(C), m, q, int(elements[k]),
+            None if seeds is None else seeds[k].ctypes.data, int(counts[k]), theta[k].ctypes.data,
+            est[k:].ctypes.data, mass[k:].ctypes.data,
+            None if grad is None else grad[k].ctypes.data, None if gmass is None else gmass[k].ctypes.data)
+        if rc != 0:
+            raise ValueError("oracle rejected the problem")
+
     order = np.argsort(-counts.astype(np.int64), kind="stable")
     with ThreadPoolExecutor(_threads(threads)) as ex:
         list(ex.map(one, order.tolist()))

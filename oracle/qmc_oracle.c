@@ -752,6 +752,64 @@ QO_EXPORT int qo_integrate_one(uint32_t source, uint32_t integrand, uint32_t s,
     return 0;
 }
 
+/* Sec. 2.5.1 for integration: the QMC estimate over element p of a Sobol'
+ * sequence partitioned across 2^q processing elements by its dimension 0 --
+ * samples x_J = dimensions 1..s of point qo_partition_index(2, q, p, J),
+ * J = 0 .. n-1, of the m-column matrices C ([s+1][m]) randomised by `scramble`
+ * with seeds[s].  The 2^q elements' points together are the sequence's first
+ * 2^q n points, so with equal counts the mean of their estimates is the
+ * estimate over those points -- an integral of up to 2^(32+q) samples from
+ * 32-bit counts.  Outputs as qo_integrate_one. */
+QO_EXPORT int qo_integrate_partitioned(uint32_t integrand, uint32_t s, uint32_t scramble,
+                                       const uint32_t* C, uint32_t m, uint32_t q, uint64_t p,
+                                       const uint32_t* seeds, uint32_t n, const float* theta,
+                                       double* est, double* mass, double* grad, double* grad_mass)
+{
+    if (s == 0 || s > 32 || m < 32 || m > 64 || q > 32 || m < 32 + q) return -1;
+    if (integrand == QO_F_BILINEAR2D && s != 2) return -1;
+    if (integrand == QO_F_GAUSSMIX4_6D && s != 6) return -1;
+    if (integrand == QO_F_SCENE4D && s != 4) return -1;
+    if (integrand > QO_F_SCENE4D) return -1;
+
+    neumaier sum = {0, 0}, abs_sum = {0, 0};
+    neumaier gsum[16], gabs[16];
+    for (int k = 0; k < 16; ++k) gsum[k] = gabs[k] = (neumaier){0, 0};
+
+    double x[32], df[16];
+    for (uint32_t J = 0; J < n; ++J) {
+        uint64_t i = qo_partition_index(2, q, p, J);
+        for (uint32_t j = 0; j < s; ++j) {
+            uint32_t v = randomise_sobol(qo_sobol_u64(C + (uint64_t)m * (j + 1), m, i), scramble,
+                                         seeds ? seeds[j] : 0u);
+            x[j] = (double)qo_map_u32_to_unifloat(v);
+        }
+        double f;
+        switch (integrand) {
+        case QO_F_BILINEAR2D: f = f_bilinear(x); break;
+        case QO_F_GENZ_PRODUCT_PEAK: f = f_genz_product_peak(x, s, theta); break;
+        case QO_F_GENZ_OSCILLATORY: f = f_genz_oscillatory(x, s, theta); break;
+        case QO_F_SCENE4D: f = f_scene(x, theta); break;
+        default: f = f_gaussmix(x, theta, grad ? df : NULL); break;
+        }
+        neu_add(&sum, f);
+        neu_add(&abs_sum, fabs(f));
+        if (grad && integrand == QO_F_GAUSSMIX4_6D)
+            for (int k = 0; k < 16; ++k) {
+                neu_add(&gsum[k], df[k]);
+                neu_add(&gabs[k], fabs(df[k]));
+            }
+    }
+    double inv = n ? 1.0 / (double)n : 0.0;
+    *est = n ? (sum.s + sum.c) / (double)n : 0.0;
+    if (mass) *mass = (abs_sum.s + abs_sum.c) * inv;
+    if (grad)
+        for (int k = 0; k < 16; ++k) {
+            grad[k] = n ? (gsum[k].s + gsum[k].c) / (double)n : 0.0;
+            if (grad_mass) grad_mass[k] = (gabs[k].s + gabs[k].c) * inv;
+        }
+    return 0;
+}
+
 /* Integrand value (and Gaussian-mixture gradient) at one fp64 point; used by
  * the finite-difference pins. */
 QO_EXPORT double qo_integrand(uint32_t integrand, uint32_t s, const double* x,
