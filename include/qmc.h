@@ -141,6 +141,18 @@ typedef struct qmc_problem {
     uint32_t image_width;        /* PIXEL_LATTICE, RANDOM_LATTICE: pixels per image row (>= 1);
                                     the image has ceil(n_integrals / image_width) rows (both
                                     sides at most 2^20 for RANDOM_LATTICE).  Ignored otherwise. */
+    uint32_t index_bits;         /* SOBOL: columns per dimension of d_matrices, 0 (= 32, the
+                                    layout of qmc_sobol_matrices) or 32..64 (the layout of
+                                    qmc_sobol_matrices_wide) */
+    uint32_t partition_log2;     /* SOBOL, Sec. 2.5.1: 0, or q in 1..32 with index_bits >= 32 + q:
+                                    d_matrices holds s+1 dimensions, dimension 0 the extra
+                                    one, and integral p enumerates element p mod 2^q of the
+                                    sequence partitioned by it -- sample J of integral p is
+                                    dimensions 1..s of point J 2^q + c (c = the q-bit
+                                    reversal of p mod 2^q).  With equal counts n, 2^q
+                                    consecutive integrals are one integral over the
+                                    sequence's first 2^q n points (up to 2^(32+q) samples):
+                                    the mean of their estimates.  0 for other sources. */
 } qmc_problem;
 
 /* ABI revision of this header (bumped on any incompatible change). */

@@ -58,7 +58,8 @@ class qmc_problem(ctypes.Structure):
     _fields_ = [("source", c_uint32), ("integrand", c_uint32), ("s", c_uint32), ("randomize", c_uint32),
                 ("d_matrices", c_void_p), ("d_g", c_void_p), ("d_seeds", c_void_p),
                 ("seeds_per_integral", c_uint32), ("chunk", c_uint32), ("block", c_uint32),
-                ("max_count", c_uint32), ("with_gradient", c_uint32), ("image_width", c_uint32)]
+                ("max_count", c_uint32), ("with_gradient", c_uint32), ("image_width", c_uint32),
+                ("index_bits", c_uint32), ("partition_log2", c_uint32)]
 
 
 _P = c_void_p
@@ -305,11 +306,12 @@ def qmc_read_device_error(workspace, stream=None) -> int:
 # ----------------------------------------------------------------- conveniences
 def make_problem(source, integrand, s, randomize=0, matrices=None, g=None, seeds=None,
                  seeds_per_integral=False, chunk=0, block=0, max_count=0, with_gradient=False,
-                 image_width=0) -> qmc_problem:
+                 image_width=0, index_bits=0, partition_log2=0) -> qmc_problem:
     """A qmc_problem holding device pointers of the given tensors; the problem keeps
     references to them so their memory stays valid while it is alive."""
     p = qmc_problem(source, integrand, s, randomize, _dev(matrices), _dev(g), _dev(seeds),
-                    int(bool(seeds_per_integral)), chunk, block, max_count, int(bool(with_gradient)), image_width)
+                    int(bool(seeds_per_integral)), chunk, block, max_count, int(bool(with_gradient)), image_width,
+                    index_bits, partition_log2)
     p._tensors = (matrices, g, seeds)
     return p
 

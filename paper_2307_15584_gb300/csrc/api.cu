@@ -118,7 +118,7 @@ using namespace qmc;
 
 extern "C" {
 
-uint32_t qmc_abi_version(void) { return 3u; }
+uint32_t qmc_abi_version(void) { return 4u; }
 
 const char* qmc_status_string(qmc_status st) {
   switch (st) {
@@ -402,6 +402,12 @@ qmc_status validate_problem(const qmc_problem* p, bool need_source) {
       (s == 0 || s > 16))
     return QMC_ERR_INVALID_ARG;
   if (p->seeds_per_integral > 1) return QMC_ERR_INVALID_ARG;
+  if (p->source == QMC_SOURCE_SOBOL) {  // Sec. 2.5.1: J < 2^32 and q index bits below 32 + q <= m
+    const uint32_t m = p->index_bits ? p->index_bits : 32u;
+    if (m < 32 || m > 64 || p->partition_log2 > 32 || m < 32 + p->partition_log2) return QMC_ERR_INVALID_ARG;
+  } else if (p->index_bits || p->partition_log2) {
+    return QMC_ERR_INVALID_ARG;
+  }
   if (p->chunk != 0 && (p->chunk < 32 || p->chunk > 8192 || (p->chunk & (p->chunk - 1))))
     return QMC_ERR_INVALID_ARG;
   if (p->block != 0 && (p->block % 32 || p->block > 256)) return QMC_ERR_INVALID_ARG;
@@ -470,6 +476,11 @@ qmc_status prepare(const qmc_problem* p, uint32_t n, const uint32_t* d_counts, c
     a.seeds = nullptr;
     a.image_width = p->image_width;
     a.grid_log2 = image_grid_log2(n, p->image_width);
+  }
+  if (p->source == QMC_SOURCE_SOBOL) {
+    a.sobol_m = p->index_bits ? p->index_bits : 32u;
+    a.part_log2 = p->partition_log2;
+    if (a.part_log2 && a.matrices) a.matrices += a.sobol_m;  // dimensions 1..s; dimension 0 partitions
   }
   if (p->source == QMC_SOURCE_RANDOM_LATTICE) {
     if (((uint64_t)n + p->image_width - 1) / p->image_width > (1u << 20)) return QMC_ERR_INVALID_ARG;

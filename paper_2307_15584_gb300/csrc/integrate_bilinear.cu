@@ -8,6 +8,7 @@ template <>
 struct Integrand<QMC_F_BILINEAR2D> {
   static constexpr int S = 2;
   static constexpr bool kAdaptive = false;
+  static constexpr int kMinBlocks = 1;  // resident 256-thread blocks per SM the registers must allow
   float wsum = 1.0f;
   __device__ void setup(const float*, uint32_t) {}
   template <bool EXACT>

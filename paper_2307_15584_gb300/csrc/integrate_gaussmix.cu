@@ -16,6 +16,8 @@ template <>
 struct Integrand<QMC_F_GAUSSMIX4_6D> {
   static constexpr int S = 6;
   static constexpr bool kAdaptive = true;
+  static constexpr int kMinBlocks = 1;  // resident 256-thread blocks per SM the registers must allow
+  static constexpr float kErrUnit = 8.0f * kU32 * kLn2;  // relative error of G per unit |t|
   float wsum;
   float w[4], mu[4], nu[4], kh[4], kl[4];
   float is2[4], is3[4];  // 1/sigma^2, 1/sigma^3 (gradient only)

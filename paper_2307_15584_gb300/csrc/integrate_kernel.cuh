@@ -29,23 +29,29 @@ namespace integ {
 template <int S, int SCR>  // SCR: 0 none, 1 XOR, 2 nested
 struct SobolSource {
   static constexpr int kRow = (S + 3) & ~3;  // table row stride: whole 128-bit words
-  const uint32_t* cols;  // shared: [s][32], mirrored when nested
+  const uint32_t* cols;  // shared: [s][m], mirrored when nested
   const uint32_t* tab;   // shared: [C/32][kRow], y(32 r)
-  uint32_t s;
+  uint32_t s, m, q;      // dimensions, columns per dimension, partition exponent (Sec. 2.5.1)
   uint32_t lane_y[S];    // y(lane)
-  uint32_t yl[S];        // y(start) ^ y(lane) (^ seed for XOR)
+  uint32_t yl[S];        // y(start) ^ y(lane) (^ seed for XOR) (^ the element's fixed low part)
   NestedKey key[S];
 
-  // the columns first (a multiple of 32 words keeps the table 16-byte aligned)
-  static size_t smem_bytes(uint32_t s, uint32_t chunk_log2) {
-    return ((size_t)s * 32 + ((size_t)1 << (chunk_log2 - 5)) * kRow) * sizeof(uint32_t);
+  // offset of the table: the columns, rounded up to whole 16-byte words
+  __host__ __device__ static uint32_t table_offset(uint32_t s, uint32_t m) { return (s * m + 3u) & ~3u; }
+
+  static size_t smem_bytes(const IntegrateArgs& a) {
+    return ((size_t)table_offset(a.s, a.sobol_m) + ((size_t)1 << (a.chunk_log2 - 5)) * kRow) * sizeof(uint32_t);
   }
 
+  // Sample J of an item (J below 2^32) is index i = (J << q) | c_p of an m-column sequence;
+  // every column touched lies below q + 32 <= m (checked on the host).
   __device__ void kernel_setup(const IntegrateArgs& a, uint32_t* smem) {
     s = a.s;
+    m = a.sobol_m;
+    q = a.part_log2;
     uint32_t* c = smem;
-    uint32_t* t = smem + s * 32;
-    for (uint32_t i = threadIdx.x; i < s * 32; i += blockDim.x) {
+    uint32_t* t = smem + table_offset(s, m);
+    for (uint32_t i = threadIdx.x; i < s * m; i += blockDim.x) {
       const uint32_t v = __ldg(a.matrices + i);
       c[i] = SCR == 2 ? __brev(v) : v;
     }
@@ -56,7 +62,7 @@ struct SobolSource {
       uint32_t y = 0;
       if (j < s)
         for (uint32_t b = 0; (r >> b) != 0; ++b)
-          if ((r >> b) & 1u) y ^= c[j * 32 + 5 + b];
+          if ((r >> b) & 1u) y ^= c[j * m + q + 5 + b];
       t[i] = y;
     }
     __syncthreads();
@@ -68,7 +74,7 @@ struct SobolSource {
       uint32_t y = 0;
       if ((uint32_t)j < s)
         for (uint32_t b = 0; b < 5; ++b)
-          if ((lane >> b) & 1u) y ^= c[j * 32 + b];
+          if ((lane >> b) & 1u) y ^= c[j * m + q + b];
       lane_y[j] = y;
     }
   }
@@ -76,12 +82,18 @@ struct SobolSource {
   __device__ void item_setup(const IntegrateArgs& a, uint32_t p, uint32_t start) {
     const uint32_t khi = start >> a.chunk_log2;
     const uint32_t* sd = a.seeds ? a.seeds + (a.seeds_per_integral ? (size_t)p * s : 0) : nullptr;
+    // partitioned: integral p enumerates element p mod 2^q, whose indices carry the q-bit
+    // reversal of the element number in their low bits
+    const uint32_t cp = q ? __brev(p) >> (32u - q) : 0u;  // the low q bits of p, reversed
 #pragma unroll
     for (int j = 0; j < S; ++j) {
       uint32_t y = 0;
-      if ((uint32_t)j < s)
+      if ((uint32_t)j < s) {
         for (uint32_t b = 0; (khi >> b) != 0; ++b)
-          if ((khi >> b) & 1u) y ^= cols[j * 32 + a.chunk_log2 + b];
+          if ((khi >> b) & 1u) y ^= cols[j * m + q + a.chunk_log2 + b];
+        for (uint32_t b = 0; (cp >> b) != 0; ++b)
+          if ((cp >> b) & 1u) y ^= cols[j * m + b];
+      }
       const uint32_t seed = (sd && (uint32_t)j < s) ? __ldg(sd + j) : 0u;
       yl[j] = y ^ lane_y[j] ^ (SCR == 1 ? seed : 0u);
       key[j] = nested_key(seed);
@@ -91,9 +103,9 @@ struct SobolSource {
   __device__ __forceinline__ void point(uint32_t r, uint32_t /*il*/, bool /*valid*/, float* x) const {
     uint32_t row[kRow];
 #pragma unroll
-    for (int q = 0; q < kRow / 4; ++q) {  // 128-bit shared loads
-      const uint4 w = reinterpret_cast<const uint4*>(tab + r * kRow)[q];
-      row[4 * q] = w.x, row[4 * q + 1] = w.y, row[4 * q + 2] = w.z, row[4 * q + 3] = w.w;
+    for (int k = 0; k < kRow / 4; ++k) {  // 128-bit shared loads
+      const uint4 w = reinterpret_cast<const uint4*>(tab + r * kRow)[k];
+      row[4 * k] = w.x, row[4 * k + 1] = w.y, row[4 * k + 2] = w.z, row[4 * k + 3] = w.w;
     }
 #pragma unroll
     for (int j = 0; j < S; ++j) {
@@ -111,7 +123,7 @@ struct LatticeSource {
   uint32_t g[S];
   uint32_t sh[S];
 
-  static size_t smem_bytes(uint32_t, uint32_t) { return 0; }
+  static size_t smem_bytes(const IntegrateArgs&) { return 0; }
 
   __device__ void kernel_setup(const IntegrateArgs& a, uint32_t*) {
     s = a.s;
@@ -143,7 +155,7 @@ struct PixelLatticeSource {
   uint32_t shift;
   uint32_t g[S];
 
-  static size_t smem_bytes(uint32_t, uint32_t) { return 0; }
+  static size_t smem_bytes(const IntegrateArgs&) { return 0; }
 
   __device__ void kernel_setup(const IntegrateArgs& a, uint32_t*) {
 #pragma unroll
@@ -174,7 +186,7 @@ struct RandomLatticeSource {
   const uint32_t* jump;  // LFSR: the 32-step jump table in shared memory
   uint32_t g[S];
 
-  static size_t smem_bytes(uint32_t, uint32_t) {
+  static size_t smem_bytes(const IntegrateArgs&) {
     return KIND == QMC_RLAT_LFSR ? kLfsrJumpWords * sizeof(uint32_t) : 0;
   }
 
@@ -218,7 +230,7 @@ struct PointsSource {
   const float* rows;
   uint32_t s;
 
-  static size_t smem_bytes(uint32_t, uint32_t) { return 0; }
+  static size_t smem_bytes(const IntegrateArgs&) { return 0; }
 
   __device__ void kernel_setup(const IntegrateArgs& a, uint32_t*) { s = a.s; }
 
@@ -289,9 +301,9 @@ __device__ __forceinline__ uint32_t find_integral(const uint32_t* off, uint32_t 
   return lo;
 }
 
-// Per-sample rounding-error coefficient of the fp32 mixture path: relative
-// error of G <= 8 u ln2 |t| (u = 2^-24), see Integrand<GAUSSMIX4_6D>.
-constexpr float kKappa = 8.0f * 5.9604645e-8f * kLn2;
+// Unit roundoff of fp32 (2^-24).  Each adaptive integrand states kErrUnit, the
+// factor that turns its per-sample err into an absolute error scale.
+constexpr float kU32 = 5.9604645e-8f;
 
 // One pass over the samples of the current item.  Returns nothing; adds into
 // acc and, on the fp32 pass, the squared per-sample error scales into e2.
@@ -353,7 +365,7 @@ __device__ __forceinline__ void run_item(const Src& src, const F& f, uint32_t le
 }
 
 template <class Src, int FN, bool GRAD>
-__global__ void __launch_bounds__(256) integrate_main(IntegrateArgs a) {
+__global__ void __launch_bounds__(256, Integrand<FN>::kMinBlocks) integrate_main(IntegrateArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   using F = Integrand<FN>;
   constexpr int NV = GRAD ? 17 : 1;
@@ -383,7 +395,7 @@ __global__ void __launch_bounds__(256) integrate_main(IntegrateArgs a) {
     run_item<false, GRAD>(src, f, len, acc, e2);
     if constexpr (F::kAdaptive) {
       // Budget test on the item: the fp32 rounding errors of the samples are
-      // treated as independent, so their sum has scale kKappa sqrt(e2); an
+      // treated as independent, so their sum has scale kErrUnit sqrt(e2); an
       // item whose 3-sigma error exceeds 0.6e-6 of its sum (plus its share of
       // the 1e-12 W absolute floor) is recomputed on the exact path.  The test
       // depends only on the item's data, so results stay reproducible.
@@ -391,7 +403,7 @@ __global__ void __launch_bounds__(256) integrate_main(IntegrateArgs a) {
       for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
       const Comp tot = warp_comp_sum(acc[0].comp());
       const float budget = 0.6e-6f * fabsf(tot.sum + tot.err) + 0.5e-12f * f.wsum * (float)len;
-      if (3.0f * kKappa * sqrtf(e2) > budget) {
+      if (3.0f * F::kErrUnit * sqrtf(e2) > budget) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) acc[v] = Kahan{};
         run_item<true, GRAD>(src, f, len, acc, e2);
@@ -420,7 +432,7 @@ __global__ void __launch_bounds__(256) integrate_main(IntegrateArgs a) {
 template <class Src, int FN, bool GRAD>
 cudaError_t launch_main_t(const IntegrateArgs& a, uint32_t block, cudaStream_t stream) {
   auto kernel = integrate_main<Src, FN, GRAD>;
-  const size_t smem = Src::smem_bytes(a.s, a.chunk_log2);
+  const size_t smem = Src::smem_bytes(a);
   if (smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -35,8 +35,8 @@ def test_header_symbols_exported(B):
     for name in declared:
         assert hasattr(lib, name), name
     assert sorted(B.EXPORTED) == sorted(declared)
-    assert B.qmc_abi_version() == 3
-    assert ctypes.sizeof(B.qmc_problem) == 64  # 4 + 3 pointers + 6 words, as in include/qmc.h
+    assert B.qmc_abi_version() == 4
+    assert ctypes.sizeof(B.qmc_problem) == 72  # 4 + 3 pointers + 8 words, as in include/qmc.h
     assert "INVALID" in B.qmc_status_string(1)
 
 
@@ -213,3 +213,19 @@ def test_random_lattice_validation(B):
         kw = dict(base)
         kw.update(bad)
         assert L.qmc_integrate(ref(_problem(B, **kw)), 4, FAKE, FAKE, FAKE, ws, 1 << 30, None) == 1, bad
+
+
+def test_partitioned_integration_validation(B):
+    """Sec. 2.5.1 integration: 32..64 columns, q <= 32 with m >= 32 + q, Sobol' only."""
+    L = B._lib
+    ref = ctypes.byref
+    ws = 1 << 20
+    for bad in (dict(index_bits=31), dict(index_bits=65), dict(index_bits=0, partition_log2=1),
+                dict(index_bits=40, partition_log2=9), dict(index_bits=64, partition_log2=33),
+                dict(source=B.SOURCE_LATTICE, g=FAKE, randomize=0, index_bits=64),
+                dict(source=B.SOURCE_LATTICE, g=FAKE, randomize=0, partition_log2=1)):
+        assert L.qmc_integrate(ref(_problem(B, **bad)), 4, FAKE, FAKE, FAKE, ws, 1 << 30, None) == 1, bad
+        assert B.qmc_integrate_workspace_bytes(_problem(B, **bad), 4, None) == 0, bad
+    for good in (dict(index_bits=32), dict(index_bits=40, partition_log2=8), dict(index_bits=64, partition_log2=32)):
+        assert B.qmc_integrate_workspace_bytes(_problem(B, **good), 4, None) > 0, good
+        assert L.qmc_integrate(ref(_problem(B, **good)), 0, FAKE, FAKE, FAKE, ws, 1 << 30, None) == 0, good
