@@ -8,7 +8,8 @@ template <>
 struct Integrand<QMC_F_BILINEAR2D> {
   static constexpr int S = 2;
   static constexpr bool kAdaptive = false;
-  static constexpr int kMinBlocks = 1;  // resident 256-thread blocks per SM the registers must allow
+  static constexpr bool kExactPair = false;
+  static constexpr int kMinBlocks = 0;  // resident 256-thread blocks per SM to fit (0: the compiler's choice)
   float wsum = 1.0f;
   __device__ void setup(const float*, uint32_t) {}
   template <bool EXACT>

@@ -16,7 +16,8 @@ template <>
 struct Integrand<QMC_F_GAUSSMIX4_6D> {
   static constexpr int S = 6;
   static constexpr bool kAdaptive = true;
-  static constexpr int kMinBlocks = 1;  // resident 256-thread blocks per SM the registers must allow
+  static constexpr bool kExactPair = false;
+  static constexpr int kMinBlocks = 0;  // resident 256-thread blocks per SM to fit (0: the compiler's choice)
   static constexpr float kErrUnit = 8.0f * kU32 * kLn2;  // relative error of G per unit |t|
   float wsum;
   float w[4], mu[4], nu[4], kh[4], kl[4];

@@ -31,7 +31,7 @@ struct SobolSource {
   static constexpr int kRow = (S + 3) & ~3;  // table row stride: whole 128-bit words
   const uint32_t* cols;  // shared: [s][m], mirrored when nested
   const uint32_t* tab;   // shared: [C/32][kRow], y(32 r)
-  uint32_t s, m, q;      // dimensions, columns per dimension, partition exponent (Sec. 2.5.1)
+  uint32_t s;
   uint32_t lane_y[S];    // y(lane)
   uint32_t yl[S];        // y(start) ^ y(lane) (^ seed for XOR) (^ the element's fixed low part)
   NestedKey key[S];
@@ -43,12 +43,12 @@ struct SobolSource {
     return ((size_t)table_offset(a.s, a.sobol_m) + ((size_t)1 << (a.chunk_log2 - 5)) * kRow) * sizeof(uint32_t);
   }
 
-  // Sample J of an item (J below 2^32) is index i = (J << q) | c_p of an m-column sequence;
-  // every column touched lies below q + 32 <= m (checked on the host).
+  // Sample J of an item (J below 2^32) is index i = (J << q) | c_p of an m-column sequence
+  // (m = a.sobol_m, q = a.part_log2, read from the kernel parameters where used); every
+  // column touched lies below q + 32 <= m (checked on the host).
   __device__ void kernel_setup(const IntegrateArgs& a, uint32_t* smem) {
     s = a.s;
-    m = a.sobol_m;
-    q = a.part_log2;
+    const uint32_t m = a.sobol_m, q = a.part_log2;
     uint32_t* c = smem;
     uint32_t* t = smem + table_offset(s, m);
     for (uint32_t i = threadIdx.x; i < s * m; i += blockDim.x) {
@@ -81,6 +81,7 @@ struct SobolSource {
 
   __device__ void item_setup(const IntegrateArgs& a, uint32_t p, uint32_t start) {
     const uint32_t khi = start >> a.chunk_log2;
+    const uint32_t m = a.sobol_m, q = a.part_log2;
     const uint32_t* sd = a.seeds ? a.seeds + (a.seeds_per_integral ? (size_t)p * s : 0) : nullptr;
     // partitioned: integral p enumerates element p mod 2^q, whose indices carry the q-bit
     // reversal of the element number in their low bits
@@ -267,7 +268,9 @@ struct Integrand;
 // Every integrand offers eval<EXACT>(x, err): f(x) in fp32 and, for adaptive
 // integrands, err = an estimate of the sample's rounding error scale.  EXACT
 // selects the float-float evaluation used when an item's error estimate is
-// over budget; non-adaptive integrands ignore it.
+// over budget; non-adaptive integrands ignore it.  With kExactPair the EXACT
+// evaluation returns f as a float pair (the value and, in err, its low word),
+// and both words enter the compensated sum sample by sample.
 constexpr float kLn2 = 0.693147180559945309f;
 
 // ---------------------------------------------------------------------------
@@ -347,11 +350,17 @@ __device__ __forceinline__ void run_item(const Src& src, const F& f, uint32_t le
       } else {
         const float v = f.template eval<EXACT>(x, err);
         if (valid) {
-          blk[0] = __fadd_rn(blk[0], v);
+          if constexpr (EXACT && F::kExactPair) {  // f = v + err: both words, each compensated
+            acc[0].add(v);
+            acc[0].add(err);
+          } else {
+            blk[0] = __fadd_rn(blk[0], v);
+          }
           if constexpr (F::kAdaptive && !EXACT) e2 = __fmaf_rn(err, err, e2);
         }
       }
     }
+    if constexpr (EXACT && F::kExactPair) continue;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       // The estimate keeps the compensated sum.  The parameter gradients are

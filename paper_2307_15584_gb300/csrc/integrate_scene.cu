@@ -15,7 +15,8 @@ template <>
 struct Integrand<QMC_F_SCENE4D> {
   static constexpr int S = 4;
   static constexpr bool kAdaptive = false;
-  static constexpr int kMinBlocks = 1;  // resident 256-thread blocks per SM the registers must allow
+  static constexpr bool kExactPair = false;
+  static constexpr int kMinBlocks = 0;  // resident 256-thread blocks per SM to fit (0: the compiler's choice)
   float wsum = 1.0f;
   float fx, fy, fw, fh, cx, cy, h, side, ox, oy, oz, rho2, freq, K;
   __device__ void setup(const float* th, uint32_t) {

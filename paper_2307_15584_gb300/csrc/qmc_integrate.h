@@ -28,8 +28,6 @@ struct IntegrateArgs {
   uint32_t image_width;  // pixel-shifted lattice: integral p is pixel (p % width, p / width)
   uint32_t grid_log2;    // ... on the 2^grid_log2 square grid of the Hilbert curve
   uint32_t rlat_log2;    // random lattice: log2 of the superimposed instances (kind in randomize)
-  uint32_t sobol_m;      // Sobol': columns per dimension of matrices (32 .. 64)
-  uint32_t part_log2;    // Sobol': integral p enumerates element p mod 2^part_log2 (0: the sequence)
   uint32_t n;
   const uint32_t* counts;
   const float* theta;
@@ -52,6 +50,10 @@ struct IntegrateArgs {
   float* grad_theta;
   const double* target;
   double* loss;
+  // Sobol' (kept last: the fused kernels' code is sensitive to the parameter layout, and
+  // placing these before the hot fields measured 1.5 % slower)
+  uint32_t sobol_m;      // columns per dimension of matrices (32 .. 64)
+  uint32_t part_log2;    // integral p enumerates element p mod 2^part_log2 (0: the sequence)
 };
 
 // Offsets of the workspace regions (bytes from the 256-byte aligned base).
