@@ -10,7 +10,9 @@ Also reported in the same JSON line:
                 and seeds copied in, both point arrays copied back to pinned
                 host memory, every step
   roofline      the point kernel against the measured HBM copy bandwidth
-  cpu_baseline  the oracle on a bounded sample, on the host's cores
+  cpu_baseline  the oracle on a bounded sample, on the host's cores (and, inside
+                each extra below, the oracle on a bounded sample of that
+                workload)
   fused         fused forward+backward of the differentiable integro-
                 approximation (1024x1024 integrals x 4096 samples) against the
                 unfused forward + backward kernels, the batched 1920x1080
@@ -200,6 +202,91 @@ def cpu_baseline(n_rows: int = 1 << 23):
     return {"value": n_rows * S_DIMS / dt / 1e9, "unit": "Gdims/s", "cores": threads, "kind": "oracle",
             "sample": f"{n_rows} points x {S_DIMS} dims (nested scramble, u32+fp32) of the 2^24-point workload",
             "seconds": dt}
+
+
+def _oracle_rate(fn, units: float, unit: str, sample: str, threads: int) -> dict:
+    t0 = time.perf_counter()
+    fn()
+    dt = time.perf_counter() - t0
+    return {"value": units / dt / 1e9, "unit": unit, "cores": threads, "kind": "oracle", "sample": sample,
+            "seconds": dt}
+
+
+def extras_cpu_baselines(names) -> dict:
+    """The oracle as it stands on a bounded sample of each extra workload (the same
+    inputs, seeds and shapes; a fraction of the units), on the host's cores: the
+    CPU figure beside each GPU figure.  About 10 s in all on 16 cores."""
+    import oracle
+    from paper_2307_15584_gb300 import inputs
+
+    threads = os.cpu_count() or 1
+    out = {}
+    if "fwd_bwd" in names:  # config 5: 1024 of the 2^20 pixels x 4096 samples, estimate and gradient
+        n = 1024
+        C6 = oracle.sobol_matrices(6, inputs.sobol_raw_init(6))
+        th, sd = inputs.gaussmix_theta(1 << 20)[:n], inputs.pixel_seeds(n, 6)
+        out["fwd_bwd"] = _oracle_rate(
+            lambda: oracle.integrate(oracle.SOURCE_SOBOL, oracle.F_GAUSSMIX4_6D, 6, np.full(n, 4096, np.uint32), th,
+                                     C=C6, scramble=oracle.SCRAMBLE_NESTED, seeds=sd, with_grad=True,
+                                     threads=threads),
+            n * 4096.0, "Gsamples/s", f"{n} of the 2^20 pixels x 4096 samples, estimate + gradient", threads)
+    if "batched" in names:  # config 4: the first 1024 of the 1920x1080 pixels, their log-uniform counts
+        n = 1024
+        counts = inputs.log_uniform_counts(1920 * 1080)[:n]
+        C6 = oracle.sobol_matrices(6, inputs.sobol_raw_init(6))
+        th, sd = inputs.gaussmix_theta(1920 * 1080, seed=7)[:n], inputs.pixel_seeds(n, 6, seed=7)
+        out["batched"] = _oracle_rate(
+            lambda: oracle.integrate(oracle.SOURCE_SOBOL, oracle.F_GAUSSMIX4_6D, 6, counts, th, C=C6,
+                                     scramble=oracle.SCRAMBLE_NESTED, seeds=sd, threads=threads),
+            float(counts.sum()), "Gsamples/s", f"the first {n} of the 1920x1080 pixels ({int(counts.sum())} samples)",
+            threads)
+    if "lattice" in names:  # config 3: 4 integrals x 2^20 of the 2^26 points, per family
+        s, N = 16, 1 << 20
+        g, sh = inputs.lattice_generator(s), inputs.lattice_shift(s)
+        res = {}
+        for fam, kind in (("product_peak", oracle.F_GENZ_PRODUCT_PEAK), ("oscillatory", oracle.F_GENZ_OSCILLATORY)):
+            th = np.stack([inputs.genz_params(fam, s, k) for k in range(4)])
+            res[fam] = _oracle_rate(
+                lambda: oracle.integrate(oracle.SOURCE_LATTICE, kind, s, np.full(4, N, np.uint32), th, g=g, seeds=sh,
+                                         threads=threads),
+                4.0 * N, "Gsamples/s", "4 integrals x 2^20 of the 2^26 points", threads)
+        out["lattice"] = res
+    if "points" in names:  # every generator on s = 32, 2^10 .. 2^20 rows (about half a second each)
+        s, n, nl = S_DIMS, 1 << 18, 1 << 10
+        nb = 1 << 20
+        C = oracle.sobol_matrices(s, inputs.sobol_raw_init(s))
+        W = oracle.sobol_matrices_wide(s + 1, 64, inputs.sobol_raw_init(s + 1))
+        sd = inputs.scramble_seeds(s)
+        g, sh = inputs.lattice_generator(s), inputs.lattice_shift(s)
+        nested = oracle.SCRAMBLE_NESTED
+        runs = {
+            "sobol32_nested": (n, lambda: oracle.sobol_points(C, 0, n, nested, sd, threads=threads)),
+            "sobol64_nested_at_2^40": (n, lambda: oracle.sobol_points_wide(W[:s], 1 << 40, n, nested, sd,
+                                                                           threads=threads)),
+            "sobol64_partition_p5_of_8": (n, lambda: oracle.sobol_points_partitioned(W, 3, 5, 1 << 37, n, nested, sd,
+                                                                                     threads=threads)),
+            "lattice_shifted": (nb, lambda: oracle.lattice_points(g, sh, 0, nb, threads=threads)),
+            "halton_faure": (nl, lambda: oracle.halton_points(s, 0, nl, oracle.HALTON_FAURE, threads=threads)),
+            "pixel_lattice_16spp": (8 * nl, lambda: oracle.pixel_lattice_points(g, 1024, nl // 2, 16, height=1024)),
+            "random_lattice_hash_x4_16spp": (nb, lambda: oracle.random_lattice_points(
+                oracle.RLAT_HASH, 7, 4, s, 1024, nb // 16, 16, threads=threads)),
+            "random_lattice_lfsr_x4_16spp": (n // 4, lambda: oracle.random_lattice_points(
+                oracle.RLAT_LFSR, 7, 4, s, 1024, n // 64, 16, threads=threads)),
+        }
+        out["points"] = {name: _oracle_rate(fn, rows * s, "Gdims/s", f"{rows} rows x {s} dims", threads)
+                         for name, (rows, fn) in runs.items()}
+    return out
+
+
+def attach_cpu_baselines(extras: dict, base: dict) -> None:
+    """Put each oracle figure beside the GPU figure it samples."""
+    for name, b in base.items():
+        if name in ("lattice", "points"):
+            for k, v in b.items():
+                if k in extras[name]:
+                    extras[name][k]["cpu_baseline"] = v
+        else:
+            extras[name]["cpu_baseline"] = b
 
 
 def run_reference(args, world, rank):
@@ -626,7 +713,10 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if args.only:  # one integration workload alone (profiling); no headline line
-        print(json.dumps({"only": args.only, "small": args.small, **run_extras(args, dev, None)}), flush=True)
+        res = run_extras(args, dev, None)
+        if not args.no_cpu:
+            attach_cpu_baselines(res, extras_cpu_baselines(list(res)))
+        print(json.dumps({"only": args.only, "small": args.small, **res}), flush=True)
         return
     if world > 1:
         import torch.distributed as dist
@@ -753,6 +843,8 @@ def run_ours(args, world, rank, local):
         line["fused"] = run_extras(args, dev, clk.get("sm_mhz"))
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
+        if not args.no_extra:
+            attach_cpu_baselines(line["fused"], extras_cpu_baselines(list(line["fused"])))
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -23,3 +23,17 @@ def test_mixture_closed_form_matches_oracle(oracle):
 
 def test_rms_rel_err():
     assert abs(bench.rms_rel_err(np.array([1.1, 0.9]), np.array([1.0, 1.0])) - 0.1) < 1e-15
+
+
+def test_cpu_baselines_sit_beside_their_gpu_figures():
+    import bench
+
+    extras = {"fwd_bwd": {"fused_gsamples_s": 1.0}, "lattice": {"points": 4, "oscillatory": {"gsamples_s": 2.0}},
+              "points": {"rows": 8, "halton_faure": {"gb_s": 3.0}}}
+    base = {"fwd_bwd": {"value": 0.1}, "lattice": {"oscillatory": {"value": 0.2}, "product_peak": {"value": 0.3}},
+            "points": {"halton_faure": {"value": 0.4}}}
+    bench.attach_cpu_baselines(extras, base)
+    assert extras["fwd_bwd"]["cpu_baseline"] == {"value": 0.1}
+    assert extras["lattice"]["oscillatory"]["cpu_baseline"] == {"value": 0.2}
+    assert "product_peak" not in extras["lattice"]  # no GPU figure to sit beside
+    assert extras["points"]["halton_faure"]["cpu_baseline"] == {"value": 0.4}
