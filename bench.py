@@ -549,12 +549,12 @@ def bench_points(dev, steps, warmup, small, sm_mhz):
     }
     # instruction counts per coordinate (ncu, profiles/inst_per_coord.txt) for the issue roofline
     common = ["points_common.cuh", "qmc_device.cuh", "qmc_internal.h"]
-    inst_keys = {"sobol32_nested": ("sobol_points_fast<1,2>", "sobol_points.cu"),
-                 "lattice_shifted": ("lattice_points_fast<1,0,1>", "lattice_points.cu"),
-                 "halton_faure": ("halton_points_kernel<faure>", "halton_points.cu"),
-                 "pixel_lattice_16spp": ("pixel_lattice_points_fast", "lattice_points.cu"),
-                 "random_lattice_hash_x4_16spp": ("random_lattice_points_fast<hash>", "lattice_points.cu"),
-                 "random_lattice_lfsr_x4_16spp": ("random_lattice_points_fast<lfsr>", "lattice_points.cu")}
+    inst_keys = {"sobol32_nested": ("sobol_points_fast<1,2>", ["sobol_points.cu"]),
+                 "lattice_shifted": ("lattice_points_fast<1,0,1>", ["lattice_points.cu"]),
+                 "halton_faure": ("halton_points_kernel<faure>", ["halton_points.cu", "halton_points.h"]),
+                 "pixel_lattice_16spp": ("pixel_lattice_points_fast", ["lattice_points.cu"]),
+                 "random_lattice_hash_x4_16spp": ("random_lattice_points_fast<hash>", ["lattice_points.cu"]),
+                 "random_lattice_lfsr_x4_16spp": ("random_lattice_points_fast<lfsr>", ["lattice_points.cu"])}
     clock = sm_mhz or measured_peaks()["sm_max_mhz"]
     issue_peak = SMS * SCHEDULERS_PER_SM * WARP * clock * 1e6  # thread-instructions/s
     res = {"rows": n, "s": s, "bytes_per_launch": n * s * 8,
@@ -565,7 +565,7 @@ def bench_points(dev, steps, warmup, small, sm_mhz):
         entry = {"ms": ms, "gdims_s": n * s / (ms * 1e-3) / 1e9, "gb_s": gbs, "frac_hbm": gbs / peak}
         if name in inst_keys:
             key, src = inst_keys[name]
-            ipc = _profile_value("inst_per_coord.txt", key, [src] + common)
+            ipc = _profile_value("inst_per_coord.txt", key, src + common)
             if ipc is not None:
                 entry["inst_per_coord"] = ipc
                 entry["frac_issue"] = ipc * n * s / (ms * 1e-3) / issue_peak

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/qmc.h"
+#include "halton_points.h"
 #include "qmc_integrate.h"
 #include "qmc_internal.h"
 

@@ -6,6 +6,7 @@
 #include <mutex>
 #include <vector>
 
+#include "halton_points.h"
 #include "points_common.cuh"
 
 namespace qmc {
@@ -42,31 +43,53 @@ struct HaltonTables {
   uint64_t magic_group[kHaltonMaxDims];  // floor(2^64 / b^L) + 1: x / b^L = umulhi(x, .) for x < 2^32
   uint64_t magic_max[kHaltonMaxDims];    // floor(2^64 / b^K) + 1: the same for b^K
   uint64_t scale[kHaltonMaxDims];        // floor(2^64 / b^K): floor(N 2^32 / b^K) up to one correction
+  uint64_t magic_base[kHaltonMaxDims];   // floor(2^64 / b) + 1: x / b = umulhi(x, .) for x < 2^32
   uint16_t perm[kHaltonPermWords];
 };
 __device__ HaltonTables g_halton;
 
-// Work layout.  A block takes tiles of R rows (R a multiple of 128).  A warp
-// takes one output dimension for 128 rows of the tile at a time, so its lanes
-// share the dimension's constants and group count, and each lane carries four
-// independent rows (lane, lane+32, ..) through the group loop.  Results go to a
-// shared-memory tile [R][s] (odd row stride: no bank conflicts), which the block
-// then writes out with coalesced stores.
-constexpr uint32_t kHaltonRowsPerUnit = 128;
+// Work layout.  The output is [count][s] row-major.  Lanes own dimensions: a
+// warp takes a chunk of up to 32 consecutive output dimensions (w of them) and
+// k = floor(32 / w) consecutive rows per step, lane l holding dimension l mod w
+// of row l / w, so each step writes k whole rows of the chunk -- coalesced,
+// with no staging.  A unit is kHaltonSteps steps of one chunk; each lane walks
+// its dimension down the rows, advancing the digit groups of i mod b^K by the
+// index step k 2^q instead of recomputing them: one table lookup and one
+// multiply-add per row, the higher groups touched only on a carry (or every
+// row when the step has higher digits, as in a partitioned sequence).
+constexpr uint32_t kHaltonSteps = 256;
+constexpr int kHaltonMaxGroups = 6;  // G <= 6 for every base up to the 64th prime (base 37: L = 1, K = 6)
 
-// floor(N 2^32 / b^K) for N < b^K <= 2^32: one multiply-high by floor(2^64 / b^K)
-// is at most one below; the remainder decides.
-__device__ __forceinline__ uint32_t halton_scale(uint32_t N, uint32_t mp, uint64_t scale) {
-  const uint64_t num = (uint64_t)N << 32;
-  uint64_t w = __umul64hi(num, scale);
-  if (num - w * mp >= mp) ++w;
-  return (uint32_t)w;
+// floor(N 2^32 / b^K) for N < b^K < 2^32: with S = floor(2^64 / b^K) = S_hi 2^32 + S_lo,
+// w = floor(N S / 2^32) = N S_hi + umulhi(N, S_lo) is at most one below (and below
+// 2^32, so the 32-bit sum is exact); the remainder N 2^32 - w b^K decides.
+__device__ __forceinline__ uint32_t halton_scale(uint32_t N, uint32_t mp, uint32_t s_lo, uint32_t s_hi) {
+  uint32_t w = N * s_hi + __umulhi(N, s_lo);
+  if (((uint64_t)N << 32) - (uint64_t)w * mp >= mp) ++w;
+  return w;
+}
+
+// The digit groups of x < b^K, least significant first: g < G-1 hold L digits
+// (x mod b^L by the magic reciprocal), the top group the remaining L' digits.
+__device__ __forceinline__ void halton_groups(uint32_t x, uint32_t G, uint32_t bL, uint64_t mg,
+                                              uint32_t (&out)[kHaltonMaxGroups]) {
+#pragma unroll
+  for (int g = 0; g < kHaltonMaxGroups; ++g) {
+    if ((uint32_t)g + 1 < G) {
+      const uint32_t q = (uint32_t)__umul64hi(x, mg);
+      out[g] = x - q * bL;
+      x = q;
+    } else if ((uint32_t)g + 1 == G) {
+      out[g] = x;
+    } else {
+      out[g] = 0;
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kThreads) halton_points_kernel(HaltonArgs p) {
   extern __shared__ __align__(16) uint32_t hsmem[];
-  uint32_t* stage = hsmem;                                            // [R][stride]
-  uint16_t* htab = reinterpret_cast<uint16_t*>(hsmem + p.stage_words);  // digit-group tables
+  uint16_t* htab = reinterpret_cast<uint16_t*>(hsmem);  // digit-group tables
   for (uint32_t jo = 0; jo < p.s; ++jo) {
     const uint32_t j = p.dim0 + jo;
     const uint32_t b = g_halton.base[j];
@@ -78,69 +101,136 @@ __global__ void __launch_bounds__(kThreads) halton_points_kernel(HaltonArgs p) {
       const bool top = e >= bL;
       uint32_t x = top ? e - bL : e;
       const uint32_t nd = top ? g_halton.top_digits[j] : g_halton.digits[j];
+      const uint64_t mb = g_halton.magic_base[j];
       uint32_t num = 0;
       for (uint32_t k = 0; k < nd; ++k) {  // lowest digit first: it becomes the most significant
-        uint32_t d = x % b;
-        x /= b;
-        if (p.mode == 1) d = g_halton.perm[poff + d];
-        else if (p.mode == 2) d = (p.mult[jo] * d) % b;
+        const uint32_t q = (uint32_t)__umul64hi(x, mb);
+        uint32_t d = x - q * b;
+        x = q;
+        if (p.mode == 1) {
+          d = g_halton.perm[poff + d];
+        } else if (p.mode == 2) {
+          const uint32_t md = p.mult[jo] * d;  // < b^2
+          d = md - (uint32_t)__umul64hi(md, mb) * b;
+        }
         num = num * b + d;
       }
       t[e] = (uint16_t)num;
     }
   }
+  __syncthreads();
 
-  const uint32_t s = p.s, R = p.tile_rows, stride = p.stage_stride;
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
-  const uint32_t units = s * (R / kHaltonRowsPerUnit);
-  const uint64_t mag_s = s > 1 ? ~0ull / s + 1 : 0;  // e / s for e < 2^32
-  const uint64_t n_tiles = (p.count + R - 1) / R;
-  for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const uint64_t row0 = tile * R;
-    const uint64_t left = p.count - row0;
-    const uint32_t rows = left < R ? (uint32_t)left : R;
-    __syncthreads();  // tables built / the previous tile written out
-    for (uint32_t u = warp; u < units; u += warps) {
-      const uint32_t jo = u / (R / kHaltonRowsPerUnit);
-      const uint32_t r0 = (u - jo * (R / kHaltonRowsPerUnit)) * kHaltonRowsPerUnit + lane;
-      const uint32_t j = p.dim0 + jo;
-      const uint32_t b = g_halton.base[j];
-      uint32_t v[4];
-      if (b == 2) {
+  const uint32_t s = p.s, lane = threadIdx.x & 31u;
+  const uint32_t w0 = s < 32u ? s : 32u, k0 = 32u / w0;
+  const uint32_t w1 = s > 32u ? s - 32u : 0u, k1 = w1 ? 32u / w1 : 1u;
+  const uint64_t U0 = (uint64_t)kHaltonSteps * k0, U1 = (uint64_t)kHaltonSteps * k1;
+  const uint64_t n0 = (p.count + U0 - 1) / U0, n1 = w1 ? (p.count + U1 - 1) / U1 : 0;
+  const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  // this lane's place in a unit of either chunk: (row offset, output dimension)
+  const uint32_t ro0 = lane / w0, jo0 = lane % w0;
+  const uint32_t ro1 = w1 ? lane / w1 : 0u, jo1 = w1 ? 32u + lane % w1 : 0u;
+  for (uint64_t u = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < n0 + n1; u += nw) {
+    const bool c1 = u >= n0;
+    const uint32_t w = c1 ? w1 : w0, k = c1 ? k1 : k0;
+    const uint64_t U = c1 ? U1 : U0;
+    const uint64_t r0 = (c1 ? u - n0 : u) * U;
+    if (lane >= k * w) continue;  // w does not divide 32: the remaining lanes idle
+    const uint32_t jo = c1 ? jo1 : jo0;
+    const uint64_t row = r0 + (c1 ? ro1 : ro0);
+    const uint64_t r_end = r0 + U < p.count ? r0 + U : p.count;
+    if (row >= r_end) continue;
+    const uint32_t steps = ((uint32_t)(r_end - row) + k - 1) / k;  // r_end - row <= U = 128 k
+    const uint64_t doff = (uint64_t)k * s;
+    uint64_t off = row * s + jo;
+    const uint32_t j = p.dim0 + jo;
+    const uint32_t b = g_halton.base[j];
+    const uint64_t i = ((p.index_begin + row) << p.q) | p.pconst;
+    // Base 2 (the bit reversal of the low 32 index bits, which advance by k 2^q mod 2^32)
+    // runs the same loop with a lowest group that never carries, so the warp does not
+    // split into two loops.
+    const bool two = b == 2;
+    uint32_t lo = (uint32_t)i;
+    const uint32_t dlo = (uint32_t)((uint64_t)k << p.q);
+    const uint32_t mp = two ? 1u : g_halton.max_power[j];
+    const uint32_t bL = two ? 0xFFFFFFFFu : g_halton.group_pow[j], bLp = two ? 1u : g_halton.top_pow[j];
+    const uint32_t G = two ? 2u : g_halton.groups[j];
+    const uint64_t mg = two ? 0ull : g_halton.magic_group[j], sc = two ? 0ull : g_halton.scale[j];
+    const uint32_t s_lo = (uint32_t)sc, s_hi = (uint32_t)(sc >> 32);
+    const uint16_t* tab = htab + p.table_off[jo];
+    const uint32_t x = two ? 0u
+                           : (i >> 32) ? (uint32_t)(i % mp)
+                                       : (uint32_t)i - mp * (uint32_t)__umul64hi((uint32_t)i, g_halton.magic_max[j]);
+    uint32_t xg[kHaltonMaxGroups], dg[kHaltonMaxGroups], wg[kHaltonMaxGroups];
+    halton_groups(x, G, bL, mg, xg);
+    const uint32_t D = two ? 0u : p.delta[jo];  // (k 2^q) mod b^K
+    halton_groups(D, G, bL, mg, dg);
+    const bool d_hi = D >= bL;  // the step reaches beyond the lowest group
+    // weights of the mirrored groups: N = sum_g T_g[x_g] wg[g], the lowest group the most significant
+    uint32_t wacc = 1;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) v[c] = __brev((uint32_t)(((p.index_begin + row0 + r0 + 32u * c) << p.q) | p.pconst));
-      } else {
-        const uint32_t mp = g_halton.max_power[j], bL = g_halton.group_pow[j], G = g_halton.groups[j];
-        const uint64_t mg = g_halton.magic_group[j], mm = g_halton.magic_max[j];
-        const uint16_t* t = htab + p.table_off[jo];
-        uint32_t x[4], N[4];
+    for (int g = kHaltonMaxGroups - 1; g >= 0; --g) {
+      wg[g] = wacc;
+      if ((uint32_t)g + 1 == G) wacc = bLp;
+      else if ((uint32_t)g + 1 < G) wacc *= bL;
+    }
+    auto entry = [&](int g) -> uint32_t {  // T_g[x_g]: the top group has its own table after the full one
+      return two ? 0u : (uint32_t)tab[(uint32_t)g + 1 == G ? bL + xg[g] : xg[g]];
+    };
+    auto rest = [&]() {  // the groups above the lowest
+      uint32_t r = 0;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const uint64_t i = ((p.index_begin + row0 + r0 + 32u * c) << p.q) | p.pconst;
-          x[c] = (i >> 32) ? (uint32_t)(i % mp) : (uint32_t)i - mp * (uint32_t)__umul64hi((uint32_t)i, mm);
-          N[c] = 0;
+      for (int g = 1; g < kHaltonMaxGroups; ++g)
+        if ((uint32_t)g < G) r += entry(g) * wg[g];
+      return r;
+    };
+    // add the step's higher digits (when d_hi) and a carry to groups 1.., wrapping mod b^K
+    auto add_high = [&](uint32_t carry) {
+#pragma unroll
+      for (int g = 1; g < kHaltonMaxGroups; ++g) {
+        if ((uint32_t)g < G) {
+          const uint32_t lim = (uint32_t)g + 1 == G ? bLp : bL;
+          const uint32_t v = xg[g] + (d_hi ? dg[g] : 0u) + carry;
+          carry = v >= lim ? 1u : 0u;
+          xg[g] = carry ? v - lim : v;
         }
-        for (uint32_t m = 1; m < G; ++m) {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const uint32_t q = (uint32_t)__umul64hi(x[c], mg);
-            N[c] = N[c] * bL + t[x[c] - q * bL];
-            x[c] = q;
+      }
+    };
+    uint32_t nrest = rest();
+    uint32_t t1 = entry(1);  // group 1's current entry
+    const uint32_t lim1 = G == 2 ? bLp : bL, w1g = wg[1];
+    uint32_t x0 = xg[0];
+    const uint32_t d0 = dg[0], w0g = wg[0];
+    auto emit = [&]() {  // the current row's coordinate
+      const uint32_t N = nrest + (two ? 0u : (uint32_t)tab[x0]) * w0g;
+      const uint32_t v = two ? __brev(lo) : halton_scale(N, mp, s_lo, s_hi);
+      store1(p.out_u32, p.out_f32, off, v);
+      off += doff;
+      lo += dlo;
+      x0 += d0;
+      const bool carry0 = x0 >= bL;
+      if (carry0) x0 -= bL;
+      return carry0;
+    };
+    if (!d_hi) {  // the step lies in the lowest group: the higher groups move only on its carry
+      for (uint32_t t = 0; t < steps; ++t) {
+        if (emit()) {
+          if (xg[1] + 1 < lim1) {  // the common carry: group 1 moves by one
+            ++xg[1];
+            const uint32_t t1n = entry(1);
+            nrest += (t1n - t1) * w1g;  // exact modulo 2^32, and the result is below b^K
+            t1 = t1n;
+          } else {
+            add_high(1u);
+            nrest = rest();
+            t1 = entry(1);
           }
         }
-        const uint32_t bLp = g_halton.top_pow[j];
-        const uint64_t sc = g_halton.scale[j];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) v[c] = halton_scale(N[c] * bLp + t[bL + x[c]], mp, sc);
       }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) stage[(r0 + 32u * c) * stride + jo] = v[c];
-    }
-    __syncthreads();
-    const uint32_t elems = rows * s;
-    for (uint32_t e = threadIdx.x; e < elems; e += blockDim.x) {
-      const uint32_t r = s > 1 ? (uint32_t)__umul64hi(e, mag_s) : e;
-      store1(p.out_u32, p.out_f32, row0 * s + e, stage[r * stride + (e - r * s)]);
+    } else {  // every step moves the higher groups (a partitioned sequence)
+      for (uint32_t t = 0; t < steps; ++t) {
+        add_high(emit() ? 1u : 0u);
+        nrest = rest();
+      }
     }
   }
 }
@@ -217,6 +307,7 @@ static const HaltonTables* halton_host_tables() {
       h.magic_group[j] = UINT64_MAX / bL + 1;
       h.magic_max[j] = UINT64_MAX / mp + 1;
       h.scale[j] = UINT64_MAX / mp;  // mp is odd for b > 2: floor(2^64 / mp) = floor((2^64 - 1) / mp)
+      h.magic_base[j] = UINT64_MAX / b + 1;
       h.perm_off[j] = off;
       if (off + b <= kHaltonPermWords)
         for (uint32_t d = 0; d < b; ++d) h.perm[off + d] = faure[b][d];
@@ -251,17 +342,22 @@ cudaError_t launch_halton_points(const HaltonArgs& args, cudaStream_t stream) {
   if (e != cudaSuccess) return e;
   const HaltonTables& h = *halton_host_tables();  // non-null: ensure_halton_tables succeeded
   HaltonArgs p = args;
-  // tile rows: a multiple of 128, at least 32 units of (dimension, 128 rows) per tile
-  p.tile_rows = kHaltonRowsPerUnit * ((32 + p.s - 1) / p.s > 2 ? (32 + p.s - 1) / p.s : 2);
-  p.stage_stride = p.s | 1u;  // odd: the lanes of a warp hit distinct banks
-  p.stage_words = p.tile_rows * p.stage_stride;
   uint32_t table_words = 0;  // uint16 entries
   for (uint32_t jo = 0; jo < p.s; ++jo) {
     const uint32_t j = p.dim0 + jo;
+    p.table_off[jo] = 0;  // base 2 reads no table; its offset stays inside the buffer all the same
+    p.delta[jo] = 0;
+    if (h.base[j] == 2) continue;
     p.table_off[jo] = table_words;
-    if (h.base[j] != 2) table_words += h.group_pow[j] + h.top_pow[j];
+    if (h.groups[j] < 2) return cudaErrorInvalidValue;  // the lowest group is a full one
+    table_words += h.group_pow[j] + h.top_pow[j];
+    // the index step of this dimension's lanes: k rows, k = floor(32 / w) for the chunk's width w
+    const uint32_t chunk_w = jo < 32 ? (p.s < 32 ? p.s : 32) : p.s - 32;
+    const uint64_t k = 32 / chunk_w, mp = h.max_power[j];
+    const uint64_t pow2q = (p.q < 64 ? (1ull << p.q) : 0ull) % mp;
+    p.delta[jo] = (uint32_t)((k % mp) * pow2q % mp);
   }
-  const size_t smem = (size_t)p.stage_words * sizeof(uint32_t) + (size_t)table_words * sizeof(uint16_t);
+  const size_t smem = ((size_t)(table_words ? table_words : 1) * sizeof(uint16_t) + 15) & ~(size_t)15;
   const DeviceInfo& dev = device_info();
   if (smem > dev.smem_per_block_optin) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
@@ -273,8 +369,16 @@ cudaError_t launch_halton_points(const HaltonArgs& args, cudaStream_t stream) {
   cudaError_t eo = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, halton_points_kernel, kThreads, smem);
   if (eo != cudaSuccess) return eo;
   uint64_t blocks = (uint64_t)dev.sm_count * (per_sm < 1 ? 1 : per_sm);
-  const uint64_t tiles = (p.count + p.tile_rows - 1) / p.tile_rows;
-  if (tiles < blocks) blocks = tiles;
+  // units of kHaltonSteps steps: one chunk of up to 32 dimensions, k rows per step
+  const uint32_t w0 = p.s < 32 ? p.s : 32, w1 = p.s > 32 ? p.s - 32 : 0;
+  const uint64_t U0 = (uint64_t)kHaltonSteps * (32 / w0);
+  uint64_t units = (p.count + U0 - 1) / U0;
+  if (w1) {
+    const uint64_t U1 = (uint64_t)kHaltonSteps * (32 / w1);
+    units += (p.count + U1 - 1) / U1;
+  }
+  const uint64_t need = (units + kThreads / 32 - 1) / (kThreads / 32);
+  if (need < blocks) blocks = need;
   if (blocks < 1) blocks = 1;
   halton_points_kernel<<<(unsigned)blocks, kThreads, smem, stream>>>(p);
   return cudaGetLastError();

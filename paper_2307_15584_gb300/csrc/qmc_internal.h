@@ -65,30 +65,6 @@ struct RandomPointsArgs {
 
 cudaError_t launch_random_lattice_points(const RandomPointsArgs& a, cudaStream_t stream);
 
-// Radical inversion in prime bases (Sec. 2.2).  The per-base constants (the
-// first 64 primes, their domain limits, division reciprocals and Faure tables)
-// never change; points.cu writes them once per device into a device table.
-// The per-call arguments stay small (kernel parameters).
-constexpr uint32_t kHaltonMaxDims = 64;
-struct HaltonArgs {
-  uint32_t* out_u32;
-  float* out_f32;
-  uint64_t count;
-  uint64_t index_begin;                // row r: index ((index_begin + r) << q) | pconst
-  uint64_t pconst;
-  uint32_t q, dim0;                    // output dimension j is Halton dimension dim0 + j
-  uint32_t s, mode;                    // mode: 0 identity, 1 Faure, 2 linear
-  uint32_t mult[kHaltonMaxDims];       // linear digit scramble multipliers per output dimension
-  // set by the launcher: shared-memory layout
-  uint32_t tile_rows, stage_stride, stage_words;
-  uint32_t table_off[kHaltonMaxDims];
-};
-
-// Enqueues the Halton kernel; writes the device table first if this device has
-// not received it yet (a synchronous copy).
-cudaError_t launch_halton_points(const HaltonArgs& p, cudaStream_t stream);
-// The j-th prime (j < kHaltonMaxDims).
-uint32_t halton_base(uint32_t j);
 cudaError_t launch_sobol_points(PointsArgs a, cudaStream_t stream);
 cudaError_t launch_lattice_points(PointsArgs a, cudaStream_t stream);
 
