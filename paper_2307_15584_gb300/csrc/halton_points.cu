@@ -140,8 +140,13 @@ __global__ void __launch_bounds__(kThreads) halton_points_kernel(HaltonArgs p) {
     const uint64_t r_end = r0 + U < p.count ? r0 + U : p.count;
     if (row >= r_end) continue;
     const uint32_t steps = ((uint32_t)(r_end - row) + k - 1) / k;  // r_end - row <= U = 128 k
-    const uint64_t doff = (uint64_t)k * s;
-    uint64_t off = row * s + jo;
+    // the unit's outputs from its first row on; a unit spans at most 256 k s <= 2^19 elements,
+    // so the step offset stays 32-bit (the null tests are on the kernel parameters: uniform)
+    const uint64_t off0 = row * s + jo;
+    uint32_t* const ou = p.out_u32 ? p.out_u32 + off0 : nullptr;
+    float* const of = p.out_f32 ? p.out_f32 + off0 : nullptr;
+    const uint32_t dofs = k * s;
+    uint32_t ofs = 0;
     const uint32_t j = p.dim0 + jo;
     const uint32_t b = g_halton.base[j];
     const uint64_t i = ((p.index_begin + row) << p.q) | p.pconst;
@@ -203,8 +208,9 @@ __global__ void __launch_bounds__(kThreads) halton_points_kernel(HaltonArgs p) {
     auto emit = [&]() {  // the current row's coordinate
       const uint32_t N = nrest + (two ? 0u : (uint32_t)tab[x0]) * w0g;
       const uint32_t v = two ? __brev(lo) : halton_scale(N, mp, s_lo, s_hi);
-      store1(p.out_u32, p.out_f32, off, v);
-      off += doff;
+      if (p.out_u32) ou[ofs] = v;
+      if (p.out_f32) of[ofs] = map_u32_to_unifloat(v);
+      ofs += dofs;
       lo += dlo;
       x0 += d0;
       const bool carry0 = x0 >= bL;
