@@ -21,9 +21,11 @@ Also reported in the same JSON line:
                 Gsamples/s with its QMC error against the closed-form
                 integrals and its instruction-issue roofline (parity with the
                 fp64 oracle is the GPU test suite's job, not the bench's);
-                and every materialising point generator on the headline shape
+                and every materialising point generator on the headline shape;
+                and one integral of 16 (2^32 - 1) samples over the elements of
+                a partitioned 64-bit Sobol' sequence
 
---only {fwd_bwd,batched,lattice,points} --small runs one extra workload alone at
+--only {fwd_bwd,batched,lattice,points,partition,samplers} --small runs one extra workload alone at
 a reduced size (for ncu captures); --impl reference times the oracle (the plain
 CPU reference of the same computation) on a bounded sample of the headline
 workload.  Under torchrun every rank materialises its own index window (weak
@@ -60,7 +62,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="headline only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     ap.add_argument("--log2-points", type=int, default=24, help="points per GPU (2^k); 24 is the workload")
-    ap.add_argument("--only", choices=["fwd_bwd", "batched", "lattice", "points", "samplers"], default=None,
+    ap.add_argument("--only", choices=["fwd_bwd", "batched", "lattice", "points", "samplers", "partition"],
+                    default=None,
                     help="run one extra workload alone (no headline)")
     ap.add_argument("--small", action="store_true", help="reduced integration sizes (profiling)")
     ap.add_argument("--plan", choices=["window", "partition"], default="window",
@@ -251,6 +254,16 @@ def extras_cpu_baselines(names) -> dict:
                                          threads=threads),
                 4.0 * N, "Gsamples/s", "4 integrals x 2^20 of the 2^26 points", threads)
         out["lattice"] = res
+    if "partition" in names:  # the 16 elements x 2^16 of their 2^32 - 1 samples
+        s, q, n = 16, 4, 1 << 16
+        W = oracle.sobol_matrices_wide(s + 1, 64, inputs.sobol_raw_init(s + 1))
+        th = inputs.genz_params("product_peak", s, 0)
+        out["partition"] = _oracle_rate(
+            lambda: oracle.integrate_partitioned(oracle.F_GENZ_PRODUCT_PEAK, s, np.full(16, n, np.uint32),
+                                                 np.tile(th, (16, 1)), W, q, np.arange(16),
+                                                 scramble=oracle.SCRAMBLE_NESTED, seeds=inputs.scramble_seeds(s),
+                                                 threads=threads),
+            16.0 * n, "Gsamples/s", "the 16 elements x 2^16 of their 2^32 - 1 samples", threads)
     if "points" in names:  # every generator on s = 32, 2^10 .. 2^20 rows (about half a second each)
         s, n, nl = S_DIMS, 1 << 18, 1 << 10
         nb = 1 << 20
@@ -589,6 +602,41 @@ def error_spectrum_low_ratio(err: np.ndarray, band: float = 0.125) -> float:
     return float(P[low].mean() / P[r > 0].mean())
 
 
+def bench_partition(dev, steps, warmup, small, sm_mhz):
+    """One integral over the first 16 (2^32 - 1) ~ 6.9e10 points of a 64-bit Sobol'
+    sequence (Sec. 2.5.1): the 16 elements of the sequence partitioned by its
+    dimension 0 integrate as 16 integrals of 2^32 - 1 samples each (2^24 when
+    small), whose mean is the estimate; Genz product peak, s = 16, nested
+    scramble, with the error against the closed form."""
+    import torch
+
+    from paper_2307_15584_gb300 import binding as B
+    from paper_2307_15584_gb300 import inputs
+
+    stream = torch.cuda.current_stream()
+    s, q = 16, 4
+    P, n = 1 << q, (1 << 24) if small else (1 << 32) - 1
+    W = B.qmc_sobol_matrices_wide(s + 1, 64, inputs.sobol_raw_init(s + 1))
+    th = inputs.genz_params("product_peak", s, 0)
+    counts = np.full(P, n, np.uint32)
+    d = {"W": B.u32_tensor(W, dev), "sd": B.u32_tensor(inputs.scramble_seeds(s), dev),
+         "c": B.u32_tensor(counts, dev), "th": torch.from_numpy(np.tile(th, (P, 1))).to(dev)}
+    prob = B.make_problem(B.SOURCE_SOBOL, B.F_GENZ_PRODUCT_PEAK, s, B.SCRAMBLE_NESTED, matrices=d["W"], seeds=d["sd"],
+                          index_bits=64, partition_log2=q)
+    ws = B.alloc_workspace(prob, P, counts, dev)
+    est = torch.empty(P, dtype=torch.float64, device=dev)
+    tuned = B.qmc_tune_integrate(prob, P, d["c"], d["th"], est, ws)
+    ms = statistics.median(timed(lambda: B.qmc_integrate(prob, P, d["c"], d["th"], est, ws), steps, warmup, stream))
+    e = est.cpu().numpy()
+    exact = genz_exact("product_peak", th, s)
+    samples = float(counts.sum())
+    return {"elements": P, "samples_per_element": n, "samples": int(samples), "index_bits": 64, "ms": ms,
+            "gsamples_s": samples / (ms * 1e-3) / 1e9, "tuned": {"chunk": tuned.chunk, "block": tuned.block},
+            "estimate": float(e.mean()), "rel_err_vs_exact": float(abs(e.mean() - exact) / exact),
+            "element_rel_spread": float((e.max() - e.min()) / exact), "parity": PARITY_NOTE,
+            "roofline": issue_roofline(samples / (ms * 1e-3), "integrate_main<sobol16,nested,product_peak>", sm_mhz)}
+
+
 def bench_samplers(dev, steps, warmup, small, sm_mhz):
     """Fig. 1 substitute (Sec. 3): two 1920x1080 images (480x270 when small),
     estimated at 4 / 16 / 64 / 256 samples per pixel by the samplers the paper
@@ -691,9 +739,9 @@ def bench_samplers(dev, steps, warmup, small, sm_mhz):
 
 
 def run_extras(args, dev, sm_mhz):
-    which = [args.only] if args.only else ["fwd_bwd", "batched", "lattice", "points", "samplers"]
+    which = [args.only] if args.only else ["fwd_bwd", "batched", "lattice", "points", "partition", "samplers"]
     fns = {"fwd_bwd": bench_fwd_bwd, "batched": bench_batched, "lattice": bench_lattice,
-           "points": bench_points, "samplers": bench_samplers}
+           "points": bench_points, "samplers": bench_samplers, "partition": bench_partition}
     out = {}
     for name in which:
         steps = 3 if args.small else 5
