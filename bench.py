@@ -280,6 +280,8 @@ def extras_cpu_baselines(names) -> dict:
                                                                                      threads=threads)),
             "lattice_shifted": (nb, lambda: oracle.lattice_points(g, sh, 0, nb, threads=threads)),
             "halton_faure": (nl, lambda: oracle.halton_points(s, 0, nl, oracle.HALTON_FAURE, threads=threads)),
+            "halton_faure_partition_p5_of_8": (n, lambda: oracle.halton_points_partitioned(
+                s, 3, 5, 1 << 30, n, oracle.HALTON_FAURE, threads=threads)),
             "pixel_lattice_16spp": (8 * nl, lambda: oracle.pixel_lattice_points(g, 1024, nl // 2, 16, height=1024)),
             "random_lattice_hash_x4_16spp": (nb, lambda: oracle.random_lattice_points(
                 oracle.RLAT_HASH, 7, 4, s, 1024, nb // 16, 16, threads=threads)),
@@ -527,7 +529,8 @@ def bench_points(dev, steps, warmup, small, sm_mhz):
     u32 + fp32, 8 B written per coordinate; 2^20 rows when small): the 32-bit
     Sobol' headline kernel again, Sobol' with 64-bit indices at 2^40 (Alg. 3),
     one element of a partitioned Sobol' sequence (Sec. 2.5.1), the shifted
-    rank-1 lattice, Halton (Faure), the pixel-shifted lattice and the per-pixel
+    rank-1 lattice, Halton (Faure; whole, and one element of the sequence
+    partitioned by its base-2 dimension), the pixel-shifted lattice and the per-pixel
     random lattices with 4 superimposed instances (2^20 pixels x 16 samples).
     Each against the measured copy bandwidth."""
     import torch
@@ -551,6 +554,8 @@ def bench_points(dev, steps, warmup, small, sm_mhz):
                                                                             B.SCRAMBLE_NESTED, sd, u, f),
         "lattice_shifted": lambda: B.qmc_lattice_points(g, sh, s, 0, n, 0, u, f),
         "halton_faure": lambda: B.qmc_halton_points(s, B.HALTON_FAURE, None, 0, n, u, f),
+        "halton_faure_partition_p5_of_8": lambda: B.qmc_halton_points_partitioned(s, B.HALTON_FAURE, None, 3, 5,
+                                                                                  1 << 30, n, u, f),
         "pixel_lattice_16spp": lambda: B.qmc_pixel_lattice_points(g, s, 1024, n // 16 // 1024 or 1, 0,
                                                                    n // 16, 16, u, f),
         "random_lattice_hash_x4_16spp": lambda: B.qmc_random_lattice_points(B.RLAT_HASH, 7, 4, s, 1024,
