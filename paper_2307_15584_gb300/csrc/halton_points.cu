@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kThreads) halton_points_kernel(HaltonArgs p) {
     const uint64_t row = r0 + (c1 ? ro1 : ro0);
     const uint64_t r_end = r0 + U < p.count ? r0 + U : p.count;
     if (row >= r_end) continue;
-    const uint32_t steps = ((uint32_t)(r_end - row) + k - 1) / k;  // r_end - row <= U = 128 k
+    const uint32_t steps = ((uint32_t)(r_end - row) + k - 1) / k;  // r_end - row <= U = kHaltonSteps k
     // the unit's outputs from its first row on; a unit spans at most 256 k s <= 2^19 elements,
     // so the step offset stays 32-bit (the null tests are on the kernel parameters: uniform)
     const uint64_t off0 = row * s + jo;
