@@ -42,7 +42,7 @@ struct HaltonTables {
   uint32_t top_pow[kHaltonMaxDims];    // b^L'
   uint64_t magic_group[kHaltonMaxDims];  // floor(2^64 / b^L) + 1: x / b^L = umulhi(x, .) for x < 2^32
   uint64_t magic_max[kHaltonMaxDims];    // floor(2^64 / b^K) + 1: the same for b^K
-  uint64_t scale[kHaltonMaxDims];        // floor(2^64 / b^K): floor(N 2^32 / b^K) up to one correction
+  uint32_t recip96[kHaltonMaxDims][3];   // ceil(2^96 / b^K) = [2] 2^64 + [1] 2^32 + [0]: floor(N 2^32 / b^K)
   uint64_t magic_base[kHaltonMaxDims];   // floor(2^64 / b) + 1: x / b = umulhi(x, .) for x < 2^32
   uint16_t perm[kHaltonPermWords];
 };
@@ -60,13 +60,12 @@ __device__ HaltonTables g_halton;
 constexpr uint32_t kHaltonSteps = 256;
 constexpr int kHaltonMaxGroups = 6;  // G <= 6 for every base up to the 64th prime (base 37: L = 1, K = 6)
 
-// floor(N 2^32 / b^K) for N < b^K < 2^32: with S = floor(2^64 / b^K) = S_hi 2^32 + S_lo,
-// w = floor(N S / 2^32) = N S_hi + umulhi(N, S_lo) is at most one below (and below
-// 2^32, so the 32-bit sum is exact); the remainder N 2^32 - w b^K decides.
-__device__ __forceinline__ uint32_t halton_scale(uint32_t N, uint32_t mp, uint32_t s_lo, uint32_t s_hi) {
-  uint32_t w = N * s_hi + __umulhi(N, s_lo);
-  if (((uint64_t)N << 32) - (uint64_t)w * mp >= mp) ++w;
-  return w;
+// floor(N 2^32 / b^K) for N < b^K < 2^32, exactly: with M = ceil(2^96 / b^K) = M2 2^64 + M1 2^32 + M0,
+// N M / 2^64 exceeds N 2^32 / b^K by less than N / 2^64 < 1 / b^K (as N b^K < 2^64), which never
+// reaches the next integer, so the result is floor(N M / 2^64) = N M2 + hi32(N M1 + umulhi(N, M0)).
+__device__ __forceinline__ uint32_t halton_scale(uint32_t N, uint32_t m0, uint32_t m1, uint32_t m2) {
+  const uint64_t a = (uint64_t)N * m1 + __umulhi(N, m0);
+  return N * m2 + (uint32_t)(a >> 32);
 }
 
 // The digit groups of x < b^K, least significant first: g < G-1 hold L digits
@@ -157,10 +156,11 @@ __global__ void __launch_bounds__(kThreads) halton_points_kernel(HaltonArgs p) {
     uint32_t lo = (uint32_t)i;
     const uint32_t dlo = (uint32_t)((uint64_t)k << p.q);
     const uint32_t mp = two ? 1u : g_halton.max_power[j];
+    const uint32_t m0 = two ? 0u : g_halton.recip96[j][0], m1 = two ? 0u : g_halton.recip96[j][1];
+    const uint32_t m2 = two ? 0u : g_halton.recip96[j][2];
     const uint32_t bL = two ? 0xFFFFFFFFu : g_halton.group_pow[j], bLp = two ? 1u : g_halton.top_pow[j];
     const uint32_t G = two ? 2u : g_halton.groups[j];
-    const uint64_t mg = two ? 0ull : g_halton.magic_group[j], sc = two ? 0ull : g_halton.scale[j];
-    const uint32_t s_lo = (uint32_t)sc, s_hi = (uint32_t)(sc >> 32);
+    const uint64_t mg = two ? 0ull : g_halton.magic_group[j];
     const uint16_t* tab = htab + p.table_off[jo];
     const uint32_t x = two ? 0u
                            : (i >> 32) ? (uint32_t)(i % mp)
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kThreads) halton_points_kernel(HaltonArgs p) {
     const uint32_t d0 = dg[0], w0g = wg[0];
     auto emit = [&]() {  // the current row's coordinate
       const uint32_t N = nrest + (two ? 0u : (uint32_t)tab[x0]) * w0g;
-      const uint32_t v = two ? __brev(lo) : halton_scale(N, mp, s_lo, s_hi);
+      const uint32_t v = two ? __brev(lo) : halton_scale(N, m0, m1, m2);
       if (p.out_u32) ou[ofs] = v;
       if (p.out_f32) of[ofs] = map_u32_to_unifloat(v);
       ofs += dofs;
@@ -312,7 +312,10 @@ static const HaltonTables* halton_host_tables() {
       h.top_pow[j] = (uint32_t)bLp;
       h.magic_group[j] = UINT64_MAX / bL + 1;
       h.magic_max[j] = UINT64_MAX / mp + 1;
-      h.scale[j] = UINT64_MAX / mp;  // mp is odd for b > 2: floor(2^64 / mp) = floor((2^64 - 1) / mp)
+      const unsigned __int128 r96 = ((((unsigned __int128)1) << 96) - 1) / mp + 1;  // mp odd: not a divisor of 2^96
+      h.recip96[j][0] = (uint32_t)r96;
+      h.recip96[j][1] = (uint32_t)(r96 >> 32);
+      h.recip96[j][2] = (uint32_t)(r96 >> 64);
       h.magic_base[j] = UINT64_MAX / b + 1;
       h.perm_off[j] = off;
       if (off + b <= kHaltonPermWords)
