@@ -266,11 +266,13 @@ template <int FN>
 struct Integrand;
 
 // Every integrand offers eval<EXACT>(x, err): f(x) in fp32 and, for adaptive
-// integrands, err = an estimate of the sample's rounding error scale.  EXACT
-// selects the float-float evaluation used when an item's error estimate is
-// over budget; non-adaptive integrands ignore it.  With kExactPair the EXACT
-// evaluation returns f as a float pair (the value and, in err, its low word),
-// and both words enter the compensated sum sample by sample.
+// integrands, err = an estimate of the sample's rounding error scale (kErrUnit
+// turns it into an absolute scale).  EXACT selects the float-float evaluation
+// used when an item's error estimate is over budget; non-adaptive integrands
+// ignore it.  With kExactPair the EXACT evaluation returns f as a float pair
+// (the value and, in err, its low word), and both words enter the compensated
+// sum sample by sample.  kMinBlocks is the kernel's minimum of resident
+// 256-thread blocks per SM (0: the compiler's choice of registers).
 constexpr float kLn2 = 0.693147180559945309f;
 
 // ---------------------------------------------------------------------------
