@@ -274,6 +274,7 @@ def extras_cpu_baselines(names) -> dict:
         nested = oracle.SCRAMBLE_NESTED
         runs = {
             "sobol32_nested": (n, lambda: oracle.sobol_points(C, 0, n, nested, sd, threads=threads)),
+            "sobol32_nested_from_index_1": (n, lambda: oracle.sobol_points(C, 1, n, nested, sd, threads=threads)),
             "sobol64_nested_at_2^40": (n, lambda: oracle.sobol_points_wide(W[:s], 1 << 40, n, nested, sd,
                                                                            threads=threads)),
             "sobol64_partition_p5_of_8": (n, lambda: oracle.sobol_points_partitioned(W, 3, 5, 1 << 37, n, nested, sd,
@@ -527,7 +528,8 @@ def bench_lattice(dev, steps, warmup, small, sm_mhz):
 def bench_points(dev, steps, warmup, small, sm_mhz):
     """Every materialising generator on the headline's shape (s = 32, 2^24 rows,
     u32 + fp32, 8 B written per coordinate; 2^20 rows when small): the 32-bit
-    Sobol' headline kernel again, Sobol' with 64-bit indices at 2^40 (Alg. 3),
+    Sobol' headline kernel again, the same from index 1 (off the fast path's
+    group grid: the walking kernel), Sobol' with 64-bit indices at 2^40 (Alg. 3),
     one element of a partitioned Sobol' sequence (Sec. 2.5.1), the shifted
     rank-1 lattice, Halton (Faure; whole, and one element of the sequence
     partitioned by its base-2 dimension), the pixel-shifted lattice and the per-pixel
@@ -549,6 +551,7 @@ def bench_points(dev, steps, warmup, small, sm_mhz):
     g, sh = B.u32_tensor(inputs.lattice_generator(s), dev), B.u32_tensor(inputs.lattice_shift(s), dev)
     runs = {
         "sobol32_nested": lambda: B.qmc_sobol_points(C, s, 0, n, B.SCRAMBLE_NESTED, sd, u, f),
+        "sobol32_nested_from_index_1": lambda: B.qmc_sobol_points(C, s, 1, n, B.SCRAMBLE_NESTED, sd, u, f),
         "sobol64_nested_at_2^40": lambda: B.qmc_sobol_points_wide(W, 64, s, 1 << 40, n, B.SCRAMBLE_NESTED, sd, u, f),
         "sobol64_partition_p5_of_8": lambda: B.qmc_sobol_points_partitioned(W, 64, s, 3, 5, 1 << 37, n,
                                                                             B.SCRAMBLE_NESTED, sd, u, f),

@@ -157,6 +157,95 @@ __global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
   if (TMA) stager.finish(lane);
 }
 
+// K1 walking path, for what the fast path's 16-byte groups do not fit (s / gcd(s, 128) > 4, or
+// an index_begin off the group grid).  Lanes own dimensions: a warp takes a chunk of up to 32
+// consecutive output dimensions (w of them) and k = floor(32 / w) consecutive rows per step, lane l
+// holding dimension l mod w of row l / w, so each step writes k whole rows of the chunk with
+// coalesced 4-byte stores.  Each lane walks its dimension down kWalkSteps steps: with the
+// enumeration index J = (J_hi << u) | J_lo, y_j = pc_j ^ Hlo_j[J_lo] ^ Hhi_j(J_hi), Hlo a
+// shared-memory table of 2^u rows (u >= 5, so one step of k <= 32 wraps J_lo at most once) and Hhi
+// changed, when J_lo wraps, by the columns of the J_hi bits that flip.
+constexpr uint32_t kWalkSteps = 256;
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) sobol_points_walk(PointsArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const uint32_t s = a.s, m = a.m, u = a.u_log2, nlo = 1u << u;
+  uint32_t* cols = smem;          // [s][m], mirrored for nested
+  uint32_t* hlo = cols + s * m;   // [2^u][s]
+  uint32_t* pc = hlo + nlo * s;   // [s]: the fixed low index part
+  for (uint32_t idx = threadIdx.x; idx < s * m; idx += blockDim.x) {
+    const uint32_t c = __ldg(a.matrices + idx);
+    cols[idx] = (MODE == 2) ? __brev(c) : c;
+  }
+  __syncthreads();
+  for (uint32_t idx = threadIdx.x; idx < nlo * s; idx += blockDim.x) {
+    const uint32_t g = idx / s, j = idx - g * s;
+    uint32_t y = 0;
+    for (uint32_t b = 0; (g >> b) != 0 && a.col0 + b < m; ++b)
+      if ((g >> b) & 1u) y ^= cols[j * m + a.col0 + b];
+    hlo[idx] = y;
+  }
+  for (uint32_t j = threadIdx.x; j < s; j += blockDim.x) {
+    uint32_t y = 0;
+    for (uint32_t b = 0; b < a.col0; ++b)
+      if ((a.pconst >> b) & 1u) y ^= cols[j * m + b];
+    pc[j] = y;
+  }
+  __syncthreads();
+
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t nch = (s + 31u) >> 5, wl = s - 32u * (nch - 1u), kl = 32u / wl;  // the last chunk: wl wide
+  const uint64_t Uf = kWalkSteps, Ul = (uint64_t)kWalkSteps * kl;  // rows per unit: full chunks, the last
+  const uint64_t nf = (a.count + Uf - 1) / Uf, nl = (a.count + Ul - 1) / Ul;
+  const uint64_t n_units = (uint64_t)(nch - 1u) * nf + nl;
+  const uint32_t hi_col = a.col0 + u;  // column of the lowest J_hi bit
+  const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t un = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); un < n_units; un += nw) {
+    const bool last = un >= (uint64_t)(nch - 1u) * nf;
+    const uint32_t c = last ? nch - 1u : (uint32_t)(un / nf);
+    const uint32_t w = last ? wl : 32u, k = last ? kl : 1u;
+    const uint64_t U = last ? Ul : Uf;
+    const uint64_t r0 = (last ? un - (uint64_t)(nch - 1u) * nf : un - (uint64_t)c * nf) * U;
+    if (lane >= k * w) continue;  // w does not divide 32: the remaining lanes idle
+    const uint32_t jo = 32u * c + lane % w;
+    const uint64_t row = r0 + lane / w;
+    const uint64_t r_end = r0 + U < a.count ? r0 + U : a.count;
+    if (row >= r_end) continue;
+    const uint32_t steps = ((uint32_t)(r_end - row) + k - 1) / k;  // r_end - row <= U <= kWalkSteps k
+    const uint64_t J = a.index_begin + row;
+    uint32_t jlo = (uint32_t)J & (nlo - 1u);
+    uint64_t jhi = J >> u;
+    const uint32_t* cj = cols + jo * m;
+    uint32_t base = pc[jo];
+    for (uint32_t b = 0; (jhi >> b) != 0 && hi_col + b < m; ++b)
+      if ((jhi >> b) & 1u) base ^= cj[hi_col + b];
+    const uint32_t seed = MODE != 0 ? __ldg(a.seeds + jo) : 0u;
+    if (MODE == 1) base ^= seed;
+    const NestedKey key = nested_key(seed);
+    // the unit's outputs from its first row on: at most kWalkSteps k s <= 2^23 elements (s <= 1024)
+    const uint64_t off0 = row * s + jo;
+    uint32_t* const ou = a.out_u32 ? a.out_u32 + off0 : nullptr;
+    float* const of = a.out_f32 ? a.out_f32 + off0 : nullptr;
+    const uint32_t dofs = k * s;
+    uint32_t ofs = 0;
+    for (uint32_t t = 0; t < steps; ++t) {
+      uint32_t y = hlo[jlo * s + jo] ^ base;
+      if (MODE == 2) y = __brev(nested_mix(y, key));
+      if (a.out_u32) ou[ofs] = y;
+      if (a.out_f32) of[ofs] = map_u32_to_unifloat(y);
+      ofs += dofs;
+      jlo += k;
+      if (jlo >= nlo) {  // J_hi advances by one: the bits of jhi ^ (jhi + 1) flip
+        jlo -= nlo;
+        ++jhi;
+        const uint32_t nflip = (uint32_t)__ffsll((long long)jhi);  // jhi > 0
+        for (uint32_t b = 0; b < nflip && hi_col + b < m; ++b) base ^= cj[hi_col + b];
+      }
+    }
+  }
+}
+
 // K1 generic path: one element per thread, columns read through the cache.
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) sobol_points_generic(PointsArgs a) {
@@ -195,7 +284,22 @@ cudaError_t launch_sobol_points(PointsArgs a, cudaStream_t stream) {
   if (tma && (stage_words + table_words) * sizeof(uint32_t) > optin) tma = false;
   if (table_words * sizeof(uint32_t) > optin) fast = false;
   if (!fast) {
-    switch (a.scramble) {
+    // the walking path: the columns and a low table of 2^w rows, 5 <= w <= 8, in shared memory
+    uint32_t w = 8;
+    while (w > 5 && ((size_t)a.s * a.m + ((size_t)1 << w) * a.s + a.s) * sizeof(uint32_t) > optin) --w;
+    const size_t walk_smem = ((size_t)a.s * a.m + ((size_t)1 << w) * a.s + a.s) * sizeof(uint32_t);
+    if (walk_smem <= optin && a.s <= 1024) {
+      a.u_log2 = w;
+      const uint32_t nch = (a.s + 31u) >> 5, wl = a.s - 32u * (nch - 1u);
+      const uint64_t Ul = (uint64_t)kWalkSteps * (32u / wl);
+      const uint64_t units = (uint64_t)(nch - 1u) * ((a.count + kWalkSteps - 1) / kWalkSteps) + (a.count + Ul - 1) / Ul;
+      switch (a.scramble) {
+        case 0: return launch_persistent(sobol_points_walk<0>, units, walk_smem, stream, a);
+        case 1: return launch_persistent(sobol_points_walk<1>, units, walk_smem, stream, a);
+        default: return launch_persistent(sobol_points_walk<2>, units, walk_smem, stream, a);
+      }
+    }
+    switch (a.scramble) {  // tables beyond shared memory: one element per thread
       case 0: return launch_grid_stride(sobol_points_generic<0>, a.count * a.s, stream, a);
       case 1: return launch_grid_stride(sobol_points_generic<1>, a.count * a.s, stream, a);
       default: return launch_grid_stride(sobol_points_generic<2>, a.count * a.s, stream, a);

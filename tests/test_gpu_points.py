@@ -34,9 +34,11 @@ def _sobol_case(B, oracle, s, begin, count, mode, seed=7):
 
 
 @pytest.mark.parametrize("mode", [0, 1, 2])
-@pytest.mark.parametrize("s", [1, 2, 3, 4, 5, 6, 12, 16, 24, 31, 32, 33, 64, 96])
+@pytest.mark.parametrize("s", [1, 2, 3, 4, 5, 6, 7, 12, 16, 24, 31, 32, 33, 64, 96, 100, 1000])
 def test_sobol_points_bit_exact(B, oracle, s, mode):
-    """Fast path (s with K <= 4) and generic path, several groups and a ragged tail."""
+    """Fast path (s with K <= 4), the walking path (5, 7, 31, 33, 100: lanes own dimensions,
+    idle lanes, chunks of 32 and a narrower last one) and, for tables beyond shared memory
+    (1000 dimensions), one element per thread; several groups and a ragged tail."""
     count = 4096 * 3 + 37
     _sobol_case(B, oracle, s, 0, count, mode)
 
