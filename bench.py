@@ -571,6 +571,7 @@ def bench_points(dev, steps, warmup, small, sm_mhz):
     # instruction counts per coordinate (ncu, profiles/inst_per_coord.txt) for the issue roofline
     common = ["points_common.cuh", "qmc_device.cuh", "qmc_internal.h"]
     inst_keys = {"sobol32_nested": ("sobol_points_fast<1,2>", ["sobol_points.cu"]),
+                 "sobol32_nested_from_index_1": ("sobol_points_walk<2>", ["sobol_points.cu"]),
                  "lattice_shifted": ("lattice_points_fast<1,0,1>", ["lattice_points.cu"]),
                  "halton_faure": ("halton_points_kernel<faure>", ["halton_points.cu", "halton_points.h"]),
                  "pixel_lattice_16spp": ("pixel_lattice_points_fast", ["lattice_points.cu"]),

@@ -129,3 +129,29 @@ def test_random_lattice_fullsize(B, oracle, out, kind):
                        np.uint32)
         np.testing.assert_array_equal(gu[n], ref, err_msg=f"row {r}")
         np.testing.assert_array_equal(gf[n].view(np.uint32), oracle.map_u32_to_unifloat(ref).view(np.uint32))
+
+
+def test_sobol_walk_fullsize(B, oracle, out):
+    """The bench's walking-kernel configuration: s = 32 from index 1 (off the fast path's
+    group grid), nested scramble, 2^24 rows."""
+    u, f = out
+    C = B.qmc_sobol_matrices(S, inputs.sobol_raw_init(S))
+    seeds = inputs.scramble_seeds(S)
+    B.qmc_sobol_points(B.u32_tensor(C), S, 1, N, B.SCRAMBLE_NESTED, B.u32_tensor(seeds), u, f)
+    torch.cuda.synchronize()
+    _check_rows(B, oracle, u, f, _rows(8),
+                lambda r: oracle.sobol_points(C, 1 + r, 1, oracle.SCRAMBLE_NESTED, seeds, threads=1)[0][0])
+    # rows 2^k - 1 .. of the first 2^20 points from index 1 are a shifted window; the block of
+    # indices [2^20, 2^21) lies at rows 2^20 - 1 .. 2^21 - 2 and stratifies dimension 0 fully
+    top = (u[(1 << 20) - 1: (1 << 21) - 1].to(torch.int64) & 0xFFFFFFFF) >> 12
+    assert torch.equal(torch.sort(top[:, 0]).values, torch.arange(1 << 20, device="cuda"))
+
+
+def test_halton_partition_fullsize(B, oracle, out):
+    """The bench's partitioned Halton configuration: element 5 of 8 from J = 2^30, Faure."""
+    u, f = out
+    q, p, j0 = 3, 5, 1 << 30
+    B.qmc_halton_points_partitioned(S, B.HALTON_FAURE, None, q, p, j0, N, u, f)
+    torch.cuda.synchronize()
+    _check_rows(B, oracle, u, f, _rows(9),
+                lambda r: oracle.halton_points_partitioned(S, q, p, j0 + r, 1, oracle.HALTON_FAURE, threads=1)[0])
