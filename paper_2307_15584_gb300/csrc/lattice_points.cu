@@ -91,20 +91,22 @@ __global__ void __launch_bounds__(kThreads) lattice_points_generic(PointsArgs a)
   }
 }
 
-// Pixel-shifted lattice, coalesced path (s % 4 == 0, 16-byte aligned outputs,
-// 32 spp s <= 2^31).  A warp takes batches of 32 consecutive pixels: lane l
-// computes the shift of pixel l of the batch once (Hilbert position, then
-// phi_3), and the batch's 32 spp rows are written as consecutive 16-byte chunks,
-// each chunk's pixel shift fetched from its lane with a shuffle.
+// Pixel-shifted lattice, coalesced path (16-byte aligned outputs, 32 spp s <= 2^31).
+// A warp takes batches of 32 consecutive pixels: lane l computes the shift of pixel
+// l of the batch once (Hilbert position, then phi_3), and the batch's 32 spp rows
+// are written as consecutive 16-byte chunks, each element's pixel shift fetched from
+// its lane with a shuffle.  V4 (s % 4 == 0): a chunk holds four dimensions of one
+// row; otherwise each of its four elements finds its own row, dimension and pixel.
+template <bool V4>
 __global__ void __launch_bounds__(kThreads) pixel_lattice_points_fast(PixelPointsArgs a) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t n_batches = (a.n_pixels + 31) >> 5;
   uint64_t b0, b1;
   warp_range(n_batches, b0, b1);
   // x / d = umulhi(x, floor(2^64 / d) + 1) exactly for x < 2^32 and d > 1
-  const uint64_t mag_s = ~0ull / a.s + 1;  // s >= 4
+  const uint64_t mag_s = a.s > 1 ? ~0ull / a.s + 1 : 0;
   const uint64_t mag_spp = a.spp > 1 ? ~0ull / a.spp + 1 : 0;
-  const uint32_t chunks_per_pixel = a.spp * (a.s >> 2);
+  const uint32_t per_pixel = a.spp * a.s;  // elements
   for (uint64_t b = b0; b < b1; ++b) {
     const uint64_t first = b << 5;  // batch's first pixel, relative to pixel_begin
     const uint64_t left = a.n_pixels - first;
@@ -114,21 +116,43 @@ __global__ void __launch_bounds__(kThreads) pixel_lattice_points_fast(PixelPoint
       const uint64_t p = a.pixel_begin + first + lane;
       sh = pixel_shift((uint32_t)(p % a.width), (uint32_t)(p / a.width), a.grid_log2);
     }
-    const uint32_t chunks = npx * chunks_per_pixel;
-    const uint64_t off0 = first * a.spp * a.s;  // element offset of the batch
+    const uint32_t total = npx * per_pixel;  // the batch's elements
+    const uint32_t chunks = (total + 3u) >> 2;
+    const uint64_t off0 = first * per_pixel;  // element offset of the batch: a multiple of 32
     for (uint32_t c0 = 0; c0 < chunks; c0 += 32) {  // same trip count in every lane
       const uint32_t c = c0 + lane;
       const uint32_t e = 4u * c;  // element within the batch, < 2^32
-      const uint32_t row = (uint32_t)__umul64hi(e, mag_s);
-      const uint32_t j = e - row * a.s;
-      const uint32_t pl = a.spp > 1 ? (uint32_t)__umul64hi(row, mag_spp) : row;
-      const uint32_t smp = row - pl * a.spp;
-      const uint32_t shift = __shfl_sync(0xffffffffu, sh, pl & 31u);
+      uint32_t v[4];
+      if (V4) {
+        const uint32_t row = (uint32_t)__umul64hi(e, mag_s);
+        const uint32_t j = e - row * a.s;
+        const uint32_t pl = a.spp > 1 ? (uint32_t)__umul64hi(row, mag_spp) : row;
+        const uint32_t smp = row - pl * a.spp;
+        const uint32_t base = __brev(smp) + __shfl_sync(0xffffffffu, sh, pl & 31u);
+        if (c < chunks) {
+#pragma unroll
+          for (int t = 0; t < 4; ++t) v[t] = base * (__ldg(a.g + j + t) | 1u);
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const uint32_t et = e + t;
+          const uint32_t row = a.s > 1 ? (uint32_t)__umul64hi(et, mag_s) : et;
+          const uint32_t j = et - row * a.s;
+          const uint32_t pl = a.spp > 1 ? (uint32_t)__umul64hi(row, mag_spp) : row;
+          const uint32_t smp = row - pl * a.spp;
+          const uint32_t base = __brev(smp) + __shfl_sync(0xffffffffu, sh, pl & 31u);
+          v[t] = base * (__ldg(a.g + j) | 1u);  // j < s for every element
+        }
+      }
       if (c < chunks) {
-        const uint32_t base = __brev(smp) + shift;
-        const uint32_t v[4] = {base * (__ldg(a.g + j) | 1u), base * (__ldg(a.g + j + 1) | 1u),
-                               base * (__ldg(a.g + j + 2) | 1u), base * (__ldg(a.g + j + 3) | 1u)};
-        store4(a.out_u32, a.out_f32, off0 + e, v);
+        if (e + 4u <= total) {
+          store4(a.out_u32, a.out_f32, off0 + e, v);
+        } else {  // the batch's ragged end (s % 4 != 0)
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (e + t < total) store1(a.out_u32, a.out_f32, off0 + e + t, v[t]);
+        }
       }
     }
   }
@@ -200,7 +224,7 @@ __device__ __forceinline__ void rlat_generators(uint32_t seed, uint32_t k, uint3
 // shared memory ([pixel][R][s]; spp / R samples share each word), then writes
 // the batch's rows as consecutive 16-byte chunks, each chunk one sample and
 // four consecutive dimensions: one 128-bit shared load, four multiplies.
-template <int KIND>
+template <int KIND, bool V4>
 __global__ void __launch_bounds__(kThreads) random_lattice_points_fast(RandomPointsArgs a) {
   extern __shared__ __align__(16) uint32_t rsm[];
   uint32_t* jump = rsm;  // LFSR: the 32-step jump table (the walk below needs no other level)
@@ -213,7 +237,7 @@ __global__ void __launch_bounds__(kThreads) random_lattice_points_fast(RandomPoi
     __syncthreads();
   }
   const uint32_t s = a.s, R = 1u << a.r_log2, Rs = R * s, stride = s + 4u;
-  const uint64_t mag_s = ~0ull / s + 1;  // s >= 4
+  const uint64_t mag_s = s > 1 ? ~0ull / s + 1 : 0;
   const uint64_t mag_spp = a.spp > 1 ? ~0ull / a.spp + 1 : 0;
   const uint64_t n_batches = (a.n_pixels + a.batch_pixels - 1) / a.batch_pixels;
   for (uint64_t b = blockIdx.x; b < n_batches; b += gridDim.x) {
@@ -229,7 +253,7 @@ __global__ void __launch_bounds__(kThreads) random_lattice_points_fast(RandomPoi
     __syncthreads();
     if (KIND == QMC_RLAT_HASH) {  // every component independently
       for (uint32_t idx = threadIdx.x; idx < npx * Rs; idx += blockDim.x) {
-        const uint32_t row = (uint32_t)__umul64hi(idx, mag_s);  // (pixel, instance)
+        const uint32_t row = s > 1 ? (uint32_t)__umul64hi(idx, mag_s) : idx;  // (pixel, instance)
         const uint32_t j = idx - row * s, q = row >> a.r_log2;
         gvec[row * stride + j] = rlat_hash(a.seed, row & (R - 1u), j, pxy[2 * q], pxy[2 * q + 1]) | 1u;
       }
@@ -244,18 +268,38 @@ __global__ void __launch_bounds__(kThreads) random_lattice_points_fast(RandomPoi
       }
     }
     __syncthreads();
-    const uint32_t chunks = npx * a.spp * (s >> 2);
-    const uint64_t off0 = first * a.spp * s;
+    const uint32_t total = npx * a.spp * s;  // the batch's elements
+    const uint32_t chunks = (total + 3u) >> 2;
+    const uint64_t off0 = first * a.spp * s;  // a multiple of 4 (16-byte chunks)
     for (uint32_t c = threadIdx.x; c < chunks; c += blockDim.x) {
       const uint32_t e = 4u * c;  // element within the batch, < 2^31
-      const uint32_t row = (uint32_t)__umul64hi(e, mag_s);
-      const uint32_t j = e - row * s;
-      const uint32_t pl = a.spp > 1 ? (uint32_t)__umul64hi(row, mag_spp) : row;
-      const uint32_t t = row - pl * a.spp;
-      const uint4 g = *reinterpret_cast<const uint4*>(gvec + (pl * R + (t & (R - 1u))) * stride + j);
-      const uint32_t phi = __brev(~(t >> a.r_log2));  // phi_2(2^32 - 1 - i), Alg. 4
-      const uint32_t v[4] = {phi * g.x, phi * g.y, phi * g.z, phi * g.w};
-      store4(a.out_u32, a.out_f32, off0 + e, v);
+      uint32_t v[4];
+      if (V4) {  // four dimensions of one row: one 128-bit shared load
+        const uint32_t row = (uint32_t)__umul64hi(e, mag_s);
+        const uint32_t j = e - row * s;
+        const uint32_t pl = a.spp > 1 ? (uint32_t)__umul64hi(row, mag_spp) : row;
+        const uint32_t t = row - pl * a.spp;
+        const uint4 g = *reinterpret_cast<const uint4*>(gvec + (pl * R + (t & (R - 1u))) * stride + j);
+        const uint32_t phi = __brev(~(t >> a.r_log2));  // phi_2(2^32 - 1 - i), Alg. 4
+        v[0] = phi * g.x, v[1] = phi * g.y, v[2] = phi * g.z, v[3] = phi * g.w;
+      } else {  // each element its own row
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t et = e + q < total ? e + q : total - 1u;  // past the end: any valid word
+          const uint32_t row = s > 1 ? (uint32_t)__umul64hi(et, mag_s) : et;
+          const uint32_t j = et - row * s;
+          const uint32_t pl = a.spp > 1 ? (uint32_t)__umul64hi(row, mag_spp) : row;
+          const uint32_t t = row - pl * a.spp;
+          v[q] = __brev(~(t >> a.r_log2)) * gvec[(pl * R + (t & (R - 1u))) * stride + j];
+        }
+      }
+      if (e + 4u <= total) {
+        store4(a.out_u32, a.out_f32, off0 + e, v);
+      } else {  // the batch's ragged end (s % 4 != 0)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (e + q < total) store1(a.out_u32, a.out_f32, off0 + e + q, v[q]);
+      }
     }
   }
 }
@@ -290,13 +334,20 @@ cudaError_t launch_random_lattice_points(const RandomPointsArgs& args, cudaStrea
   // batch: up to 48 KiB of generator words (at least one pixel), at most 256 pixels
   uint64_t pixels = (48u * 1024u / 4u) / Rrow;
   if (pixels > 256) pixels = 256;
+  if ((a.s & 3u) != 0) pixels &= ~3ull;  // batches of 4k pixels: every batch's first element offset
+                                         // first spp s is a multiple of 4, so 16-byte chunks stay aligned
+  const bool batched = pixels >= 1;
   if (pixels < 1) pixels = 1;
   a.batch_pixels = (uint32_t)pixels;
   const size_t smem =
       ((hash ? 0 : (size_t)kLfsrJumpWords) + ((2 * pixels + 3) & ~3ull) + pixels * Rrow) * sizeof(uint32_t);
-  if ((a.s & 3u) == 0 && pixels * a.spp * a.s <= (1ull << 31) && aligned16(a.out_u32) && aligned16(a.out_f32) &&
+  if (batched && pixels * a.spp * a.s <= (1ull << 31) && aligned16(a.out_u32) && aligned16(a.out_f32) &&
       smem <= dev.smem_per_block_optin) {
-    const auto kernel = hash ? random_lattice_points_fast<QMC_RLAT_HASH> : random_lattice_points_fast<QMC_RLAT_LFSR>;
+    const bool v4 = (a.s & 3u) == 0;
+    const auto kernel = hash ? (v4 ? random_lattice_points_fast<QMC_RLAT_HASH, true>
+                                   : random_lattice_points_fast<QMC_RLAT_HASH, false>)
+                             : (v4 ? random_lattice_points_fast<QMC_RLAT_LFSR, true>
+                                   : random_lattice_points_fast<QMC_RLAT_LFSR, false>);
     if (smem > 48 * 1024) {
       const cudaError_t ea = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (ea != cudaSuccess) return ea;
@@ -324,16 +375,16 @@ cudaError_t launch_random_lattice_points(const RandomPointsArgs& args, cudaStrea
 
 cudaError_t launch_pixel_lattice_points(const PixelPointsArgs& a, cudaStream_t stream) {
   const DeviceInfo& dev = device_info();
-  if ((a.s & 3u) == 0 && (uint64_t)32 * a.spp * a.s <= (1ull << 31) && aligned16(a.out_u32) &&
-      aligned16(a.out_f32)) {
+  if ((uint64_t)32 * a.spp * a.s <= (1ull << 31) && aligned16(a.out_u32) && aligned16(a.out_f32)) {
+    const auto kernel = (a.s & 3u) == 0 ? pixel_lattice_points_fast<true> : pixel_lattice_points_fast<false>;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pixel_lattice_points_fast, kThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0);
     if (e != cudaSuccess) return e;
     uint64_t blocks = (uint64_t)dev.sm_count * (per_sm < 1 ? 1 : per_sm);
     const uint64_t need = (((a.n_pixels + 31) >> 5) + kThreads / 32 - 1) / (kThreads / 32);
     if (need < blocks) blocks = need;
     if (blocks < 1) blocks = 1;
-    pixel_lattice_points_fast<<<(unsigned)blocks, kThreads, 0, stream>>>(a);
+    kernel<<<(unsigned)blocks, kThreads, 0, stream>>>(a);
     return cudaGetLastError();
   }
   uint64_t blocks = (a.n_pixels * a.spp + kThreads - 1) / kThreads;

@@ -21,7 +21,11 @@ def B():
                                                       (1920, 1080, 2, 16, 1920 * 1080 - 300, 300),
                                                       # coalesced path (s % 4 == 0): ragged batches, spp = 1
                                                       (37, 23, 1, 4, 5, 37 * 23 - 5), (100, 70, 16, 32, 1234, 3001),
-                                                      (256, 256, 3, 8, 0, 65536), (1920, 1080, 4, 12, 777, 4099)])
+                                                      (256, 256, 3, 8, 0, 65536), (1920, 1080, 4, 12, 777, 4099),
+                                                      # coalesced path, s % 4 != 0: chunks straddle rows and
+                                                      # pixels, ragged batch ends
+                                                      (1920, 1080, 16, 2, 12345, 1000), (333, 77, 7, 1, 3, 333 * 70),
+                                                      (64, 48, 9, 5, 1, 64 * 48 - 1), (128, 128, 1, 7, 0, 5000)])
 def test_pixel_lattice_points_bit_exact(B, oracle, width, height, spp, s, begin, n):
     g = inputs.lattice_generator(s, seed=13)
     u = torch.empty((n * spp, s), dtype=torch.int32, device="cuda")

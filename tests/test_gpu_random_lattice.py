@@ -23,8 +23,11 @@ def B():
 @pytest.mark.parametrize("kind", [0, 1])
 @pytest.mark.parametrize("R", [1, 4, 16])
 @pytest.mark.parametrize("width,height,spp,s,begin,n", [
-    (37, 23, 17, 6, 0, 37 * 23),          # generic path (s % 4 != 0)
+    (37, 23, 17, 6, 0, 37 * 23),          # s % 4 != 0: chunks straddle rows and pixels
     (64, 64, 5, 3, 100, 700),
+    (1920, 1080, 16, 2, 12345, 1000),     # 2-D per-pixel sampling
+    (333, 77, 7, 1, 3, 2000),
+    (64, 48, 9, 5, 1, 64 * 48 - 1),
     (100, 70, 16, 32, 1234, 3001),        # coalesced path, ragged pixel batches
     (37, 23, 1, 4, 5, 37 * 23 - 5),       # spp = 1
     (1920, 1080, 4, 12, 1920 * 1080 - 4099, 4099),
