@@ -280,6 +280,7 @@ def extras_cpu_baselines(names) -> dict:
             "sobol64_partition_p5_of_8": (n, lambda: oracle.sobol_points_partitioned(W, 3, 5, 1 << 37, n, nested, sd,
                                                                                      threads=threads)),
             "lattice_shifted": (nb, lambda: oracle.lattice_points(g, sh, 0, nb, threads=threads)),
+            "lattice_shifted_from_index_1": (nb, lambda: oracle.lattice_points(g, sh, 1, nb, threads=threads)),
             "halton_faure": (nl, lambda: oracle.halton_points(s, 0, nl, oracle.HALTON_FAURE, threads=threads)),
             "halton_faure_partition_p5_of_8": (n, lambda: oracle.halton_points_partitioned(
                 s, 3, 5, 1 << 30, n, oracle.HALTON_FAURE, threads=threads)),
@@ -530,6 +531,7 @@ def bench_points(dev, steps, warmup, small, sm_mhz):
     u32 + fp32, 8 B written per coordinate; 2^20 rows when small): the 32-bit
     Sobol' headline kernel again, the same from index 1 (off the fast path's
     group grid: the walking kernel), Sobol' with 64-bit indices at 2^40 (Alg. 3),
+    the shifted rank-1 lattice from index 1 (the flat-chunk kernel),
     one element of a partitioned Sobol' sequence (Sec. 2.5.1), the shifted
     rank-1 lattice, Halton (Faure; whole, and one element of the sequence
     partitioned by its base-2 dimension), the pixel-shifted lattice and the per-pixel
@@ -556,6 +558,7 @@ def bench_points(dev, steps, warmup, small, sm_mhz):
         "sobol64_partition_p5_of_8": lambda: B.qmc_sobol_points_partitioned(W, 64, s, 3, 5, 1 << 37, n,
                                                                             B.SCRAMBLE_NESTED, sd, u, f),
         "lattice_shifted": lambda: B.qmc_lattice_points(g, sh, s, 0, n, 0, u, f),
+        "lattice_shifted_from_index_1": lambda: B.qmc_lattice_points(g, sh, s, 1, n, 0, u, f),
         "halton_faure": lambda: B.qmc_halton_points(s, B.HALTON_FAURE, None, 0, n, u, f),
         "halton_faure_partition_p5_of_8": lambda: B.qmc_halton_points_partitioned(s, B.HALTON_FAURE, None, 3, 5,
                                                                                   1 << 30, n, u, f),
@@ -573,6 +576,7 @@ def bench_points(dev, steps, warmup, small, sm_mhz):
     inst_keys = {"sobol32_nested": ("sobol_points_fast<1,2>", ["sobol_points.cu"]),
                  "sobol32_nested_from_index_1": ("sobol_points_walk<2>", ["sobol_points.cu"]),
                  "lattice_shifted": ("lattice_points_fast<1,0,1>", ["lattice_points.cu"]),
+                 "lattice_shifted_from_index_1": ("lattice_points_flat<0>", ["lattice_points.cu"]),
                  "halton_faure": ("halton_points_kernel<faure>", ["halton_points.cu", "halton_points.h"]),
                  "pixel_lattice_16spp": ("pixel_lattice_points_fast", ["lattice_points.cu"]),
                  "random_lattice_hash_x4_16spp": ("random_lattice_points_fast<hash>", ["lattice_points.cu"]),

@@ -76,6 +76,50 @@ __global__ void __launch_bounds__(kThreads) lattice_points_fast(PointsArgs a) {
   if (TMA) stager.finish(lane);
 }
 
+// K2 for the shapes the fast path's groups do not fit (s / gcd(s, 128) > 4, or an
+// index_begin off the group grid): a warp takes batches of kFlatRows consecutive
+// rows and writes them as 16-byte chunks of the flat [row][s] layout, each element
+// of a chunk finding its own row and dimension (one exact multiply-high division).
+// kFlatRows is a multiple of 4, so every batch starts on a 16-byte boundary.
+constexpr uint32_t kFlatRows = 512;
+
+template <bool BACKWARD>
+__global__ void __launch_bounds__(kThreads) lattice_points_flat(PointsArgs a) {
+  const uint32_t lane = threadIdx.x & 31u, s = a.s;
+  const uint64_t mag_s = s > 1 ? ~0ull / s + 1 : 0;  // x / s = umulhi(x, .) for x < 2^32, s > 1
+  const uint64_t n_batches = (a.count + kFlatRows - 1) / kFlatRows;
+  uint64_t b0, b1;
+  warp_range(n_batches, b0, b1);
+  for (uint64_t b = b0; b < b1; ++b) {
+    const uint64_t row0 = b * kFlatRows;
+    const uint64_t left = a.count - row0;
+    const uint32_t rows = left < kFlatRows ? (uint32_t)left : kFlatRows;
+    const uint32_t total = rows * s;  // <= 2^19 elements (s <= 1024)
+    const uint64_t off0 = row0 * s;   // a multiple of 4
+    const uint32_t k0 = (uint32_t)a.index_begin + (uint32_t)row0;  // index of the batch's first row, mod 2^32
+    for (uint32_t e = 4u * lane; e < total; e += 128u) {
+      uint32_t v[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const uint32_t et = e + t < total ? e + t : total - 1u;
+        const uint32_t r = s > 1 ? (uint32_t)__umul64hi(et, mag_s) : et;
+        const uint32_t j = et - r * s;
+        const uint32_t g = __ldg(a.matrices + j) | 1u;
+        const uint32_t sh = a.seeds ? __ldg(a.seeds + j) : 0u;
+        const uint32_t phi = __brev(k0 + r);
+        v[t] = BACKWARD ? sh - g - phi * g : phi * g + sh;  // phi_2(~k) = ~phi_2(k)
+      }
+      if (e + 4u <= total) {
+        store4(a.out_u32, a.out_f32, off0 + e, v);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (e + t < total) store1(a.out_u32, a.out_f32, off0 + e + t, v[t]);
+      }
+    }
+  }
+}
+
 template <bool BACKWARD>
 __global__ void __launch_bounds__(kThreads) lattice_points_generic(PointsArgs a) {
   const uint64_t total = a.count * a.s;
@@ -402,6 +446,11 @@ cudaError_t launch_lattice_points(PointsArgs a, cudaStream_t stream) {
   const bool fast = K != 0 && (a.index_begin & ((1ull << a.q_log2) - 1u)) == 0 && aligned16(a.out_u32) &&
                     aligned16(a.out_f32);
   if (!fast) {
+    if (aligned16(a.out_u32) && aligned16(a.out_f32) && a.s <= 1024) {
+      const uint64_t batches = (a.count + kFlatRows - 1) / kFlatRows;
+      return backward ? launch_persistent(lattice_points_flat<true>, batches, 0, stream, a)
+                      : launch_persistent(lattice_points_flat<false>, batches, 0, stream, a);
+    }
     return backward ? launch_grid_stride(lattice_points_generic<true>, a.count * a.s, stream, a)
                     : launch_grid_stride(lattice_points_generic<false>, a.count * a.s, stream, a);
   }

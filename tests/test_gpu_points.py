@@ -106,8 +106,11 @@ def test_config2_full_size_sampled(B, oracle):
 
 
 @pytest.mark.parametrize("backward", [False, True])
-@pytest.mark.parametrize("s", [1, 2, 3, 5, 16, 17, 32])
+@pytest.mark.parametrize("s", [1, 2, 3, 5, 7, 16, 17, 32, 100, 1024])
 def test_lattice_points_bit_exact(B, oracle, s, backward):
+    """The grouped fast path (s / gcd(s, 128) <= 4, index_begin on its grid) and the flat-chunk
+    path (5, 7, 17, 100, 1024 dimensions, or begin 7): batches of 512 rows, chunks straddling
+    rows, a ragged last batch, indices up to 2^32 - 1."""
     g = inputs.lattice_generator(s)
     sh = inputs.lattice_shift(s)
     for begin, count, shift in ((0, 4096 * 2 + 13, sh), (7, 3001, None), ((1 << 32) - 2000, 2000, sh)):
