@@ -139,9 +139,10 @@ __global__ void __launch_bounds__(kThreads) lattice_points_generic(PointsArgs a)
 // A warp takes batches of 32 consecutive pixels: lane l computes the shift of pixel
 // l of the batch once (Hilbert position, then phi_3), and the batch's 32 spp rows
 // are written as consecutive 16-byte chunks, each element's pixel shift fetched from
-// its lane with a shuffle.  V4 (s % 4 == 0): a chunk holds four dimensions of one
-// row; otherwise each of its four elements finds its own row, dimension and pixel.
-template <bool V4>
+// its lane with a shuffle.  LAYOUT 1 (s % 4 == 0): a chunk holds four dimensions of
+// one row; LAYOUT 2 (s = 1, 2): a chunk holds 4 / s whole rows; LAYOUT 0: each of its
+// four elements finds its own row, dimension and pixel.
+template <int LAYOUT>
 __global__ void __launch_bounds__(kThreads) pixel_lattice_points_fast(PixelPointsArgs a) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t n_batches = (a.n_pixels + 31) >> 5;
@@ -167,7 +168,25 @@ __global__ void __launch_bounds__(kThreads) pixel_lattice_points_fast(PixelPoint
       const uint32_t c = c0 + lane;
       const uint32_t e = 4u * c;  // element within the batch, < 2^32
       uint32_t v[4];
-      if (V4) {
+      if (LAYOUT == 2) {
+        const uint32_t rpc = 4u / a.s;  // rows per chunk
+        const uint32_t g0 = __ldg(a.g) | 1u, g1 = a.s == 2 ? (__ldg(a.g + 1) | 1u) : 0u;
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q) {
+          if (q < rpc) {
+            const uint32_t row = (a.s == 2 ? e >> 1 : e) + q;
+            const uint32_t pl = a.spp > 1 ? (uint32_t)__umul64hi(row, mag_spp) : row;
+            const uint32_t smp = row - pl * a.spp;
+            const uint32_t base = __brev(smp) + __shfl_sync(0xffffffffu, sh, pl & 31u);
+            if (a.s == 2) {
+              v[2 * q] = base * g0;
+              v[2 * q + 1] = base * g1;
+            } else {
+              v[q] = base * g0;
+            }
+          }
+        }
+      } else if (LAYOUT == 1) {
         const uint32_t row = (uint32_t)__umul64hi(e, mag_s);
         const uint32_t j = e - row * a.s;
         const uint32_t pl = a.spp > 1 ? (uint32_t)__umul64hi(row, mag_spp) : row;
@@ -268,7 +287,7 @@ __device__ __forceinline__ void rlat_generators(uint32_t seed, uint32_t k, uint3
 // shared memory ([pixel][R][s]; spp / R samples share each word), then writes
 // the batch's rows as consecutive 16-byte chunks, each chunk one sample and
 // four consecutive dimensions: one 128-bit shared load, four multiplies.
-template <int KIND, bool V4>
+template <int KIND, int LAYOUT>  // LAYOUT as in pixel_lattice_points_fast
 __global__ void __launch_bounds__(kThreads) random_lattice_points_fast(RandomPointsArgs a) {
   extern __shared__ __align__(16) uint32_t rsm[];
   uint32_t* jump = rsm;  // LFSR: the 32-step jump table (the walk below needs no other level)
@@ -318,7 +337,26 @@ __global__ void __launch_bounds__(kThreads) random_lattice_points_fast(RandomPoi
     for (uint32_t c = threadIdx.x; c < chunks; c += blockDim.x) {
       const uint32_t e = 4u * c;  // element within the batch, < 2^31
       uint32_t v[4];
-      if (V4) {  // four dimensions of one row: one 128-bit shared load
+      if (LAYOUT == 2) {  // 4 / s whole rows: the index math once per row
+        const uint32_t rpc = 4u / s;
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q) {
+          if (q < rpc) {
+            const uint32_t row0 = s == 2 ? e >> 1 : e;
+            const uint32_t row = row0 + q < total / s ? row0 + q : total / s - 1u;  // past the end: any row
+            const uint32_t pl = a.spp > 1 ? (uint32_t)__umul64hi(row, mag_spp) : row;
+            const uint32_t t = row - pl * a.spp;
+            const uint32_t phi = __brev(~(t >> a.r_log2));
+            const uint32_t* gw = gvec + (pl * R + (t & (R - 1u))) * stride;
+            if (s == 2) {
+              v[2 * q] = phi * gw[0];
+              v[2 * q + 1] = phi * gw[1];
+            } else {
+              v[q] = phi * gw[0];
+            }
+          }
+        }
+      } else if (LAYOUT == 1) {  // four dimensions of one row: one 128-bit shared load
         const uint32_t row = (uint32_t)__umul64hi(e, mag_s);
         const uint32_t j = e - row * s;
         const uint32_t pl = a.spp > 1 ? (uint32_t)__umul64hi(row, mag_spp) : row;
@@ -387,11 +425,13 @@ cudaError_t launch_random_lattice_points(const RandomPointsArgs& args, cudaStrea
       ((hash ? 0 : (size_t)kLfsrJumpWords) + ((2 * pixels + 3) & ~3ull) + pixels * Rrow) * sizeof(uint32_t);
   if (batched && pixels * a.spp * a.s <= (1ull << 31) && aligned16(a.out_u32) && aligned16(a.out_f32) &&
       smem <= dev.smem_per_block_optin) {
-    const bool v4 = (a.s & 3u) == 0;
-    const auto kernel = hash ? (v4 ? random_lattice_points_fast<QMC_RLAT_HASH, true>
-                                   : random_lattice_points_fast<QMC_RLAT_HASH, false>)
-                             : (v4 ? random_lattice_points_fast<QMC_RLAT_LFSR, true>
-                                   : random_lattice_points_fast<QMC_RLAT_LFSR, false>);
+    const int layout = (a.s & 3u) == 0 ? 1 : a.s <= 2 ? 2 : 0;
+    const auto kernel = hash ? (layout == 1   ? random_lattice_points_fast<QMC_RLAT_HASH, 1>
+                                : layout == 2 ? random_lattice_points_fast<QMC_RLAT_HASH, 2>
+                                              : random_lattice_points_fast<QMC_RLAT_HASH, 0>)
+                             : (layout == 1   ? random_lattice_points_fast<QMC_RLAT_LFSR, 1>
+                                : layout == 2 ? random_lattice_points_fast<QMC_RLAT_LFSR, 2>
+                                              : random_lattice_points_fast<QMC_RLAT_LFSR, 0>);
     if (smem > 48 * 1024) {
       const cudaError_t ea = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (ea != cudaSuccess) return ea;
@@ -420,7 +460,9 @@ cudaError_t launch_random_lattice_points(const RandomPointsArgs& args, cudaStrea
 cudaError_t launch_pixel_lattice_points(const PixelPointsArgs& a, cudaStream_t stream) {
   const DeviceInfo& dev = device_info();
   if ((uint64_t)32 * a.spp * a.s <= (1ull << 31) && aligned16(a.out_u32) && aligned16(a.out_f32)) {
-    const auto kernel = (a.s & 3u) == 0 ? pixel_lattice_points_fast<true> : pixel_lattice_points_fast<false>;
+    const auto kernel = (a.s & 3u) == 0 ? pixel_lattice_points_fast<1>
+                        : a.s <= 2       ? pixel_lattice_points_fast<2>
+                                         : pixel_lattice_points_fast<0>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0);
     if (e != cudaSuccess) return e;
