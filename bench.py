@@ -153,6 +153,28 @@ def integrate_sources(key: str) -> list[str]:
     unit = "integrate_gaussmix.cu" if "gaussmix" in key else "integrate_genz.cu"
     return [unit] + INTEGRATE_COMMON
 KERNEL_SOURCES = {"sobol_points_fast<1,2>": POINTS_SOURCES}
+POINTS_COMMON = ["points_common.cuh", "qmc_device.cuh", "qmc_internal.h"]
+# the points workloads' kernels: (profile key, the kernel's own sources besides POINTS_COMMON)
+POINTS_KERNELS = {"sobol32_nested": ("sobol_points_fast<1,2>", ["sobol_points.cu"]),
+                  "sobol32_nested_from_index_1": ("sobol_points_walk<2>", ["sobol_points.cu"]),
+                  "lattice_shifted": ("lattice_points_fast<1,0,1>", ["lattice_points.cu"]),
+                  "lattice_shifted_from_index_1": ("lattice_points_flat<0>", ["lattice_points.cu"]),
+                  "halton_faure": ("halton_points_kernel<faure>", ["halton_points.cu", "halton_points.h"]),
+                  "pixel_lattice_16spp": ("pixel_lattice_points_fast", ["lattice_points.cu"]),
+                  "random_lattice_hash_x4_16spp": ("random_lattice_points_fast<hash>", ["lattice_points.cu"]),
+                  "random_lattice_lfsr_x4_16spp": ("random_lattice_points_fast<lfsr>", ["lattice_points.cu"])}
+
+
+def profile_sources(fname: str, key: str) -> list[str]:
+    """The sources whose digest keys a committed profile figure."""
+    if fname == "traffic.txt":
+        return KERNEL_SOURCES[key]
+    if fname == "inst_per_sample.txt":
+        return integrate_sources(key)
+    for k, src in POINTS_KERNELS.values():
+        if k == key:
+            return src + POINTS_COMMON
+    raise KeyError(key)
 
 
 def _profile_value(fname: str, key: str, files):
@@ -572,15 +594,6 @@ def bench_points(dev, steps, warmup, small, sm_mhz):
                                                                             u, f),
     }
     # instruction counts per coordinate (ncu, profiles/inst_per_coord.txt) for the issue roofline
-    common = ["points_common.cuh", "qmc_device.cuh", "qmc_internal.h"]
-    inst_keys = {"sobol32_nested": ("sobol_points_fast<1,2>", ["sobol_points.cu"]),
-                 "sobol32_nested_from_index_1": ("sobol_points_walk<2>", ["sobol_points.cu"]),
-                 "lattice_shifted": ("lattice_points_fast<1,0,1>", ["lattice_points.cu"]),
-                 "lattice_shifted_from_index_1": ("lattice_points_flat<0>", ["lattice_points.cu"]),
-                 "halton_faure": ("halton_points_kernel<faure>", ["halton_points.cu", "halton_points.h"]),
-                 "pixel_lattice_16spp": ("pixel_lattice_points_fast", ["lattice_points.cu"]),
-                 "random_lattice_hash_x4_16spp": ("random_lattice_points_fast<hash>", ["lattice_points.cu"]),
-                 "random_lattice_lfsr_x4_16spp": ("random_lattice_points_fast<lfsr>", ["lattice_points.cu"])}
     clock = sm_mhz or measured_peaks()["sm_max_mhz"]
     issue_peak = SMS * SCHEDULERS_PER_SM * WARP * clock * 1e6  # thread-instructions/s
     res = {"rows": n, "s": s, "bytes_per_launch": n * s * 8,
@@ -589,9 +602,9 @@ def bench_points(dev, steps, warmup, small, sm_mhz):
         ms = statistics.median(timed(fn, steps, warmup, stream))
         gbs = n * s * 8 / (ms * 1e-3) / 1e9
         entry = {"ms": ms, "gdims_s": n * s / (ms * 1e-3) / 1e9, "gb_s": gbs, "frac_hbm": gbs / peak}
-        if name in inst_keys:
-            key, src = inst_keys[name]
-            ipc = _profile_value("inst_per_coord.txt", key, src + common)
+        if name in POINTS_KERNELS:
+            key = POINTS_KERNELS[name][0]
+            ipc = _profile_value("inst_per_coord.txt", key, profile_sources("inst_per_coord.txt", key))
             if ipc is not None:
                 entry["inst_per_coord"] = ipc
                 entry["frac_issue"] = ipc * n * s / (ms * 1e-3) / issue_peak

@@ -37,3 +37,21 @@ def test_cpu_baselines_sit_beside_their_gpu_figures():
     assert extras["lattice"]["oscillatory"]["cpu_baseline"] == {"value": 0.2}
     assert "product_peak" not in extras["lattice"]  # no GPU figure to sit beside
     assert extras["points"]["halton_faure"]["cpu_baseline"] == {"value": 0.4}
+
+
+def test_committed_profile_figures_match_the_sources():
+    """Every figure in the digest-keyed profile tables was taken on the committed sources: a
+    kernel edit without a re-capture shows up here (bench.py would report it as null)."""
+    import os
+
+    import bench
+    from paper_2307_15584_gb300.build import source_digest
+
+    for fname in ("traffic.txt", "inst_per_coord.txt", "inst_per_sample.txt"):
+        path = os.path.join(bench.ROOT, "profiles", fname)
+        for line in open(path):
+            parts = line.split()
+            if len(parts) != 3 or line.startswith("#"):
+                continue
+            key, digest, _ = parts
+            assert source_digest(bench.profile_sources(fname, key)) == digest, (fname, key)
