@@ -155,3 +155,18 @@ def test_halton_partition_fullsize(B, oracle, out):
     torch.cuda.synchronize()
     _check_rows(B, oracle, u, f, _rows(9),
                 lambda r: oracle.halton_points_partitioned(S, q, p, j0 + r, 1, oracle.HALTON_FAURE, threads=1)[0])
+
+
+def test_lattice_flat_fullsize(B, oracle, out):
+    """The bench's flat-chunk lattice configuration: the shifted rank-1 lattice, s = 32, from
+    index 1 (off the grouped kernel's grid), 2^24 rows."""
+    u, f = out
+    g, sh = inputs.lattice_generator(S), inputs.lattice_shift(S)
+    B.qmc_lattice_points(B.u32_tensor(g), B.u32_tensor(sh), S, 1, N, 0, u, f)
+    torch.cuda.synchronize()
+    _check_rows(B, oracle, u, f, _rows(10),
+                lambda r: np.array([oracle.lib().qo_lattice_u32(1 + r, int(g[j]), int(sh[j]), 0) for j in range(S)],
+                                   np.uint32))
+    # indices [2^20, 2^21) sit at rows 2^20 - 1 .. 2^21 - 2 and stratify every dimension
+    _stratified_top_bits((u[(1 << 20) - 1: (1 << 21) - 1] - torch.from_numpy(sh.view(np.int32)).cuda()[None, :])
+                         .contiguous(), (0, 13, 31), 20)
