@@ -170,3 +170,22 @@ def test_lattice_flat_fullsize(B, oracle, out):
     # indices [2^20, 2^21) sit at rows 2^20 - 1 .. 2^21 - 2 and stratify every dimension
     _stratified_top_bits((u[(1 << 20) - 1: (1 << 21) - 1] - torch.from_numpy(sh.view(np.int32)).cuda()[None, :])
                          .contiguous(), (0, 13, 31), 20)
+
+
+def test_sobol_wide_fullsize(B, oracle, out):
+    """The bench's 64-bit-index configuration (Alg. 3): s = 32 of the 64-column matrices from
+    index 2^40, nested scramble, 2^24 rows."""
+    u, f = out
+    W = B.qmc_sobol_matrices_wide(S + 1, 64, inputs.sobol_raw_init(S + 1))
+    seeds = inputs.scramble_seeds(S)
+    B.qmc_sobol_points_wide(B.u32_tensor(W), 64, S, 1 << 40, N, B.SCRAMBLE_NESTED, B.u32_tensor(seeds), u, f)
+    torch.cuda.synchronize()
+    Ws = np.ascontiguousarray(W[:S])
+
+    def ref(r):
+        row, _ = oracle.sobol_points_wide(Ws, (1 << 40) + r, 1, oracle.SCRAMBLE_NESTED, seeds, threads=1)
+        return row[0]
+
+    _check_rows(B, oracle, u, f, _rows(11, 300), ref)
+    # an aligned block of 2^20 points beyond 2^40: dimension 0 (the identity) stratified fully
+    _stratified_top_bits(u, (0,), 20)
