@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(kThreads) lattice_points_flat(PointsArgs a) {
   }
 }
 
+// K2 fallback for outputs that are not 16-byte aligned: one element per thread.
 template <bool BACKWARD>
 __global__ void __launch_bounds__(kThreads) lattice_points_generic(PointsArgs a) {
   const uint64_t total = a.count * a.s;
@@ -222,8 +223,9 @@ __global__ void __launch_bounds__(kThreads) pixel_lattice_points_fast(PixelPoint
 }
 
 
-// Pixel-shifted rank-1 lattice (Sec. 3): one thread per (pixel, sample) row;
-// row r holds sample r % spp of pixel pixel_begin + r / spp.
+// Pixel-shifted rank-1 lattice (Sec. 3), fallback for outputs that are not 16-byte aligned
+// (or 32 spp s beyond 2^31): one thread per (pixel, sample) row; row r holds sample r % spp
+// of pixel pixel_begin + r / spp.
 __global__ void __launch_bounds__(kThreads) pixel_lattice_points_kernel(PixelPointsArgs a) {
   const uint64_t rows = a.n_pixels * a.spp;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -386,7 +388,8 @@ __global__ void __launch_bounds__(kThreads) random_lattice_points_fast(RandomPoi
   }
 }
 
-// Generic path: one element per thread.
+// Fallback for outputs that are not 16-byte aligned or batches beyond shared memory:
+// one element per thread.
 template <int KIND>
 __global__ void __launch_bounds__(kThreads) random_lattice_points_generic(RandomPointsArgs a) {
   __shared__ uint32_t jump[KIND == QMC_RLAT_LFSR ? kJumpLevels * kLfsrJumpWords : 1];
