@@ -308,7 +308,10 @@ def make_problem(source, integrand, s, randomize=0, matrices=None, g=None, seeds
                  seeds_per_integral=False, chunk=0, block=0, max_count=0, with_gradient=False,
                  image_width=0, index_bits=0, partition_log2=0) -> qmc_problem:
     """A qmc_problem holding device pointers of the given tensors; the problem keeps
-    references to them so their memory stays valid while it is alive."""
+    references to them so their memory stays valid while it is alive.  Fields as in
+    include/qmc.h: for SOURCE_SOBOL, index_bits is the matrices' columns per dimension
+    (0 = 32) and partition_log2 = q makes integral p integrate element p mod 2^q of the
+    sequence partitioned by the matrices' dimension 0 (which then hold s + 1 dimensions)."""
     p = qmc_problem(source, integrand, s, randomize, _dev(matrices), _dev(g), _dev(seeds),
                     int(bool(seeds_per_integral)), chunk, block, max_count, int(bool(with_gradient)), image_width,
                     index_bits, partition_log2)
