@@ -15,6 +15,16 @@
  *     qmc_read_device_error() returns.
  *   - Invalid arguments are rejected before anything is enqueued.  No C++
  *     exception crosses this boundary.
+ *   - QMC_ERR_CUDA: qmc_last_cuda_error() gives the CUDA runtime's error code
+ *     behind the most recent QMC_ERR_CUDA returned on the calling thread.
+ *   - Fault injection (for tests of a caller's error handling, host side
+ *     only): with the environment variable QMC_FAULT_INJECT=launch, every
+ *     entry point that would enqueue GPU work validates its arguments as usual
+ *     and then returns QMC_ERR_CUDA without any CUDA call;
+ *     qmc_last_cuda_error() then reports QMC_INJECTED_FAULT.  The variable is
+ *     read on every call.
+ *   - NVTX: every entry point that enqueues GPU work opens an NVTX range
+ *     named after it (domain "qmc"), visible to Nsight tools.
  *   - Point layouts are row-major [count][s]: row r holds point index_begin + r.
  *   - Indices are 32-bit unless an entry point says otherwise: index_begin +
  *     count must not exceed 2^32 (Sec. 2.5 warns that indices wrapping around
@@ -49,14 +59,18 @@ typedef enum qmc_status {
     QMC_ERR_CUDA = 4,        /* the CUDA runtime reported an error at launch */
     QMC_ERR_TIMEOUT = 5,     /* reserved: a bounded device wait gave up */
     QMC_ERR_UNSUPPORTED = 6, /* a valid combination this build does not implement */
-    QMC_ERR_WORKSPACE = 7    /* workspace missing, misaligned or too small */
+    QMC_ERR_WORKSPACE = 7,   /* workspace missing, misaligned or too small */
+    QMC_ERR_IO = 8           /* a file could not be read or written (autotune cache) */
 } qmc_status;
 
 /* Randomisation of Sobol' points, kept in integers (Sec. 2.1, Sec. 2.3). */
 typedef enum qmc_scramble {
     QMC_SCRAMBLE_NONE = 0,   /* plain Eq. (ts) */
     QMC_SCRAMBLE_XOR = 1,    /* random digital shift: y ^ seed (Sec. 2.3) */
-    QMC_SCRAMBLE_NESTED = 2  /* hash-based nested (Owen-type) scramble, per-dimension seed */
+    QMC_SCRAMBLE_NESTED = 2, /* hash-based nested (Owen-type) scramble, per-dimension seed */
+    QMC_SCRAMBLE_NESTED_XOR = 3 /* the digital shift y ^ seed (Sec. 2.3), then the nested
+                                   scramble keyed by the same seed (Sec. 2.1): each dimension's
+                                   one seed word selects both */
 } qmc_scramble;
 
 /* Flags of rank-1 lattice points. */
@@ -81,7 +95,8 @@ typedef enum qmc_source {
 /* Generator vectors of the random rank-1 lattices (Sec. 2.4.2). */
 typedef enum qmc_rlat_kind {
     QMC_RLAT_HASH = 0,  /* g_j = hash_value(j, pixel, instance) | 1 (Alg. 4) */
-    QMC_RLAT_LFSR = 1   /* g_j = 2 xi_j + 1, xi_j the LFSR state after j steps from a per-pixel seed */
+    QMC_RLAT_LFSR = 1   /* g_j = 2 xi_j + 1, xi_j = the per-pixel seed state advanced by 32 j
+                           LFSR steps (one 32-bit number per 32 register steps) */
 } qmc_rlat_kind;
 
 /* Integrands with closed-form integrals (Sec. 2.6 recommends such test
@@ -157,6 +172,15 @@ typedef struct qmc_problem {
 
 /* ABI revision of this header (bumped on any incompatible change). */
 QMC_API uint32_t qmc_abi_version(void);
+
+/* The value qmc_last_cuda_error() reports for a fault injected by
+ * QMC_FAULT_INJECT (no CUDA runtime error code is negative). */
+#define QMC_INJECTED_FAULT (-1)
+
+/* The cudaError_t code behind the most recent QMC_ERR_CUDA returned on the
+ * calling thread (0 when there was none; QMC_INJECTED_FAULT for an injected
+ * fault).  Thread-local; later successful calls do not reset it. */
+QMC_API int qmc_last_cuda_error(void);
 
 /* Human-readable name of a status code (static storage). */
 QMC_API const char* qmc_status_string(qmc_status status);
@@ -453,6 +477,35 @@ QMC_API qmc_status qmc_tune_integrate(const qmc_problem* p, uint32_t n_integrals
 QMC_API qmc_status qmc_tune_clear(void);
 
 /*
+ * Persistence of the tuner's records (host only; no GPU work).  A record is
+ * keyed by the problem class above and by the kind of device it was measured
+ * on (its name and SM count), so a file written on one GPU model is ignored on
+ * another.  The file is a JSON document:
+ *   {"qmc_autotune_cache": 1, "entries": [{"device": "...", "sms": 152,
+ *    "source": 0, "integrand": 3, "s": 6, "randomize": 2,
+ *    "seeds_per_integral": 1, "gradient": 1, "size_class": 20,
+ *    "chunk": 4096, "block": 256}, ...]}
+ * size_class = ceil(log2 n_integrals).  Entries with a missing field or an
+ * invalid split (chunk a power of two in [32, 8192], block a multiple of 32 up
+ * to 256) are skipped when loading.
+ *   qmc_tune_save   writes every record to `path` (replaced atomically);
+ *                   QMC_ERR_IO when the file cannot be written.
+ *   qmc_tune_load   adds the file's records (overriding records of the same
+ *                   class); *h_loaded (optional) = records taken; QMC_ERR_IO when
+ *                   the file cannot be read.
+ *   qmc_tune_lookup the recorded split for a problem class on the current
+ *                   device: h_out->chunk, ->block, or both 0 when none (ms = 0).
+ * Environment: QMC_AUTOTUNE_CACHE=path makes the library load that file once,
+ * before its first lookup or tuning run in the process (a missing file is an
+ * empty cache), and rewrite it after every qmc_tune_integrate; a file that
+ * cannot be written then leaves the result in memory only.
+ */
+QMC_API qmc_status qmc_tune_save(const char* path);
+QMC_API qmc_status qmc_tune_load(const char* path, uint32_t* h_loaded);
+QMC_API qmc_status qmc_tune_lookup(const qmc_problem* p, uint32_t n_integrals, uint32_t with_gradient,
+                                   qmc_tuning* h_out);
+
+/*
  * CUDA-graph capture of qmc_* calls (Sec. 2.5: many integrals in one launch
  * sequence replayed without host work).  qmc_graph_begin starts a thread-local
  * capture of `stream` (not the legacy NULL stream); every qmc_* call enqueued
@@ -479,16 +532,25 @@ QMC_API qmc_status qmc_graph_destroy(qmc_graph_t graph);
  * cudaMalloc's implicit synchronisation, or a process whose memory budget is
  * fixed at start-up.  It takes the same inputs and output as qmc_integrate but
  * no workspace: the scratch is a fixed device array of
- * QMC_STATIC_WORKSPACE_BYTES inside the library.  It allocates nothing and calls
- * no allocating routine.
+ * QMC_STATIC_WORKSPACE_BYTES inside the library.  It calls no cudaMalloc, no
+ * cudaFree and no allocating library routine.
+ *   Where the array lives: the CUDA runtime places it on a device when the
+ *   library's device code is loaded there, which with lazy module loading (the
+ *   default) happens at the first call on that device.  That first call may
+ *   therefore take device memory and synchronise like a module load, and can
+ *   fail with QMC_ERR_CUDA when the host application already holds all GPU
+ *   memory.  Make it at start-up, before memory is committed elsewhere and
+ *   before any stream capture: a call with n_integrals = 0 and the problem you
+ *   will use places the array, looks up its address and returns QMC_OK
+ *   without enqueueing work (d_counts, d_theta and d_estimate may then be
+ *   NULL).  Every later call on that device reuses it.
  *   p->max_count must bound every count; the call is rejected with
  *   QMC_ERR_WORKSPACE when the worst case for n_integrals integrals of up to
  *   max_count samples (forward only) does not fit the array, and with
  *   QMC_ERR_INVALID_ARG when max_count is 0.  Counts above max_count that do not
  *   fit are caught on the device: the estimates become NaN.
  *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress, with that device current); make that first call
- *   before capturing any stream into a CUDA graph.
+ *   (cudaGetSymbolAddress, with that device current) and keeps it per device.
  *   Every call on a device shares the one array, and it keeps the previous
  *   call's contents; each call's first kernel resets the scheduler and error
  *   words, and every other region is written before it is read.  Calls whose

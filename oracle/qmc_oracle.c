@@ -51,7 +51,7 @@
 enum { QO_SOURCE_SOBOL = 0, QO_SOURCE_LATTICE = 1, QO_SOURCE_PIXEL_LATTICE = 2,
        QO_SOURCE_RANDOM_LATTICE = 3 };
 enum { QO_RLAT_HASH = 0, QO_RLAT_LFSR = 1 };
-enum { QO_SCRAMBLE_NONE = 0, QO_SCRAMBLE_XOR = 1, QO_SCRAMBLE_NESTED = 2 };
+enum { QO_SCRAMBLE_NONE = 0, QO_SCRAMBLE_XOR = 1, QO_SCRAMBLE_NESTED = 2, QO_SCRAMBLE_NESTED_XOR = 3 };
 enum {
     QO_F_BILINEAR2D = 0,
     QO_F_GENZ_PRODUCT_PEAK = 1,
@@ -295,10 +295,14 @@ QO_EXPORT uint32_t qo_nested_scramble(uint32_t y, uint32_t seed)
     return qo_bit_reverse((uint32_t)v);
 }
 
+/* The randomisations of a Sobol' coordinate: the random digital shift of
+ * Sec. 2.3, the nested scramble above, or the shift followed by the nested
+ * scramble, both selected by the dimension's one seed word. */
 static uint32_t randomise_sobol(uint32_t y, uint32_t mode, uint32_t seed)
 {
     if (mode == QO_SCRAMBLE_XOR) return y ^ seed;  /* Sec. 2.3: random digital shift */
     if (mode == QO_SCRAMBLE_NESTED) return qo_nested_scramble(y, seed);
+    if (mode == QO_SCRAMBLE_NESTED_XOR) return qo_nested_scramble(y ^ seed, seed);
     return y;
 }
 
@@ -749,6 +753,27 @@ QO_EXPORT int qo_integrate_one(uint32_t source, uint32_t integrand, uint32_t s,
             grad[k] = n ? (gsum[k].s + gsum[k].c) / (double)n : 0.0;
             if (grad_mass) grad_mass[k] = (gabs[k].s + gabs[k].c) * inv;
         }
+    return 0;
+}
+
+/* qo_integrate_one for integrals p0 .. p1-1 of a batch, one after another:
+ * integral p reads seeds + p * seed_stride (NULL: none), counts[p] and
+ * theta + p * theta_stride, and writes est[p], mass[p], grad[16 p ..] and
+ * grad_mass[16 p ..] (the last three optional).  Returns 0, or the first
+ * non-zero return of qo_integrate_one. */
+QO_EXPORT int qo_integrate_range(uint32_t source, uint32_t integrand, uint32_t s, uint32_t scramble,
+                                 const uint32_t* C, const uint32_t* g, const uint32_t* seeds,
+                                 uint64_t seed_stride, const uint32_t* counts, const float* theta,
+                                 uint64_t theta_stride, uint64_t p0, uint64_t p1, double* est,
+                                 double* mass, double* grad, double* grad_mass)
+{
+    for (uint64_t p = p0; p < p1; ++p) {
+        int rc = qo_integrate_one(source, integrand, s, scramble, C, g,
+                                  seeds ? seeds + p * seed_stride : NULL, counts[p],
+                                  theta + p * theta_stride, est + p, mass ? mass + p : NULL,
+                                  grad ? grad + 16 * p : NULL, grad_mass ? grad_mass + 16 * p : NULL);
+        if (rc != 0) return rc;
+    }
     return 0;
 }
 

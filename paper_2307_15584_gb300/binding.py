@@ -25,8 +25,10 @@ _lib = ctypes.CDLL(LIB_PATH)
 # enums of include/qmc.h
 QMC_OK = 0
 STATUS_NAMES = {0: "QMC_OK", 1: "QMC_ERR_INVALID_ARG", 2: "QMC_ERR_RANGE", 3: "QMC_ERR_ALIGN",
-                4: "QMC_ERR_CUDA", 5: "QMC_ERR_TIMEOUT", 6: "QMC_ERR_UNSUPPORTED", 7: "QMC_ERR_WORKSPACE"}
-SCRAMBLE_NONE, SCRAMBLE_XOR, SCRAMBLE_NESTED = 0, 1, 2
+                4: "QMC_ERR_CUDA", 5: "QMC_ERR_TIMEOUT", 6: "QMC_ERR_UNSUPPORTED", 7: "QMC_ERR_WORKSPACE",
+                8: "QMC_ERR_IO"}
+QMC_INJECTED_FAULT = -1
+SCRAMBLE_NONE, SCRAMBLE_XOR, SCRAMBLE_NESTED, SCRAMBLE_NESTED_XOR = 0, 1, 2, 3
 LATTICE_BACKWARD = 1
 SOURCE_SOBOL, SOURCE_LATTICE, SOURCE_PIXEL_LATTICE, SOURCE_RANDOM_LATTICE = 0, 1, 2, 3
 RLAT_HASH, RLAT_LFSR = 0, 1
@@ -39,7 +41,8 @@ EXPORTED = ["qmc_abi_version", "qmc_status_string", "qmc_sobol_matrices", "qmc_s
             "qmc_graph_begin", "qmc_graph_end", "qmc_graph_launch", "qmc_graph_destroy",
             "qmc_pixel_lattice_points", "qmc_halton_points", "qmc_sobol_matrices_wide",
             "qmc_sobol_points_wide", "qmc_sobol_points_partitioned", "qmc_halton_points_partitioned",
-            "qmc_random_lattice_points"]
+            "qmc_random_lattice_points", "qmc_last_cuda_error", "qmc_tune_save", "qmc_tune_load",
+            "qmc_tune_lookup"]
 HALTON_PLAIN, HALTON_FAURE, HALTON_LINEAR = 0, 1, 2
 
 
@@ -94,6 +97,11 @@ _sigs = {
     "qmc_tune_integrate": (ctypes.c_int, [ctypes.POINTER(qmc_problem), c_uint32, _P, _P, _P, _P, _P, _P, _P,
                                           c_size_t, _P, ctypes.POINTER(qmc_tuning)]),
     "qmc_tune_clear": (ctypes.c_int, []),
+    "qmc_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "qmc_tune_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(c_uint32)]),
+    "qmc_tune_lookup": (ctypes.c_int, [ctypes.POINTER(qmc_problem), c_uint32, c_uint32,
+                                       ctypes.POINTER(qmc_tuning)]),
+    "qmc_last_cuda_error": (ctypes.c_int, []),
     "qmc_graph_begin": (ctypes.c_int, [_P]),
     "qmc_graph_end": (ctypes.c_int, [_P, ctypes.POINTER(c_void_p)]),
     "qmc_graph_launch": (ctypes.c_int, [c_void_p, _P]),
@@ -146,6 +154,12 @@ def qmc_abi_version() -> int:
 
 def qmc_status_string(status: int) -> str:
     return _lib.qmc_status_string(status).decode()
+
+
+def qmc_last_cuda_error() -> int:
+    """cudaError_t code behind this thread's most recent QMC_ERR_CUDA (QMC_INJECTED_FAULT
+    for a fault injected with QMC_FAULT_INJECT=launch)."""
+    return _lib.qmc_last_cuda_error()
 
 
 def qmc_sobol_matrices(s: int, raw_init) -> np.ndarray:
@@ -276,6 +290,23 @@ def qmc_tune_integrate(problem, n_integrals, counts, theta, estimate, workspace,
 
 def qmc_tune_clear() -> None:
     _check(_lib.qmc_tune_clear(), "qmc_tune_clear")
+
+
+def qmc_tune_save(path: str) -> None:
+    _check(_lib.qmc_tune_save(os.fsencode(path)), "qmc_tune_save")
+
+
+def qmc_tune_load(path: str) -> int:
+    n = c_uint32(0)
+    _check(_lib.qmc_tune_load(os.fsencode(path), ctypes.byref(n)), "qmc_tune_load")
+    return n.value
+
+
+def qmc_tune_lookup(problem, n_integrals, with_gradient=False) -> qmc_tuning:
+    out = qmc_tuning()
+    _check(_lib.qmc_tune_lookup(ctypes.byref(problem), n_integrals, int(bool(with_gradient)), ctypes.byref(out)),
+           "qmc_tune_lookup")
+    return out
 
 
 def qmc_graph_begin(stream=None) -> None:

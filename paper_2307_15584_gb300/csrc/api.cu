@@ -1,8 +1,10 @@
 // api.cu -- the C-ABI of include/qmc.h: argument validation, the host-side
 // construction of Sobol' generator matrices, and kernel dispatch.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -10,6 +12,7 @@
 #include "../../include/qmc.h"
 #include "halton_points.h"
 #include "qmc_integrate.h"
+#include "qmc_host.h"
 #include "qmc_internal.h"
 
 namespace qmc {
@@ -35,6 +38,42 @@ const DeviceInfo& device_info() {
   cache.push_back(d);
   return cache.back();
 }
+
+namespace {
+thread_local int t_last_cuda_error = 0;
+
+nvtxDomainHandle_t nvtx_domain() {
+  static const nvtxDomainHandle_t d = nvtxDomainCreateA("qmc");
+  return d;
+}
+}  // namespace
+
+qmc_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return QMC_OK;
+  t_last_cuda_error = (int)e;
+  return QMC_ERR_CUDA;
+}
+
+bool launch_fault_injected() {
+  const char* v = std::getenv("QMC_FAULT_INJECT");
+  return v != nullptr && std::strcmp(v, "launch") == 0;
+}
+
+qmc_status injected_fault() {
+  t_last_cuda_error = QMC_INJECTED_FAULT;
+  return QMC_ERR_CUDA;
+}
+
+NvtxRange::NvtxRange(const char* name) {
+  nvtxEventAttributes_t at{};
+  at.version = NVTX_VERSION;
+  at.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+  at.messageType = NVTX_MESSAGE_TYPE_ASCII;
+  at.message.ascii = name;
+  nvtxDomainRangePushEx(nvtx_domain(), &at);
+}
+
+NvtxRange::~NvtxRange() { nvtxDomainRangePop(nvtx_domain()); }
 
 WsLayout workspace_layout(uint32_t n, uint64_t capacity_items, uint32_t values_per_item) {
   auto up = [](size_t v) { return (v + 255) / 256 * 256; };
@@ -119,7 +158,9 @@ using namespace qmc;
 
 extern "C" {
 
-uint32_t qmc_abi_version(void) { return 4u; }
+uint32_t qmc_abi_version(void) { return 5u; }
+
+int qmc_last_cuda_error(void) { return t_last_cuda_error; }
 
 const char* qmc_status_string(qmc_status st) {
   switch (st) {
@@ -131,6 +172,7 @@ const char* qmc_status_string(qmc_status st) {
     case QMC_ERR_TIMEOUT: return "QMC_ERR_TIMEOUT: bounded device wait expired";
     case QMC_ERR_UNSUPPORTED: return "QMC_ERR_UNSUPPORTED: combination not implemented";
     case QMC_ERR_WORKSPACE: return "QMC_ERR_WORKSPACE: workspace missing, misaligned or too small";
+    case QMC_ERR_IO: return "QMC_ERR_IO: file could not be read or written";
   }
   return "unknown qmc_status";
 }
@@ -206,7 +248,7 @@ qmc_status qmc_sobol_points(const uint32_t* d_matrices, uint32_t s, uint64_t ind
                             uint64_t count, uint32_t scramble, const uint32_t* d_seeds,
                             uint32_t* d_out_u32, float* d_out_f32, qmc_stream_t stream) {
   if (!d_matrices) return QMC_ERR_INVALID_ARG;
-  if (scramble > QMC_SCRAMBLE_NESTED) return QMC_ERR_INVALID_ARG;
+  if (scramble > QMC_SCRAMBLE_NESTED_XOR) return QMC_ERR_INVALID_ARG;
   if (scramble != QMC_SCRAMBLE_NONE && !d_seeds) return QMC_ERR_INVALID_ARG;
   qmc_status st = check_points_args(s, index_begin, count, d_out_u32, d_out_f32);
   if (st != QMC_OK || count == 0) return st;
@@ -220,7 +262,7 @@ qmc_status qmc_sobol_points(const uint32_t* d_matrices, uint32_t s, uint64_t ind
   a.index_begin = index_begin;
   a.m = 32;
   a.scramble = scramble;
-  return launch_sobol_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+  return enqueue("qmc_sobol_points", [&] { return launch_sobol_points(a, (cudaStream_t)stream); });
 }
 
 qmc_status qmc_sobol_points_wide(const uint32_t* d_matrices, uint32_t m, uint32_t s,
@@ -228,7 +270,7 @@ qmc_status qmc_sobol_points_wide(const uint32_t* d_matrices, uint32_t m, uint32_
                                  const uint32_t* d_seeds, uint32_t* d_out_u32, float* d_out_f32,
                                  qmc_stream_t stream) {
   if (!d_matrices || m < 32 || m > 64 || s == 0 || s > 1024) return QMC_ERR_INVALID_ARG;
-  if (scramble > QMC_SCRAMBLE_NESTED) return QMC_ERR_INVALID_ARG;
+  if (scramble > QMC_SCRAMBLE_NESTED_XOR) return QMC_ERR_INVALID_ARG;
   if (scramble != QMC_SCRAMBLE_NONE && !d_seeds) return QMC_ERR_INVALID_ARG;
   if (!index_range_ok(index_begin, count, m)) return QMC_ERR_RANGE;
   const qmc_status st = check_outputs(s, count, d_out_u32, d_out_f32);
@@ -243,7 +285,7 @@ qmc_status qmc_sobol_points_wide(const uint32_t* d_matrices, uint32_t m, uint32_
   a.s = s;
   a.m = m;
   a.scramble = scramble;
-  return launch_sobol_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+  return enqueue("qmc_sobol_points_wide", [&] { return launch_sobol_points(a, (cudaStream_t)stream); });
 }
 
 qmc_status qmc_sobol_points_partitioned(const uint32_t* d_matrices, uint32_t m, uint32_t s,
@@ -252,7 +294,7 @@ qmc_status qmc_sobol_points_partitioned(const uint32_t* d_matrices, uint32_t m, 
                                         uint32_t* d_out_u32, float* d_out_f32, qmc_stream_t stream) {
   if (!d_matrices || m < 32 || m > 64 || s == 0 || s > 1024 || q >= m) return QMC_ERR_INVALID_ARG;
   if (p >> q) return QMC_ERR_INVALID_ARG;  // element p of 2^q
-  if (scramble > QMC_SCRAMBLE_NESTED) return QMC_ERR_INVALID_ARG;
+  if (scramble > QMC_SCRAMBLE_NESTED_XOR) return QMC_ERR_INVALID_ARG;
   if (scramble != QMC_SCRAMBLE_NONE && !d_seeds) return QMC_ERR_INVALID_ARG;
   if (!index_range_ok(j_begin, count, m - q)) return QMC_ERR_RANGE;
   const qmc_status st = check_outputs(s, count, d_out_u32, d_out_f32);
@@ -269,7 +311,8 @@ qmc_status qmc_sobol_points_partitioned(const uint32_t* d_matrices, uint32_t m, 
   a.m = m;
   a.col0 = q;
   a.scramble = scramble;
-  return launch_sobol_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+  return enqueue("qmc_sobol_points_partitioned",
+                 [&] { return launch_sobol_points(a, (cudaStream_t)stream); });
 }
 
 // Fills the Halton arguments shared by the plain and partitioned entries;
@@ -303,7 +346,7 @@ qmc_status qmc_halton_points(uint32_t s, uint32_t mode, const uint32_t* h_multip
   a.out_f32 = d_out_f32;
   a.count = count;
   a.index_begin = index_begin;
-  return launch_halton_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+  return enqueue("qmc_halton_points", [&] { return launch_halton_points(a, (cudaStream_t)stream); });
 }
 
 qmc_status qmc_halton_points_partitioned(uint32_t s, uint32_t mode, const uint32_t* h_multipliers,
@@ -322,7 +365,8 @@ qmc_status qmc_halton_points_partitioned(uint32_t s, uint32_t mode, const uint32
   a.index_begin = j_begin;
   a.q = q;
   a.pconst = reverse_bits(p, q);
-  return launch_halton_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+  return enqueue("qmc_halton_points_partitioned",
+                 [&] { return launch_halton_points(a, (cudaStream_t)stream); });
 }
 
 qmc_status qmc_pixel_lattice_points(const uint32_t* d_g, uint32_t s, uint32_t image_width,
@@ -349,7 +393,8 @@ qmc_status qmc_pixel_lattice_points(const uint32_t* d_g, uint32_t s, uint32_t im
   const uint32_t side = image_width > image_height ? image_width : image_height;
   while (((uint64_t)1 << k) < side) ++k;
   a.grid_log2 = k;
-  return launch_pixel_lattice_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+  return enqueue("qmc_pixel_lattice_points",
+                 [&] { return launch_pixel_lattice_points(a, (cudaStream_t)stream); });
 }
 
 qmc_status qmc_lattice_points(const uint32_t* d_g, const uint32_t* d_shift, uint32_t s,
@@ -367,7 +412,7 @@ qmc_status qmc_lattice_points(const uint32_t* d_g, const uint32_t* d_shift, uint
   a.s = s;
   a.index_begin = index_begin;
   a.scramble = flags;
-  return launch_lattice_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+  return enqueue("qmc_lattice_points", [&] { return launch_lattice_points(a, (cudaStream_t)stream); });
 }
 
 
@@ -414,7 +459,7 @@ qmc_status validate_problem(const qmc_problem* p, bool need_source) {
   if (p->block != 0 && (p->block % 32 || p->block > 256)) return QMC_ERR_INVALID_ARG;
   if (need_source) {
     if (p->source == QMC_SOURCE_SOBOL) {
-      if (!p->d_matrices || p->randomize > QMC_SCRAMBLE_NESTED) return QMC_ERR_INVALID_ARG;
+      if (!p->d_matrices || p->randomize > QMC_SCRAMBLE_NESTED_XOR) return QMC_ERR_INVALID_ARG;
       if (p->randomize != QMC_SCRAMBLE_NONE && !p->d_seeds) return QMC_ERR_INVALID_ARG;
     } else if (p->source == QMC_SOURCE_LATTICE) {
       if (!p->d_g || (p->randomize & ~QMC_LATTICE_BACKWARD)) return QMC_ERR_INVALID_ARG;
@@ -517,8 +562,6 @@ qmc_status prepare(const qmc_problem* p, uint32_t n, const uint32_t* d_counts, c
   return QMC_OK;
 }
 
-qmc_status finish(cudaError_t e) { return e == cudaSuccess ? QMC_OK : QMC_ERR_CUDA; }
-
 }  // namespace
 
 qmc_status qmc_random_lattice_points(uint32_t kind, uint32_t seed, uint32_t instances, uint32_t s,
@@ -545,7 +588,8 @@ qmc_status qmc_random_lattice_points(uint32_t kind, uint32_t seed, uint32_t inst
   a.kind = kind;
   a.seed = seed;
   a.r_log2 = ilog2(instances);
-  return launch_random_lattice_points(a, (cudaStream_t)stream) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+  return enqueue("qmc_random_lattice_points",
+                 [&] { return launch_random_lattice_points(a, (cudaStream_t)stream); });
 }
 
 size_t qmc_integrate_workspace_bytes(const qmc_problem* p, uint32_t n_integrals,
@@ -571,7 +615,8 @@ qmc_status qmc_integrate(const qmc_problem* p, uint32_t n_integrals, const uint3
   qmc_status st = prepare(p, n_integrals, d_counts, d_theta, d_workspace, workspace_bytes, false, true, pr);
   if (st != QMC_OK || n_integrals == 0) return st;
   pr.a.estimate = d_estimate;
-  return finish(launch_integrate(pr.a, pr.block, false, (cudaStream_t)stream));
+  return enqueue("qmc_integrate",
+                 [&] { return launch_integrate(pr.a, pr.block, false, (cudaStream_t)stream); });
 }
 
 qmc_status qmc_integrate_backward(const qmc_problem* p, uint32_t n_integrals,
@@ -585,7 +630,8 @@ qmc_status qmc_integrate_backward(const qmc_problem* p, uint32_t n_integrals,
   if (st != QMC_OK || n_integrals == 0) return st;
   pr.a.grad_est = d_grad_estimate;
   pr.a.grad_theta = d_grad_theta;
-  return finish(launch_integrate(pr.a, pr.block, true, (cudaStream_t)stream));
+  return enqueue("qmc_integrate_backward",
+                 [&] { return launch_integrate(pr.a, pr.block, true, (cudaStream_t)stream); });
 }
 
 qmc_status qmc_integrate_fwd_bwd(const qmc_problem* p, uint32_t n_integrals,
@@ -598,13 +644,15 @@ qmc_status qmc_integrate_fwd_bwd(const qmc_problem* p, uint32_t n_integrals,
   Prepared pr;
   qmc_status st = prepare(p, n_integrals, d_counts, d_theta, d_workspace, workspace_bytes, true, true, pr);
   if (st != QMC_OK) return st;
-  if (n_integrals == 0) return cudaMemsetAsync(d_loss, 0, sizeof(double), (cudaStream_t)stream) == cudaSuccess
-                                   ? QMC_OK : QMC_ERR_CUDA;
+  if (n_integrals == 0)
+    return enqueue("qmc_integrate_fwd_bwd",
+                   [&] { return cudaMemsetAsync(d_loss, 0, sizeof(double), (cudaStream_t)stream); });
   pr.a.target = d_target;
   pr.a.estimate = d_estimate;
   pr.a.grad_theta = d_grad_theta;
   pr.a.loss = d_loss;
-  return finish(launch_integrate(pr.a, pr.block, true, (cudaStream_t)stream));
+  return enqueue("qmc_integrate_fwd_bwd",
+                 [&] { return launch_integrate(pr.a, pr.block, true, (cudaStream_t)stream); });
 }
 
 qmc_status qmc_integrate_points(const qmc_problem* p, uint32_t n_integrals,
@@ -621,19 +669,21 @@ qmc_status qmc_integrate_points(const qmc_problem* p, uint32_t n_integrals,
   pr.a.points_shared = points_shared;
   pr.a.row_off = reinterpret_cast<uint64_t*>(static_cast<char*>(d_workspace) + L.row_off);
   pr.a.estimate = d_estimate;
-  return finish(launch_integrate(pr.a, pr.block, false, (cudaStream_t)stream));
+  return enqueue("qmc_integrate_points",
+                 [&] { return launch_integrate(pr.a, pr.block, false, (cudaStream_t)stream); });
 }
 
 qmc_status qmc_read_device_error(const void* d_workspace, uint32_t* h_error_bits,
                                  qmc_stream_t stream) {
   if (!d_workspace || !h_error_bits || ((uintptr_t)d_workspace & 255u)) return QMC_ERR_INVALID_ARG;
   WsHeader h{};
-  if (cudaMemcpyAsync(&h, d_workspace, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream) !=
-          cudaSuccess ||
-      cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
-    return QMC_ERR_CUDA;
-  *h_error_bits = h.error_bits;
-  return QMC_OK;
+  const qmc_status st = enqueue("qmc_read_device_error", [&] {
+    const cudaError_t e =
+        cudaMemcpyAsync(&h, d_workspace, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    return e != cudaSuccess ? e : cudaStreamSynchronize((cudaStream_t)stream);
+  });
+  if (st == QMC_OK) *h_error_bits = h.error_bits;
+  return st;
 }
 
 }  // extern "C"

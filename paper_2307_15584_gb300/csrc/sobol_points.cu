@@ -28,7 +28,9 @@ namespace {
 using namespace pts;
 
 // ---------------------------------------------------------------------------
-// K1 fast path.  MODE: 0 none, 1 XOR, 2 nested.  K: 16-byte chunks per lane.
+// K1 fast path.  MODE: 0 none, 1 XOR, 2 nested (a.scramble = NESTED_XOR adds the
+// digital shift before the nested scramble, folded into the fixed per-lane terms).
+// K: 16-byte chunks per lane.
 // Shared memory: cols[s][m] (mirrored for nested), hin[2^u][s], pc[s].  Table
 // entries for index bits at or above m stay zero: no enumerated index sets them.
 // ---------------------------------------------------------------------------
@@ -79,6 +81,7 @@ __global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
       for (uint32_t k = 0; k < a.q_log2 && a.col0 + k < m; ++k)
         if ((p >> k) & 1u) y ^= cols[j * m + a.col0 + k];
       if (MODE == 1) y ^= __ldg(a.seeds + j);
+      if (MODE == 2 && a.scramble == QMC_SCRAMBLE_NESTED_XOR) y ^= __brev(__ldg(a.seeds + j));  // mirrored shift
       jd[4 * c + t] = j;
       lo[4 * c + t] = y;
       key[4 * c + t] = nested_key(MODE == 2 ? __ldg(a.seeds + j) : 0u);
@@ -222,6 +225,7 @@ __global__ void __launch_bounds__(kThreads) sobol_points_walk(PointsArgs a) {
       if ((jhi >> b) & 1u) base ^= cj[hi_col + b];
     const uint32_t seed = MODE != 0 ? __ldg(a.seeds + jo) : 0u;
     if (MODE == 1) base ^= seed;
+    if (MODE == 2 && a.scramble == QMC_SCRAMBLE_NESTED_XOR) base ^= __brev(seed);  // the shift, mirrored
     const NestedKey key = nested_key(seed);
     // the unit's outputs from its first row on: at most kWalkSteps k s <= 2^23 elements (s <= 1024)
     const uint64_t off0 = row * s + jo;
@@ -258,7 +262,7 @@ __global__ void __launch_bounds__(kThreads) sobol_points_generic(PointsArgs a) {
     const uint32_t* Cj = a.matrices + (uint64_t)j * a.m;
     uint32_t y = 0;
     for (; i != 0; i &= i - 1u) y ^= __ldg(Cj + (__ffsll((long long)i) - 1));
-    if (MODE == 1) y ^= __ldg(a.seeds + j);
+    if (MODE == 1 || (MODE == 2 && a.scramble == QMC_SCRAMBLE_NESTED_XOR)) y ^= __ldg(a.seeds + j);
     if (MODE == 2) y = __brev(nested_mix(__brev(y), nested_key(__ldg(a.seeds + j))));
     store1(a.out_u32, a.out_f32, f, y);
   }

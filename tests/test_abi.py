@@ -35,7 +35,7 @@ def test_header_symbols_exported(B):
     for name in declared:
         assert hasattr(lib, name), name
     assert sorted(B.EXPORTED) == sorted(declared)
-    assert B.qmc_abi_version() == 4
+    assert B.qmc_abi_version() == 5
     assert ctypes.sizeof(B.qmc_problem) == 72  # 4 + 3 pointers + 8 words, as in include/qmc.h
     assert "INVALID" in B.qmc_status_string(1)
 
@@ -78,7 +78,7 @@ def test_points_validation(B):
     # null matrices / no outputs / bad scramble / missing seeds
     assert L.qmc_sobol_points(None, 4, 0, 16, 0, None, FAKE, None, S) == 1
     assert L.qmc_sobol_points(FAKE, 4, 0, 16, 0, None, None, None, S) == 1
-    assert L.qmc_sobol_points(FAKE, 4, 0, 16, 3, FAKE, FAKE, None, S) == 1
+    assert L.qmc_sobol_points(FAKE, 4, 0, 16, 4, FAKE, FAKE, None, S) == 1
     assert L.qmc_sobol_points(FAKE, 4, 0, 16, 2, None, FAKE, None, S) == 1
     assert L.qmc_sobol_points(FAKE, 0, 0, 16, 0, None, FAKE, None, S) == 1
     assert L.qmc_sobol_points(FAKE, 1025, 0, 16, 0, None, FAKE, None, S) == 1
@@ -229,3 +229,89 @@ def test_partitioned_integration_validation(B):
     for good in (dict(index_bits=32), dict(index_bits=40, partition_log2=8), dict(index_bits=64, partition_log2=32)):
         assert B.qmc_integrate_workspace_bytes(_problem(B, **good), 4, None) > 0, good
         assert L.qmc_integrate(ref(_problem(B, **good)), 0, FAKE, FAKE, FAKE, ws, 1 << 30, None) == 0, good
+
+
+def test_fault_injection_on_host(B, monkeypatch):
+    """QMC_FAULT_INJECT=launch: every entry point that would enqueue GPU work
+    validates its arguments, then fails its launch on the host with QMC_ERR_CUDA
+    and records QMC_INJECTED_FAULT as the thread's last CUDA error -- without a
+    GPU (this runs on the CPU) and therefore without any fault on one."""
+    L = B._lib
+    ref = ctypes.byref
+    ws = 1 << 20
+    monkeypatch.setenv("QMC_FAULT_INJECT", "launch")
+    p = _problem(B)
+    static = _problem(B, max_count=4096)
+    best = B.qmc_tuning()
+    calls = {
+        "qmc_sobol_points": lambda: L.qmc_sobol_points(FAKE, 4, 0, 16, 3, FAKE, FAKE, None, 0),
+        "qmc_sobol_points_wide": lambda: L.qmc_sobol_points_wide(FAKE, 64, 4, 1 << 40, 16, 2, FAKE, FAKE, None, 0),
+        "qmc_sobol_points_partitioned": lambda: L.qmc_sobol_points_partitioned(FAKE, 64, 4, 3, 5, 0, 16, 0, None,
+                                                                               FAKE, None, 0),
+        "qmc_lattice_points": lambda: L.qmc_lattice_points(FAKE, None, 4, 0, 16, 0, FAKE, None, 0),
+        "qmc_halton_points": lambda: L.qmc_halton_points(4, 1, None, 0, 16, FAKE, None, 0),
+        "qmc_halton_points_partitioned": lambda: L.qmc_halton_points_partitioned(4, 0, None, 2, 1, 0, 16, FAKE,
+                                                                                 None, 0),
+        "qmc_pixel_lattice_points": lambda: L.qmc_pixel_lattice_points(FAKE, 4, 8, 8, 0, 4, 2, FAKE, None, 0),
+        "qmc_random_lattice_points": lambda: L.qmc_random_lattice_points(0, 7, 4, 8, 64, 64, 0, 16, 4, FAKE,
+                                                                         None, 0),
+        "qmc_integrate": lambda: L.qmc_integrate(ref(p), 4, FAKE, FAKE, FAKE, ws, 1 << 30, 0),
+        "qmc_integrate_backward": lambda: L.qmc_integrate_backward(ref(p), 4, FAKE, FAKE, FAKE, FAKE, ws,
+                                                                   1 << 30, 0),
+        "qmc_integrate_fwd_bwd": lambda: L.qmc_integrate_fwd_bwd(ref(p), 4, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, ws,
+                                                                 1 << 30, 0),
+        "qmc_integrate_points": lambda: L.qmc_integrate_points(ref(p), 4, FAKE, FAKE, 0, FAKE, FAKE, ws, 1 << 30, 0),
+        "qmc_integrate_static": lambda: L.qmc_integrate_static(ref(static), 4, FAKE, FAKE, FAKE, 0),
+        "qmc_read_device_error": lambda: L.qmc_read_device_error(ws, ref(ctypes.c_uint32()), 0),
+        "qmc_tune_integrate": lambda: L.qmc_tune_integrate(ref(p), 4, FAKE, FAKE, None, FAKE, None, None, ws,
+                                                           1 << 30, 0, ref(best)),
+    }
+    for name, call in calls.items():
+        assert call() == 4, name
+        assert B.qmc_last_cuda_error() == B.QMC_INJECTED_FAULT, name
+    # argument errors still come first
+    assert L.qmc_sobol_points(None, 4, 0, 16, 0, None, FAKE, None, 0) == 1
+    assert L.qmc_integrate(ref(p), 4, FAKE, FAKE, FAKE, ws + 16, 1 << 30, 0) == 7
+    # any other value of the variable injects nothing: validation-only paths still succeed
+    monkeypatch.setenv("QMC_FAULT_INJECT", "none")
+    assert L.qmc_sobol_points(FAKE, 4, 0, 0, 0, None, FAKE, None, 0) == 0
+
+
+def test_autotune_cache_file(B, tmp_path):
+    """The tuner's records round-trip through the JSON cache file: valid entries
+    load, malformed ones are skipped, a saved file loads back to the same records,
+    and a lookup finds the record of the current device kind (on a machine without
+    a GPU that kind is the empty name with 0 SMs)."""
+    src = tmp_path / "in.json"
+    entry = ('{{"device": "{dev}", "sms": {sms}, "source": 0, "integrand": 3, "s": 6, "randomize": 2, '
+             '"seeds_per_integral": 1, "gradient": {g}, "size_class": 10, "chunk": {c}, "block": {b}}}')
+    src.write_text('{"qmc_autotune_cache": 1, "entries": [\n' + ",\n".join([
+        entry.format(dev="", sms=0, g=0, c=2048, b=128),
+        entry.format(dev="NVIDIA GB300", sms=152, g=1, c=4096, b=256),
+        entry.format(dev="", sms=0, g=1, c=100, b=256),  # not a power of two: skipped
+        '{"device": "", "sms": 0, "chunk": 1024}',  # incomplete: skipped
+    ]) + "\n]}\n")
+    B.qmc_tune_clear()
+    assert B.qmc_tune_load(str(src)) == 2
+    p = _problem(B)
+    hit = B.qmc_tune_lookup(p, 1000)  # size class ceil(log2 1000) = 10
+    assert (hit.chunk, hit.block) == (2048, 128)
+    assert B.qmc_tune_lookup(p, 1000, with_gradient=True).chunk == 0  # recorded for another device kind
+    assert B.qmc_tune_lookup(p, 5000).chunk == 0  # another size class
+    out = tmp_path / "out.json"
+    B.qmc_tune_save(str(out))
+    import json
+    saved = json.loads(out.read_text())["entries"]
+    assert sorted((e["device"], e["gradient"], e["chunk"], e["block"]) for e in saved) == \
+        [("", 0, 2048, 128), ("NVIDIA GB300", 1, 4096, 256)]
+    B.qmc_tune_clear()
+    assert B.qmc_tune_lookup(p, 1000).chunk == 0
+    assert B.qmc_tune_load(str(out)) == 2
+    assert B.qmc_tune_lookup(p, 1000).chunk == 2048
+    B.qmc_tune_clear()
+    with pytest.raises(B.QMCError) as e:
+        B.qmc_tune_load(str(tmp_path / "missing.json"))
+    assert e.value.status == 8
+    with pytest.raises(B.QMCError) as e:
+        B.qmc_tune_save(str(tmp_path / "no_such_dir" / "x.json"))
+    assert e.value.status == 8

@@ -39,7 +39,7 @@ def _run_wide(B, Wd, m, s, begin, count, mode, seeds_d):
 
 @pytest.mark.parametrize("m", [32, 52, 64])
 @pytest.mark.parametrize("s", [1, 6, 7, 32, 128])
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_wide_sobol_bit_exact(B, oracle, m, s, mode):
     W, _ = _wide(B, oracle, m, s)
     Wd = B.u32_tensor(W[:s])
@@ -84,7 +84,7 @@ def test_partitioned_sobol_bit_exact(B, oracle, m, s, q, p, j_begin):
     seeds = inputs.scramble_seeds(s, seed=99)
     sd = B.u32_tensor(seeds)
     count = min(2500, (1 << (m - q)) - j_begin)
-    for mode in (0, 1, 2):
+    for mode in (0, 1, 2, 3):
         u = torch.empty((count, s), dtype=torch.int32, device="cuda")
         f = torch.empty((count, s), dtype=torch.float32, device="cuda")
         B.qmc_sobol_points_partitioned(Wd, m, s, q, p, j_begin, count, mode, sd, u, f)

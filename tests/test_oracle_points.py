@@ -243,6 +243,47 @@ def test_nested_scramble_keeps_net_property(oracle, C32):
     np.testing.assert_array_equal(ux, u0 ^ seeds[None, :])
 
 
+def test_nested_xor_scramble_structure(oracle, C32):
+    """QMC_SCRAMBLE_NESTED_XOR (the digital shift, then the nested scramble, one seed
+    per dimension): dimension 0 over the first 2^w indices covers every value of
+    the first w digits, so the map is seen on all of them; it is a bijection at
+    every level and digit d of the output depends only on digits 1..d of the
+    input (nested), it keeps the (0,m,2)-net property of dimensions 0-1, and it
+    differs from both of the modes it composes."""
+    w = 12
+    for seed in inputs.scramble_seeds(4, seed=13).tolist():
+        sd = np.array([seed], np.uint32)
+        y, _ = oracle.sobol_points(C32[:1], 0, 1 << w)  # first w digits = the w-bit reversal of i
+        z, _ = oracle.sobol_points(C32[:1], 0, 1 << w, mode=oracle.SCRAMBLE_NESTED_XOR, seeds=sd)
+        y, z = y[:, 0].astype(np.uint64), z[:, 0].astype(np.uint64)
+        assert np.array_equal(np.sort(z >> np.uint64(32 - w)), np.arange(1 << w, dtype=np.uint64))
+        for d in range(1, w):
+            prefix = (y >> np.uint64(32 - d)).astype(np.int64)
+            out = z >> np.uint64(32 - d)
+            for g in range(1 << d):
+                assert len(set(out[prefix == g].tolist())) == 1, (seed, d, g)
+    seeds = inputs.scramble_seeds(2, seed=5)
+    u3, _ = oracle.sobol_points(C32[:2], 0, 1 << 12, mode=oracle.SCRAMBLE_NESTED_XOR, seeds=seeds)
+    for m in range(1, 13):
+        assert _is_tms_net(u3[: 1 << m], m, 0, (0, 1))
+    u1, _ = oracle.sobol_points(C32[:2], 0, 1 << 12, mode=oracle.SCRAMBLE_XOR, seeds=seeds)
+    u2, _ = oracle.sobol_points(C32[:2], 0, 1 << 12, mode=oracle.SCRAMBLE_NESTED, seeds=seeds)
+    u0, _ = oracle.sobol_points(C32[:2], 0, 1 << 12)
+    assert (u3 != u1).mean() > 0.9 and (u3 != u2).mean() > 0.9 and (u3 != u0).mean() > 0.9
+
+
+def test_nested_xor_uniform_over_seeds(oracle, C32):
+    """Over seeds, one fixed point's first 8 digits under NESTED_XOR are close to
+    uniform (the shift and the hash share the seed word)."""
+    seeds = inputs.words32(np.uint64(78), np.arange(1 << 13))
+    top = np.array([oracle.sobol_points(C32[1:2], 1234567, 1, mode=oracle.SCRAMBLE_NESTED_XOR,
+                                        seeds=np.array([s], np.uint32), threads=1)[0][0, 0] >> 24
+                    for s in seeds.tolist()])
+    cnt = np.bincount(top, minlength=256)
+    chi2 = ((cnt - cnt.mean()) ** 2 / cnt.mean()).sum()
+    assert chi2 < 400  # 255 dof: mean 255, sd ~22.6
+
+
 # ------------------------------------------------------------------ rank-1 lattice
 def _rev(k, m):
     return int(format(k, f"0{m}b")[::-1], 2) if m else 0

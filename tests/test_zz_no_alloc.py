@@ -20,6 +20,20 @@ def _tol(ref, W):
     return 1e-6 * np.abs(ref) + 1e-12 * W
 
 
+def test_static_startup_call_places_the_array():
+    """A caller that cannot allocate later makes one call with no integrals at
+    start-up: it places the library's array on the device and looks up its
+    address, reads no other pointer and enqueues nothing."""
+    from paper_2307_15584_gb300 import binding as B
+
+    C6 = B.u32_tensor(B.qmc_sobol_matrices(6, inputs.sobol_raw_init(6)))
+    prob = B.make_problem(B.SOURCE_SOBOL, B.F_GAUSSMIX4_6D, 6, 0, matrices=C6, max_count=4096)
+    torch.cuda.synchronize()
+    B.qmc_integrate_static(prob, 0, None, None, None)
+    B.qmc_integrate_static(prob, 0, None, None, None)  # and again: the address is kept
+    torch.cuda.synchronize()
+
+
 def test_static_matches_workspace_entry_point_twice():
     from paper_2307_15584_gb300 import binding as B
 
