@@ -46,7 +46,7 @@ struct Integrand<QMC_F_GAUSSMIX4_6D> {
   }
 
   // 2^(-q k) for component c of the scaled point X (x = X 2^-32); q_out receives q
-  // (its leading word when EXACT); with SUMS, se / so receive the sums of the
+  // (its leading word when EXACT); with SUMS, se / so are set to the sums of the
   // differences over the even / odd dimensions (gradient).
   template <bool EXACT, bool SUMS>
   __device__ __forceinline__ float gauss(const float* X, int c, float& q_out, float& t_abs, float& se,
@@ -58,7 +58,9 @@ struct Integrand<QMC_F_GAUSSMIX4_6D> {
         const float diff = __fmaf_rn(X[d], 0x1p-32f, (d & 1) ? -nu[c] : -mu[c]);  // x - m, one rounding
         q = __fmaf_rn(diff, diff, q);
         if constexpr (SUMS) {  // the differences themselves: sum x - 3 mu would cancel near the mean
-          if (d & 1) so = __fadd_rn(so, diff); else se = __fadd_rn(se, diff);
+          if (d < 2) (d & 1 ? so : se) = diff;
+          else if (d & 1) so = __fadd_rn(so, diff);
+          else se = __fadd_rn(se, diff);
         }
       }
       const float t = __fmaf_rn(q, kh[c], __fmul_rn(q, kl[c]));
@@ -73,7 +75,9 @@ struct Integrand<QMC_F_GAUSSMIX4_6D> {
         const float xd = __fmul_rn(X[d], 0x1p-32f);  // exact
         if constexpr (SUMS) {
           const float diff = __fsub_rn(xd, m);
-          if (d & 1) so = __fadd_rn(so, diff); else se = __fadd_rn(se, diff);
+          if (d < 2) (d & 1 ? so : se) = diff;
+          else if (d & 1) so = __fadd_rn(so, diff);
+          else se = __fadd_rn(se, diff);
         }
         const float hi = fmaxf(xd, m), lo = fminf(xd, m);
         const float D = __fsub_rn(hi, lo);                        // |x - m| rounded
@@ -117,7 +121,7 @@ struct Integrand<QMC_F_GAUSSMIX4_6D> {
     err = 0.0f;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      float q, t, se = 0.0f, so = 0.0f;
+      float q, t, se, so;
       const float G = gauss<EXACT, true>(x, c, q, t, se, so);
       const float wG = __fmul_rn(w[c], G);
       f = __fadd_rn(f, wG);

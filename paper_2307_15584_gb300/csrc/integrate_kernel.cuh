@@ -26,7 +26,7 @@ namespace integ {
 // unifloat_x2p32 (exact: x = map_u32_to_unifloat(u) = X * 2^-32); the
 // integrands fold the 2^-32 into their constants.
 // ---------------------------------------------------------------------------
-template <int S, int SCR>  // SCR: 0 none, 1 XOR, 2 nested
+template <int S, int SCR>  // SCR: 0 none, 1 XOR, 2 nested (or, by a.randomize, XOR then nested)
 struct SobolSource {
   static constexpr int kRow = (S + 3) & ~3;  // table row stride: whole 128-bit words
   const uint32_t* cols;  // shared: [s][m], mirrored when nested
@@ -96,7 +96,10 @@ struct SobolSource {
           if ((cp >> b) & 1u) y ^= cols[j * m + b];
       }
       const uint32_t seed = (sd && (uint32_t)j < s) ? __ldg(sd + j) : 0u;
-      yl[j] = y ^ lane_y[j] ^ (SCR == 1 ? seed : 0u);
+      // XOR: the digital shift; NESTED_XOR: the same shift before the nested scramble, in the
+      // mirrored domain the columns are stored in
+      const bool shift_mirrored = SCR == 2 && a.randomize == QMC_SCRAMBLE_NESTED_XOR;
+      yl[j] = y ^ lane_y[j] ^ (SCR == 1 ? seed : 0u) ^ (shift_mirrored ? __brev(seed) : 0u);
       key[j] = nested_key(seed);
     }
   }
@@ -313,65 +316,83 @@ constexpr float kU32 = 5.9604645e-8f;
 // One pass over the samples of the current item.  Returns nothing; adds into
 // acc and, on the fp32 pass, the squared per-sample error scales into e2.
 // Samples are summed in blocks of kBlock consecutive iterations with plain fp32
-// adds, and each block sum enters the lane's Kahan sum (a two-level reduction,
-// Sec. 2.5.1): the block adds carry at most (kBlock-1) unit roundoffs of the
-// block's absolute sum, the compensated sum carries almost nothing.
+// adds, and each block sum enters the lane's Kahan sum of the estimate (a
+// two-level reduction, Sec. 2.5.1): the block adds carry at most (kBlock-1)
+// unit roundoffs of the block's absolute sum, the compensated sum carries
+// almost nothing.  The parameter gradients' block sums enter plain running
+// sums: their error against the fp64 oracle is set by the fp32 evaluation of
+// each term (about 8u ln2 |t| relative, see the mixture), which a compensated
+// sum was measured not to reduce, at 16 more registers and 10 % of the fused
+// kernel's rate.  Whole blocks run unrolled (by kBlock, by two with the
+// gradient, whose 17 sums leave fewer registers); the item's last, partial
+// block runs sample by sample.
 constexpr uint32_t kBlock = 4;
+
+template <bool EXACT, bool GRAD, int NV, class Src, class F>
+__device__ __forceinline__ void run_sample(const Src& src, const F& f, uint32_t r, uint32_t len, float (&blk)[NV],
+                                           Kahan (&acc)[NV], float& e2) {
+  const uint32_t il = (r << 5) + (threadIdx.x & 31u);
+  const bool valid = il < len;
+  float x[F::S];
+  src.point(r, il, valid, x);
+  float err;
+  if constexpr (GRAD) {
+    float gq[16];
+    const float v = f.template eval_grad<EXACT>(x, gq, err);
+    if (valid) {
+      blk[0] = __fadd_rn(blk[0], v);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float G = gq[4 * c];
+        blk[1 + 4 * c] = __fadd_rn(blk[1 + 4 * c], G);
+        blk[2 + 4 * c] = __fmaf_rn(G, gq[4 * c + 1], blk[2 + 4 * c]);
+        blk[3 + 4 * c] = __fmaf_rn(G, gq[4 * c + 2], blk[3 + 4 * c]);
+        blk[4 + 4 * c] = __fmaf_rn(G, gq[4 * c + 3], blk[4 + 4 * c]);
+      }
+      if constexpr (F::kAdaptive && !EXACT) e2 = __fmaf_rn(err, err, e2);
+    }
+  } else {
+    const float v = f.template eval<EXACT>(x, err);
+    if (valid) {
+      if constexpr (EXACT && F::kExactPair) {  // f = v + err: both words, each compensated
+        acc[0].add(v);
+        acc[0].add(err);
+      } else {
+        blk[0] = __fadd_rn(blk[0], v);
+      }
+      if constexpr (F::kAdaptive && !EXACT) e2 = __fmaf_rn(err, err, e2);
+    }
+  }
+}
 
 template <bool EXACT, bool GRAD, int NV, class Src, class F>
 __device__ __forceinline__ void run_item(const Src& src, const F& f, uint32_t len, Kahan (&acc)[NV],
                                          float& e2) {
-  const uint32_t lane = threadIdx.x & 31u;
   const uint32_t R = (len + 31u) >> 5;
-  for (uint32_t r0 = 0; r0 < R; r0 += kBlock) {
+  auto fold = [&](const float (&blk)[NV]) {
+    if constexpr (!(EXACT && F::kExactPair)) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        if (v == 0) acc[v].add(blk[v]);                // the estimate: compensated
+        else acc[v].s = __fadd_rn(acc[v].s, blk[v]);   // the gradients: plain
+      }
+    }
+  };
+  uint32_t r0 = 0;
+  for (; r0 + kBlock <= R; r0 += kBlock) {
     float blk[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) blk[v] = 0.0f;
-    const uint32_t r1 = min(R, r0 + kBlock);
-    for (uint32_t r = r0; r < r1; ++r) {
-      const uint32_t il = (r << 5) + lane;
-      const bool valid = il < len;
-      float x[F::S];
-      src.point(r, il, valid, x);
-      float err;
-      if constexpr (GRAD) {
-        float gq[16];
-        const float v = f.template eval_grad<EXACT>(x, gq, err);
-        if (valid) {
-          blk[0] = __fadd_rn(blk[0], v);
+#pragma unroll (GRAD ? 2 : kBlock)
+    for (uint32_t k = 0; k < kBlock; ++k) run_sample<EXACT, GRAD>(src, f, r0 + k, len, blk, acc, e2);
+    fold(blk);
+  }
+  if (r0 < R) {
+    float blk[NV];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const float G = gq[4 * c];
-            blk[1 + 4 * c] = __fadd_rn(blk[1 + 4 * c], G);
-            blk[2 + 4 * c] = __fmaf_rn(G, gq[4 * c + 1], blk[2 + 4 * c]);
-            blk[3 + 4 * c] = __fmaf_rn(G, gq[4 * c + 2], blk[3 + 4 * c]);
-            blk[4 + 4 * c] = __fmaf_rn(G, gq[4 * c + 3], blk[4 + 4 * c]);
-          }
-          if constexpr (F::kAdaptive && !EXACT) e2 = __fmaf_rn(err, err, e2);
-        }
-      } else {
-        const float v = f.template eval<EXACT>(x, err);
-        if (valid) {
-          if constexpr (EXACT && F::kExactPair) {  // f = v + err: both words, each compensated
-            acc[0].add(v);
-            acc[0].add(err);
-          } else {
-            blk[0] = __fadd_rn(blk[0], v);
-          }
-          if constexpr (F::kAdaptive && !EXACT) e2 = __fmaf_rn(err, err, e2);
-        }
-      }
-    }
-    if constexpr (EXACT && F::kExactPair) continue;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      // The estimate keeps the compensated sum.  The parameter gradients are
-      // held to a tolerance relative to the mean absolute derivative, which a
-      // plain sum of the lane's block sums meets with a wide margin (about
-      // (kBlock - 1 + blocks) unit roundoffs of the sum of absolute terms).
-      if (v == 0) acc[v].add(blk[v]);
-      else acc[v].s = __fadd_rn(acc[v].s, blk[v]);
-    }
+    for (int v = 0; v < NV; ++v) blk[v] = 0.0f;
+    for (uint32_t r = r0; r < R; ++r) run_sample<EXACT, GRAD>(src, f, r, len, blk, acc, e2);
+    fold(blk);
   }
 }
 
@@ -470,7 +491,7 @@ cudaError_t launch_main_fn(const IntegrateArgs& a, uint32_t block, cudaStream_t 
     return (a.randomize & QMC_LATTICE_BACKWARD) ? launch_main_t<LatticeSource<S, true>, FN, GRAD>(a, block, stream)
                                                 : launch_main_t<LatticeSource<S, false>, FN, GRAD>(a, block, stream);
   const uint32_t scr = a.seeds ? a.randomize : 0u;
-  if (scr == QMC_SCRAMBLE_NESTED) return launch_main_t<SobolSource<S, 2>, FN, GRAD>(a, block, stream);
+  if (scr >= QMC_SCRAMBLE_NESTED) return launch_main_t<SobolSource<S, 2>, FN, GRAD>(a, block, stream);
   if (scr == QMC_SCRAMBLE_XOR) return launch_main_t<SobolSource<S, 1>, FN, GRAD>(a, block, stream);
   return launch_main_t<SobolSource<S, 0>, FN, GRAD>(a, block, stream);
 }
