@@ -25,7 +25,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 SOURCE_SOBOL, SOURCE_LATTICE, SOURCE_PIXEL_LATTICE, SOURCE_RANDOM_LATTICE = 0, 1, 2, 3
 RLAT_HASH, RLAT_LFSR = 0, 1
-SCRAMBLE_NONE, SCRAMBLE_XOR, SCRAMBLE_NESTED = 0, 1, 2
+SCRAMBLE_NONE, SCRAMBLE_XOR, SCRAMBLE_NESTED, SCRAMBLE_NESTED_XOR = 0, 1, 2, 3
 F_BILINEAR2D, F_GENZ_PRODUCT_PEAK, F_GENZ_OSCILLATORY, F_GAUSSMIX4_6D, F_SCENE4D = 0, 1, 2, 3, 4
 
 
@@ -82,6 +82,7 @@ def lib() -> ctypes.CDLL:
             "qo_pixel_shift": (u32, [u32, u32, u32]),
             "qo_pixel_lattice_u32": (u32, [u32, u32, u32]),
             "qo_integrate_one": (i32, [u32, u32, u32, u32, P, P, P, u32, P, P, P, P, P]),
+            "qo_integrate_range": (i32, [u32, u32, u32, u32, P, P, P, u64, P, P, u64, u64, u64, P, P, P, P]),
             "qo_integrand": (dbl, [u32, u32, P, P, P]),
             "qo_integrate_partitioned": (i32, [u32, u32, u32, P, u32, u32, u64, P, u32, P, P, P, P, P]),
             "qo_gaussmix_f64": (dbl, [P, P]),
@@ -284,20 +285,24 @@ def integrate(source, integrand, s, counts, theta, *, C=None, g=None, scramble=0
     grad = np.zeros((n, 16)) if with_grad else None
     gmass = np.zeros((n, 16)) if with_grad else None
 
-    def one(p):
-        rc = lib().qo_integrate_one(
-            source, integrand, s, scramble, _p(C), _p(g),
-            None if seeds is None else seeds[p].ctypes.data, int(counts[p]), theta[p].ctypes.data,
-            est[p:].ctypes.data, mass[p:].ctypes.data,
-            None if grad is None else grad[p].ctypes.data,
-            None if gmass is None else gmass[p].ctypes.data)
+    def run(rng):
+        p0, p1 = rng
+        rc = lib().qo_integrate_range(
+            source, integrand, s, scramble, _p(C), _p(g), _p(seeds), 0 if seeds is None else seeds.shape[1],
+            counts.ctypes.data, theta.ctypes.data, theta.shape[1], p0, p1, est.ctypes.data, mass.ctypes.data,
+            _p(grad), _p(gmass))
         if rc != 0:
             raise ValueError("oracle rejected the problem")
 
-    # largest integrals first so the pool stays busy
-    order = np.argsort(-counts.astype(np.int64), kind="stable")
-    with ThreadPoolExecutor(_threads(threads)) as ex:
-        list(ex.map(one, order.tolist()))
+    # contiguous ranges of about equal work (samples plus a per-integral overhead), many per
+    # thread so the pool stays busy; each integral is still computed alone, in index order
+    T = _threads(threads)
+    if n:
+        cost = np.cumsum(counts.astype(np.float64) + 64.0)
+        cuts = np.searchsorted(cost, np.linspace(0.0, cost[-1], min(n, 32 * T) + 1)[1:-1], side="right")
+        bounds = sorted({0, n, *[int(c) for c in cuts if 0 < c < n]})
+        with ThreadPoolExecutor(T) as ex:
+            list(ex.map(run, zip(bounds[:-1], bounds[1:])))
     return {"est": est, "mass": mass, "grad": grad, "grad_mass": gmass}
 
 

@@ -6,14 +6,13 @@ elements' mean against the estimate over the whole sequence; and integrals of
 2^32 - 1 samples per element, where the index reaches bit 63 and only
 properties that hold at any size can be checked.
 
-Tolerances as in the plain integration tests: |I32 - I64| <= 1e-6 |I64| +
-1e-12 W (W the mixture's weight sum, 1 otherwise); gradients within
-1e-5 (|J64| + M) + 1e-12 W, M = mean |df/dtheta|."""
+Tolerances as in the plain integration tests (tests/tolerances.py)."""
 import numpy as np
 import pytest
 import torch
 
 from paper_2307_15584_gb300 import inputs
+from tolerances import est_tol, grad_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -23,10 +22,6 @@ def B():
     from paper_2307_15584_gb300 import binding
 
     return binding
-
-
-def _est_tol(ref, W):
-    return 1e-6 * np.abs(ref) + 1e-12 * W
 
 
 def _run(B, prob, counts, theta, with_grad=False):
@@ -51,6 +46,7 @@ CASES = {
     "oscillatory_q5_m40_xor": ("oscillatory", 8, 5, 40, 1, False),
     "product_peak_q1_m33_plain": ("product_peak", 16, 1, 33, 0, False),
     "scene_q32_m64_nested": ("scene", 4, 32, 64, 2, True),
+    "product_peak_q2_m48_nested_xor": ("product_peak", 5, 2, 48, 3, True),
 }
 
 
@@ -83,11 +79,11 @@ def test_element_estimates_match_oracle(B, oracle, case):
     elements = np.arange(n, dtype=np.uint64) % (np.uint64(1) << np.uint64(q))
     ref = oracle.integrate_partitioned(OF, s, counts, theta, Wm, q, elements, scramble=scr,
                                        seeds=seeds if scr else None, with_grad=grad)
-    bad = np.abs(e - ref["est"]) > _est_tol(ref["est"], W)
+    bad = np.abs(e - ref["est"]) > est_tol(ref["est"], W)
     assert not bad.any(), (np.flatnonzero(bad)[:5], e[bad][:5], ref["est"][bad][:5])
     assert e[0] == 0.0
     if grad:
-        g_tol = 1e-5 * (np.abs(ref["grad"]) + ref["grad_mass"]) + 1e-12 * W[:, None]
+        g_tol = grad_tol(theta, ref["grad"], ref["grad_mass"])
         assert (np.abs(g - ref["grad"]) <= g_tol).all(), np.max(np.abs(g - ref["grad"]) / g_tol)
 
 
@@ -116,8 +112,8 @@ def test_elements_combine_into_the_whole_sequence(B, oracle):
     np.testing.assert_array_equal(e_wide, e_whole)
     ref = oracle.integrate(oracle.SOURCE_SOBOL, oracle.F_GAUSSMIX4_6D, s, counts[:1], th,
                            C=np.ascontiguousarray(Wm[1:, :32]), scramble=oracle.SCRAMBLE_NESTED, seeds=seeds)
-    assert abs(e_whole[0] - ref["est"][0]) <= _est_tol(ref["est"][0], W)
-    assert abs(e_parts.mean() - ref["est"][0]) <= 2 * _est_tol(ref["est"][0], W)
+    assert abs(e_whole[0] - ref["est"][0]) <= est_tol(ref["est"][0], W)
+    assert abs(e_parts.mean() - ref["est"][0]) <= 2 * est_tol(ref["est"][0], W)
 
 
 @pytest.mark.parametrize("q", [2, 32])

@@ -33,7 +33,7 @@ def _sobol_case(B, oracle, s, begin, count, mode, seed=7):
     np.testing.assert_array_equal(_f32_bits(f), of.view(np.uint32))
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 @pytest.mark.parametrize("s", [1, 2, 3, 4, 5, 6, 7, 12, 16, 24, 31, 32, 33, 64, 96, 100, 1000])
 def test_sobol_points_bit_exact(B, oracle, s, mode):
     """Fast path (s with K <= 4), the walking path (5, 7, 31, 33, 100: lanes own dimensions,
@@ -45,7 +45,7 @@ def test_sobol_points_bit_exact(B, oracle, s, mode):
 
 @pytest.mark.parametrize("begin", [1, 4, 5, 4096, 123457, (1 << 31) + 8, (1 << 32) - 3000])
 def test_sobol_points_offsets(B, oracle, begin):
-    for s, mode in ((32, 2), (2, 0), (6, 1)):
+    for s, mode in ((32, 2), (2, 0), (6, 1), (5, 3), (32, 3)):
         _sobol_case(B, oracle, s, begin, min(2999, (1 << 32) - begin), mode)
 
 
@@ -77,32 +77,27 @@ def test_config1_plain_2d_sobol_and_net(B, oracle):
         assert np.unique(code).size == 1 << 16, k1
 
 
-def test_config2_full_size_sampled(B, oracle):
+def _compare_in_chunks(B, u, f, ref_fn, rows, chunk=1 << 21):
+    """Every row of the device outputs u, f against ref_fn(r0, n) -> (u32, f32), chunk by chunk."""
+    for r0 in range(0, rows, chunk):
+        n = min(chunk, rows - r0)
+        ou, of = ref_fn(r0, n)
+        np.testing.assert_array_equal(B.as_u32(u[r0:r0 + n]), ou, err_msg=f"rows {r0}..{r0 + n}")
+        np.testing.assert_array_equal(_f32_bits(f[r0:r0 + n]), of.view(np.uint32), err_msg=f"rows {r0}..{r0 + n}")
+
+
+def test_config2_full_size_every_row(B, oracle):
     """Config 2 at full size (s = 32, 2^24 points, nested scramble, u32 + fp32) in
-    the bench's launch configuration; rows checked: the first and last 4096, the
-    group boundaries of every warp range near them, and 2^14 random rows."""
+    the bench's launch configuration: every one of the 2^29 coordinates, both
+    outputs, bit for bit against the oracle."""
     s, N = 32, 1 << 24
     C = B.qmc_sobol_matrices(s, inputs.sobol_raw_init(s))
     seeds = inputs.scramble_seeds(s)
     u, f = B.sobol_points(B.u32_tensor(C), N, scramble=2, seeds=B.u32_tensor(seeds))
-    rng = np.random.default_rng(5)
-    rows = np.unique(np.concatenate([np.arange(4096), np.arange(N - 4096, N),
-                                     rng.integers(0, N, size=1 << 14)]))
-    idx = torch.from_numpy(rows).cuda()
-    gu = B.as_u32(u.index_select(0, idx))
-    gf = _f32_bits(f.index_select(0, idx))
+    torch.cuda.synchronize()
+    _compare_in_chunks(B, u, f, lambda r0, n: oracle.sobol_points(C, r0, n, 2, seeds), N)
     del u, f
-    for r0 in (0, N - 4096):
-        ou, of = oracle.sobol_points(C, r0, 4096, 2, seeds)
-        sel = np.searchsorted(rows, np.arange(r0, r0 + 4096))
-        np.testing.assert_array_equal(gu[sel], ou)
-        np.testing.assert_array_equal(gf[sel], of.view(np.uint32))
-    pos = {r: i for i, r in enumerate(rows.tolist())}
-    rand = rows[(rows >= 4096) & (rows < N - 4096)]
-    for r in rand[:: max(1, rand.size // 2048)].tolist():
-        ou, of = oracle.sobol_points(C, r, 1, 2, seeds, threads=1)
-        np.testing.assert_array_equal(gu[pos[r]], ou[0])
-        np.testing.assert_array_equal(gf[pos[r]], of[0].view(np.uint32))
+    torch.cuda.empty_cache()
 
 
 @pytest.mark.parametrize("backward", [False, True])
@@ -121,55 +116,13 @@ def test_lattice_points_bit_exact(B, oracle, s, backward):
         np.testing.assert_array_equal(_f32_bits(f), of.view(np.uint32))
 
 
-def test_config3_lattice_full_size_sampled(B, oracle):
-    """Config 3 points: s = 16, 2^26 points, odd seeded g, integer CP shift."""
+def test_config3_lattice_full_size_every_row(B, oracle):
+    """Config 3 points: s = 16, 2^26 points, odd seeded g, integer CP shift; every
+    coordinate of both outputs bit for bit against the oracle."""
     s, N = 16, 1 << 26
     g, sh = inputs.lattice_generator(s), inputs.lattice_shift(s)
     u, f = B.lattice_points(B.u32_tensor(g), N, shift=B.u32_tensor(sh))
-    rng = np.random.default_rng(6)
-    rows = np.unique(np.concatenate([np.arange(2048), np.arange(N - 2048, N), rng.integers(0, N, 4096)]))
-    idx = torch.from_numpy(rows).cuda()
-    gu, gf = B.as_u32(u.index_select(0, idx)), _f32_bits(f.index_select(0, idx))
-    del u, f
-    for i, r in enumerate(rows.tolist()):
-        if i % 7 and 2048 <= r < N - 2048:
-            continue
-        ou, of = oracle.lattice_points(g, sh, r, 1, threads=1)
-        np.testing.assert_array_equal(gu[i], ou[0])
-        np.testing.assert_array_equal(gf[i], of[0].view(np.uint32))
-
-
-def test_map_exhaustive_all_2pow32(B, oracle):
-    """Sec. 2.1: the GPU float mapping equals the oracle's for every one of the 2^32
-    inputs (the paper's own exhaustive check) and stays below 1; the oracle's
-    monotonicity is pinned on the CPU, so equality carries it over.  The 1-D
-    lattice with g = 1 enumerates phi_2(k), a permutation of all inputs."""
-    g = B.u32_tensor(np.array([1], np.uint32))
-    chunk = 1 << 28
-    top = 0.0
-    for c in range(1 << 4):
-        u, f = B.lattice_points(g, chunk, index_begin=c * chunk)
-        uu = B.as_u32(u).reshape(-1)
-        ff = f.cpu().numpy().reshape(-1)
-        del u, f
-        np.testing.assert_array_equal(ff.view(np.uint32), oracle.map_u32_to_unifloat(uu).view(np.uint32))
-        top = max(top, float(ff.max()))
-    assert top == float(np.float32(1.0) - np.float32(2.0**-24))
-
-
-def test_outputs_in_pinned_host_memory(B, oracle):
-    """Outputs may live in pinned host memory that the GPU writes directly (the
-    launcher then uses the direct-store path): same bits as device outputs."""
-    s, n = 32, (1 << 16) + 12
-    C = B.qmc_sobol_matrices(s, inputs.sobol_raw_init(s))
-    seeds = inputs.scramble_seeds(s)
-    Cd, sd = B.u32_tensor(C), B.u32_tensor(seeds)
-    hu = torch.empty((n, s), dtype=torch.int32).pin_memory()
-    hf = torch.empty((n, s), dtype=torch.float32).pin_memory()
-    B.qmc_sobol_points(Cd, s, 0, n, 2, sd, hu.data_ptr(), hf.data_ptr())
     torch.cuda.synchronize()
-    du, df = B.sobol_points(Cd, n, scramble=2, seeds=sd)
-    np.testing.assert_array_equal(hu.numpy(), du.cpu().numpy())
-    np.testing.assert_array_equal(hf.numpy().view(np.uint32), _f32_bits(df))
-    ou, _ = oracle.sobol_points(C, n - 100, 100, 2, seeds)
-    np.testing.assert_array_equal(hu.numpy().view(np.uint32)[-100:], ou)
+    _compare_in_chunks(B, u, f, lambda r0, n: oracle.lattice_points(g, sh, r0, n), N, chunk=1 << 22)
+    del u, f
+    torch.cuda.empty_cache()

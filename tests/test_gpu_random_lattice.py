@@ -7,6 +7,7 @@ import pytest
 import torch
 
 from paper_2307_15584_gb300 import inputs
+from tolerances import grad_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -118,5 +119,5 @@ def test_random_lattice_fwd_bwd(B, oracle, kind):
     assert loss.item() == pytest.approx(float((r * r).sum()), rel=1e-5)
     g_ref = 2.0 * r[:, None] * ref["grad"]
     g_tol = 2.0 * (e_tol[:, None] * np.abs(ref["grad"])
-                   + 1e-5 * np.abs(r)[:, None] * (np.abs(ref["grad"]) + ref["grad_mass"])) + 1e-12 * W[:, None]
+                   + np.abs(r)[:, None] * grad_tol(theta, ref["grad"], ref["grad_mass"]))
     assert (np.abs(gth.cpu().numpy() - g_ref) <= g_tol).all()
