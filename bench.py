@@ -13,22 +13,25 @@ Also reported in the same JSON line:
   cpu_baseline  the oracle on a bounded sample, on the host's cores (and, inside
                 each extra below, the oracle on a bounded sample of that
                 workload)
-  fused         fused forward+backward of the differentiable integro-
-                approximation (1024x1024 integrals x 4096 samples) against the
-                unfused forward + backward kernels, the batched 1920x1080
-                integration, and the rank-1 lattice Genz integration (fused,
-                and unfused through 4 GiB of materialised points), each in
-                Gsamples/s with its QMC error against the closed-form
-                integrals and its instruction-issue roofline (parity with the
-                fp64 oracle is the GPU test suite's job, not the bench's);
-                and every materialising point generator on the headline shape;
-                and one integral of 16 (2^32 - 1) samples over the elements of
-                a partitioned 64-bit Sobol' sequence
+  fused         (last, a summary; --detail-out FILE writes every figure) the fused
+                forward+backward of the differentiable integro-approximation
+                (1024x1024 integrals x 4096 samples) against the unfused forward
+                + backward kernels, with its estimates' and gradients' errors
+                against the oracle on 1024 of the pixels; the batched 1920x1080
+                integration; the rank-1 lattice Genz integration (fused, and
+                unfused through 4 GiB of materialised points); one integral of
+                16 (2^32 - 1) samples over the elements of a partitioned 64-bit
+                Sobol' sequence -- each in Gsamples/s with its issue roofline
+                (alg_frac: the method's operations per sample; issue_frac: the
+                executed instructions; pipes: per-pipe ncu figures) and the
+                oracle's rate on all host cores and on one core; and every
+                materialising point generator on the headline shape (Gdims/s,
+                fraction of the measured copy bandwidth)
 
 --only {fwd_bwd,batched,lattice,points,partition,samplers} --small runs one extra workload alone at
-a reduced size (for ncu captures); --impl reference times the oracle (the plain
-CPU reference of the same computation) on a bounded sample of the headline
-workload.  Under torchrun every rank materialises its own index window (weak
+a reduced size (for ncu captures; samplers -- the Fig. 1 substitute -- runs only this way);
+--impl reference times the oracle (the plain CPU reference of the same computation) on a
+bounded sample of the headline workload.  Under torchrun every rank materialises its own index window (weak
 scaling, no collective on the data path), or with --plan partition its own
 element of the sequence partitioned by an extra dimension; rank 0 prints the
 line.  The oracle runs only in the cpu_baseline and reference legs.
@@ -66,6 +69,8 @@ def parse():
                     default=None,
                     help="run one extra workload alone (no headline)")
     ap.add_argument("--small", action="store_true", help="reduced integration sizes (profiling)")
+    ap.add_argument("--detail-out", default=None,
+                    help="write every figure of the extra workloads (the JSON line keeps a summary) to this file")
     ap.add_argument("--plan", choices=["window", "partition"], default="window",
                     help="per-rank work: a contiguous index window, or one element of the sequence "
                          "partitioned by its phi_2 dimension across the ranks (Sec. 2.5.1)")
@@ -197,95 +202,144 @@ def profile_traffic(kernel_key: str):
     return _profile_value("traffic.txt", kernel_key, KERNEL_SOURCES[kernel_key])
 
 
+# Operations per sample that the method itself needs in each fused workload (not what the
+# kernel executes): per coordinate of a nested-scrambled Sobol' point about 15 integer
+# operations (the column XOR, the hash steps, the float conversion); the 6-D mixture
+# 4 x (6 FSUB + 6 FFMA) + 4 ex2 and a 4-operation compensated add (146 per sample), its
+# gradient 4 x (6 + 3) more FMAs (182); per lattice coordinate one IMAD, one IADD, one
+# conversion with one brev per point; the product peak 16 x (FADD + FFMA + FMUL) and one
+# reciprocal (98 per sample in all), the oscillatory 16 FFMAs and one cosine (66).  The
+# partitioned workload: 16 nested-scrambled Sobol' coordinates (240) and the product peak.
+ALG_OPS_PER_SAMPLE = {"integrate_main<sobol6,nested,gaussmix,grad>": 182.0,
+                      "integrate_main<sobol6,nested,gaussmix>": 146.0,
+                      "integrate_main<lattice16,product_peak>": 98.0,
+                      "integrate_main<lattice16,oscillatory>": 66.0,
+                      "integrate_main<sobol16,nested,product_peak>": 338.0}
+PIPES = ("alu", "fma", "fmaheavy", "xu")
+
+
+def _profile_row(fname: str, key: str, files):
+    """All numeric fields after the digest of a digest-keyed profile line, or None."""
+    path = os.path.join(ROOT, "profiles", fname)
+    if not os.path.exists(path):
+        return None
+    from paper_2307_15584_gb300.build import source_digest
+
+    digest = source_digest(files)
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == key and parts[1] == digest:
+            return [float(v) for v in parts[2:]]
+    return None
+
+
 def issue_roofline(samples_per_s: float, key: str, sm_mhz):
-    """Instruction-issue roofline of a fused integration kernel: thread-instructions
-    per sample (ncu, committed in profiles/inst_per_sample.txt) x samples/s against
-    SMs x schedulers x 32 lanes x SM clock."""
+    """Instruction-issue roofline of a fused integration kernel against SMs x schedulers x
+    32 lanes x SM clock, two ways: `alg_frac` counts the method's own operations per sample
+    (ALG_OPS_PER_SAMPLE), `frac` the thread-instructions the kernel executes per sample
+    (ncu, profiles/inst_per_sample.txt); `pipes` = the fraction of each pipe's peak the
+    kernel kept busy (ncu, profiles/pipes.txt)."""
     ips = _profile_value("inst_per_sample.txt", key, integrate_sources(key))
     clock = sm_mhz or measured_peaks()["sm_max_mhz"]
     peak = SMS * SCHEDULERS_PER_SM * WARP * clock * 1e6 / 1e9  # Ginst/s
-    if ips is None:
-        return {"bound": "alu", "achieved": None, "peak": peak, "unit": "Ginst/s", "frac": None,
-                "inst_per_sample": None, "kernel": key}
-    achieved = samples_per_s * ips / 1e9
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Ginst/s", "frac": achieved / peak,
-            "inst_per_sample": ips, "kernel": key, "clock_mhz": clock}
+    alg = ALG_OPS_PER_SAMPLE[key]
+    out = {"bound": "alu", "peak": peak, "unit": "Ginst/s", "kernel": key, "clock_mhz": clock,
+           "alg_ops_per_sample": alg, "alg_achieved": samples_per_s * alg / 1e9,
+           "alg_frac": samples_per_s * alg / 1e9 / peak, "inst_per_sample": ips,
+           "achieved": None if ips is None else samples_per_s * ips / 1e9,
+           "frac": None if ips is None else samples_per_s * ips / 1e9 / peak}
+    pipes = _profile_row("pipes.txt", key, integrate_sources(key))
+    out["pipes"] = None if pipes is None else dict(zip(PIPES, pipes))
+    return out
 
 
 # ------------------------------------------------------------------ oracle baseline
+def _oracle_rates(run, units: float, unit: str, sample: str, one_core_fraction: int = 16) -> dict:
+    """The oracle as it stands on a bounded sample: run(k, threads) computes the sample's
+    first 1/k of the units on `threads` host threads.  Timed once on every host core
+    (`value`, `cores`) and once on a single core over 1/one_core_fraction of the units
+    (`value_1core`)."""
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    res = run(1, threads)
+    dt = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    run(one_core_fraction, 1)
+    d1 = time.perf_counter() - t1
+    out = {"value": units / dt / 1e9, "unit": unit, "cores": threads, "kind": "oracle", "sample": sample,
+           "seconds": dt, "value_1core": units / one_core_fraction / d1 / 1e9,
+           "sample_1core": f"the first 1/{one_core_fraction} of it on one core", "seconds_1core": d1}
+    return out if res is None else {**out, "_result": res}
+
+
 def cpu_baseline(n_rows: int = 1 << 23):
     import oracle
     from paper_2307_15584_gb300 import inputs
 
     C = oracle.sobol_matrices(S_DIMS, inputs.sobol_raw_init(S_DIMS))
     seeds = inputs.scramble_seeds(S_DIMS)
-    threads = os.cpu_count() or 1
-    oracle.sobol_points(C, 0, 1024, oracle.SCRAMBLE_NESTED, seeds, threads=threads)
-    t0 = time.perf_counter()
-    oracle.sobol_points(C, 0, n_rows, oracle.SCRAMBLE_NESTED, seeds, threads=threads)
-    dt = time.perf_counter() - t0
-    return {"value": n_rows * S_DIMS / dt / 1e9, "unit": "Gdims/s", "cores": threads, "kind": "oracle",
-            "sample": f"{n_rows} points x {S_DIMS} dims (nested scramble, u32+fp32) of the 2^24-point workload",
-            "seconds": dt}
-
-
-def _oracle_rate(fn, units: float, unit: str, sample: str, threads: int) -> dict:
-    t0 = time.perf_counter()
-    fn()
-    dt = time.perf_counter() - t0
-    return {"value": units / dt / 1e9, "unit": unit, "cores": threads, "kind": "oracle", "sample": sample,
-            "seconds": dt}
+    oracle.sobol_points(C, 0, 1024, oracle.SCRAMBLE_NESTED, seeds)
+    return _oracle_rates(lambda k, t: oracle.sobol_points(C, 0, n_rows // k, oracle.SCRAMBLE_NESTED, seeds,
+                                                         threads=t) and None,
+                         n_rows * S_DIMS, "Gdims/s",
+                         f"{n_rows} points x {S_DIMS} dims (nested scramble, u32+fp32) of the 2^24-point workload")
 
 
 def extras_cpu_baselines(names) -> dict:
     """The oracle as it stands on a bounded sample of each extra workload (the same
-    inputs, seeds and shapes; a fraction of the units), on the host's cores: the
-    CPU figure beside each GPU figure.  About 10 s in all on 16 cores."""
+    inputs, seeds and shapes; a fraction of the units), on all host cores and on one
+    core: the CPU figures beside each GPU figure.  About 20 s in all on 16 cores.  The
+    fused forward+backward sample keeps the oracle's results, to state the GPU's
+    errors against them."""
     import oracle
     from paper_2307_15584_gb300 import inputs
 
-    threads = os.cpu_count() or 1
     out = {}
     if "fwd_bwd" in names:  # config 5: 1024 of the 2^20 pixels x 4096 samples, estimate and gradient
         n = 1024
         C6 = oracle.sobol_matrices(6, inputs.sobol_raw_init(6))
         th, sd = inputs.gaussmix_theta(1 << 20)[:n], inputs.pixel_seeds(n, 6)
-        out["fwd_bwd"] = _oracle_rate(
-            lambda: oracle.integrate(oracle.SOURCE_SOBOL, oracle.F_GAUSSMIX4_6D, 6, np.full(n, 4096, np.uint32), th,
-                                     C=C6, scramble=oracle.SCRAMBLE_NESTED, seeds=sd, with_grad=True,
-                                     threads=threads),
-            n * 4096.0, "Gsamples/s", f"{n} of the 2^20 pixels x 4096 samples, estimate + gradient", threads)
+        out["fwd_bwd"] = _oracle_rates(
+            lambda k, t: oracle.integrate(oracle.SOURCE_SOBOL, oracle.F_GAUSSMIX4_6D, 6,
+                                          np.full(n // k, 4096, np.uint32), th[:n // k], C=C6,
+                                          scramble=oracle.SCRAMBLE_NESTED, seeds=sd[:n // k], with_grad=True,
+                                          threads=t),
+            n * 4096.0, "Gsamples/s", f"{n} of the 2^20 pixels x 4096 samples, estimate + gradient")
     if "batched" in names:  # config 4: the first 1024 of the 1920x1080 pixels, their log-uniform counts
         n = 1024
         counts = inputs.log_uniform_counts(1920 * 1080)[:n]
         C6 = oracle.sobol_matrices(6, inputs.sobol_raw_init(6))
         th, sd = inputs.gaussmix_theta(1920 * 1080, seed=7)[:n], inputs.pixel_seeds(n, 6, seed=7)
-        out["batched"] = _oracle_rate(
-            lambda: oracle.integrate(oracle.SOURCE_SOBOL, oracle.F_GAUSSMIX4_6D, 6, counts, th, C=C6,
-                                     scramble=oracle.SCRAMBLE_NESTED, seeds=sd, threads=threads),
+        k1 = 16
+        out["batched"] = _oracle_rates(
+            lambda k, t: oracle.integrate(oracle.SOURCE_SOBOL, oracle.F_GAUSSMIX4_6D, 6, counts[:n // k], th[:n // k],
+                                          C=C6, scramble=oracle.SCRAMBLE_NESTED, seeds=sd[:n // k], threads=t) and None,
             float(counts.sum()), "Gsamples/s", f"the first {n} of the 1920x1080 pixels ({int(counts.sum())} samples)",
-            threads)
+            one_core_fraction=k1)
+        # the single-core sample's own sample count: the first n / k1 pixels' counts
+        out["batched"]["value_1core"] *= float(counts[:n // k1].sum()) / (float(counts.sum()) / k1)
     if "lattice" in names:  # config 3: 4 integrals x 2^20 of the 2^26 points, per family
         s, N = 16, 1 << 20
         g, sh = inputs.lattice_generator(s), inputs.lattice_shift(s)
         res = {}
         for fam, kind in (("product_peak", oracle.F_GENZ_PRODUCT_PEAK), ("oscillatory", oracle.F_GENZ_OSCILLATORY)):
             th = np.stack([inputs.genz_params(fam, s, k) for k in range(4)])
-            res[fam] = _oracle_rate(
-                lambda: oracle.integrate(oracle.SOURCE_LATTICE, kind, s, np.full(4, N, np.uint32), th, g=g, seeds=sh,
-                                         threads=threads),
-                4.0 * N, "Gsamples/s", "4 integrals x 2^20 of the 2^26 points", threads)
+            res[fam] = _oracle_rates(
+                lambda k, t, th=th, kind=kind: oracle.integrate(oracle.SOURCE_LATTICE, kind, s,
+                                                                np.full(4, N // k, np.uint32), th, g=g, seeds=sh,
+                                                                threads=t) and None,
+                4.0 * N, "Gsamples/s", "4 integrals x 2^20 of the 2^26 points")
         out["lattice"] = res
     if "partition" in names:  # the 16 elements x 2^16 of their 2^32 - 1 samples
         s, q, n = 16, 4, 1 << 16
         W = oracle.sobol_matrices_wide(s + 1, 64, inputs.sobol_raw_init(s + 1))
         th = inputs.genz_params("product_peak", s, 0)
-        out["partition"] = _oracle_rate(
-            lambda: oracle.integrate_partitioned(oracle.F_GENZ_PRODUCT_PEAK, s, np.full(16, n, np.uint32),
-                                                 np.tile(th, (16, 1)), W, q, np.arange(16),
-                                                 scramble=oracle.SCRAMBLE_NESTED, seeds=inputs.scramble_seeds(s),
-                                                 threads=threads),
-            16.0 * n, "Gsamples/s", "the 16 elements x 2^16 of their 2^32 - 1 samples", threads)
+        out["partition"] = _oracle_rates(
+            lambda k, t: oracle.integrate_partitioned(oracle.F_GENZ_PRODUCT_PEAK, s, np.full(16, n // k, np.uint32),
+                                                      np.tile(th, (16, 1)), W, q, np.arange(16),
+                                                      scramble=oracle.SCRAMBLE_NESTED,
+                                                      seeds=inputs.scramble_seeds(s), threads=t) and None,
+            16.0 * n, "Gsamples/s", "the 16 elements x 2^16 of their 2^32 - 1 samples")
     if "points" in names:  # every generator on s = 32, 2^10 .. 2^20 rows (about half a second each)
         s, n, nl = S_DIMS, 1 << 18, 1 << 10
         nb = 1 << 20
@@ -295,37 +349,100 @@ def extras_cpu_baselines(names) -> dict:
         g, sh = inputs.lattice_generator(s), inputs.lattice_shift(s)
         nested = oracle.SCRAMBLE_NESTED
         runs = {
-            "sobol32_nested": (n, lambda: oracle.sobol_points(C, 0, n, nested, sd, threads=threads)),
-            "sobol32_nested_from_index_1": (n, lambda: oracle.sobol_points(C, 1, n, nested, sd, threads=threads)),
-            "sobol64_nested_at_2^40": (n, lambda: oracle.sobol_points_wide(W[:s], 1 << 40, n, nested, sd,
-                                                                           threads=threads)),
-            "sobol64_partition_p5_of_8": (n, lambda: oracle.sobol_points_partitioned(W, 3, 5, 1 << 37, n, nested, sd,
-                                                                                     threads=threads)),
-            "lattice_shifted": (nb, lambda: oracle.lattice_points(g, sh, 0, nb, threads=threads)),
-            "lattice_shifted_from_index_1": (nb, lambda: oracle.lattice_points(g, sh, 1, nb, threads=threads)),
-            "halton_faure": (nl, lambda: oracle.halton_points(s, 0, nl, oracle.HALTON_FAURE, threads=threads)),
-            "halton_faure_partition_p5_of_8": (n, lambda: oracle.halton_points_partitioned(
-                s, 3, 5, 1 << 30, n, oracle.HALTON_FAURE, threads=threads)),
-            "pixel_lattice_16spp": (8 * nl, lambda: oracle.pixel_lattice_points(g, 1024, nl // 2, 16, height=1024)),
-            "random_lattice_hash_x4_16spp": (nb, lambda: oracle.random_lattice_points(
-                oracle.RLAT_HASH, 7, 4, s, 1024, nb // 16, 16, threads=threads)),
-            "random_lattice_lfsr_x4_16spp": (n // 4, lambda: oracle.random_lattice_points(
-                oracle.RLAT_LFSR, 7, 4, s, 1024, n // 64, 16, threads=threads)),
+            "sobol32_nested": (n, lambda r, t: oracle.sobol_points(C, 0, r, nested, sd, threads=t)),
+            "sobol32_nested_from_index_1": (n, lambda r, t: oracle.sobol_points(C, 1, r, nested, sd, threads=t)),
+            "sobol64_nested_at_2^40": (n, lambda r, t: oracle.sobol_points_wide(W[:s], 1 << 40, r, nested, sd,
+                                                                                threads=t)),
+            "sobol64_partition_p5_of_8": (n, lambda r, t: oracle.sobol_points_partitioned(W, 3, 5, 1 << 37, r, nested,
+                                                                                          sd, threads=t)),
+            "lattice_shifted": (nb, lambda r, t: oracle.lattice_points(g, sh, 0, r, threads=t)),
+            "lattice_shifted_from_index_1": (nb, lambda r, t: oracle.lattice_points(g, sh, 1, r, threads=t)),
+            "halton_faure": (nl, lambda r, t: oracle.halton_points(s, 0, r, oracle.HALTON_FAURE, threads=t)),
+            "halton_faure_partition_p5_of_8": (n, lambda r, t: oracle.halton_points_partitioned(
+                s, 3, 5, 1 << 30, r, oracle.HALTON_FAURE, threads=t)),
+            "pixel_lattice_16spp": (8 * nl, lambda r, t: oracle.pixel_lattice_points(g, 1024, r // 16, 16,
+                                                                                     height=1024)),
+            "random_lattice_hash_x4_16spp": (nb, lambda r, t: oracle.random_lattice_points(
+                oracle.RLAT_HASH, 7, 4, s, 1024, r // 16, 16, threads=t)),
+            "random_lattice_lfsr_x4_16spp": (n // 4, lambda r, t: oracle.random_lattice_points(
+                oracle.RLAT_LFSR, 7, 4, s, 1024, r // 16, 16, threads=t)),
         }
-        out["points"] = {name: _oracle_rate(fn, rows * s, "Gdims/s", f"{rows} rows x {s} dims", threads)
+        out["points"] = {name: _oracle_rates(lambda k, t, rows=rows, fn=fn: fn(rows // k, t) and None, rows * s,
+                                             "Gdims/s", f"{rows} rows x {s} dims")
                          for name, (rows, fn) in runs.items()}
     return out
 
 
 def attach_cpu_baselines(extras: dict, base: dict) -> None:
-    """Put each oracle figure beside the GPU figure it samples."""
+    """Put each oracle figure beside the GPU figure it samples (results the oracle kept
+    for an error statement stay out of the figure)."""
     for name, b in base.items():
         if name in ("lattice", "points"):
             for k, v in b.items():
                 if k in extras[name]:
                     extras[name][k]["cpu_baseline"] = v
         else:
-            extras[name]["cpu_baseline"] = b
+            extras[name]["cpu_baseline"] = {k: v for k, v in b.items() if not k.startswith("_")}
+
+
+def gradient_errors(gpu: dict, ref: dict, theta: np.ndarray, target: np.ndarray) -> dict:
+    """Errors of the GPU's estimates, gradient means J and fused gradients dtheta
+    against the oracle on the same pixels (theta order w, mu, nu, sigma): the largest
+    relative error of the estimates and of the non-cancelling means (w, sigma: every
+    term >= 0), the largest error relative to |J| + M for the cancelling ones (mu, nu;
+    M = mean |df/dtheta|), and quantiles of |dtheta32 - dtheta64| / |dtheta64|."""
+    e, J, g = gpu["est"], gpu["J"].astype(np.float64), gpu["dtheta"].astype(np.float64)
+    e64, J64, M64 = ref["est"], ref["grad"], ref["grad_mass"]
+    out = {"pixels": int(e.size), "est_max_rel": float(np.max(np.abs(e - e64) / np.abs(e64)))}
+    for name, k in (("w", 0), ("sigma", 3)):
+        out[f"J_{name}_max_rel"] = float(np.max(np.abs(J[:, k::4] - J64[:, k::4]) / np.abs(J64[:, k::4])))
+    for name, k in (("mu", 1), ("nu", 2)):
+        out[f"J_{name}_max_over_J_plus_M"] = float(np.max(np.abs(J[:, k::4] - J64[:, k::4]) /
+                                                          (np.abs(J64[:, k::4]) + M64[:, k::4])))
+    g64 = 2.0 * (e64 - target)[:, None] * J64
+    rel = np.abs(g - g64) / np.abs(g64)
+    out["dtheta_rel_quantiles"] = {q: float(np.quantile(rel, float(q))) for q in ("0.5", "0.99", "1.0")}
+    return out
+
+
+def _r(v, digits=4):
+    return None if v is None else float(f"{v:.{digits}g}")
+
+
+def compact_extras(x: dict) -> dict:
+    """The figures of each extra workload that the one JSON line carries (the full record
+    goes to --detail-out): rates, the roofline fractions, the oracle's rates on all host
+    cores and on one core, and the errors."""
+    def cpu(e):
+        b = e.get("cpu_baseline")
+        return None if not b else [_r(b["value"], 3), _r(b.get("value_1core"), 3)]
+
+    def roof(rf):
+        pipes = rf.get("pipes")
+        return {"alg_frac": _r(rf["alg_frac"], 3), "issue_frac": _r(rf.get("frac"), 3),
+                "pipes": None if pipes is None else {k: _r(v, 2) for k, v in pipes.items()}}
+
+    out = {}
+    if "fwd_bwd" in x:
+        f = x["fwd_bwd"]
+        out["fwd_bwd"] = {"gsamples_s": _r(f["fused_gsamples_s"]), "unfused": _r(f.get("unfused_gsamples_s")),
+                          **roof(f["roofline"]), "oracle": cpu(f), "err_vs_oracle": f.get("errors_vs_oracle")}
+    if "batched" in x:
+        f = x["batched"]
+        out["batched"] = {"gsamples_s": _r(f["gsamples_s"]), **roof(f["roofline"]), "oracle": cpu(f)}
+    if "lattice" in x:
+        for fam in ("product_peak", "oscillatory"):
+            f = x["lattice"][fam]
+            out[f"lattice_{fam}"] = {"gsamples_s": _r(f["gsamples_s"]), "unfused": _r(f.get("unfused_gsamples_s")),
+                                     **roof(f["roofline"]), "oracle": cpu(f)}
+    if "partition" in x:
+        f = x["partition"]
+        out["partition"] = {"gsamples_s": _r(f["gsamples_s"]), **roof(f["roofline"]), "oracle": cpu(f),
+                            "rel_err_vs_exact": _r(f["rel_err_vs_exact"], 2)}
+    if "points" in x:
+        out["points_gdims_s_frac_hbm"] = {k: [_r(v["gdims_s"]), _r(v["frac_hbm"], 3)]
+                                          for k, v in x["points"].items() if isinstance(v, dict)}
+    return out
 
 
 def run_reference(args, world, rank):
@@ -454,6 +571,13 @@ def bench_fwd_bwd(dev, steps, warmup, small, sm_mhz):
     out["parity"] = PARITY_NOTE
     out["roofline"] = issue_roofline(out["fused_gsamples_s"] * 1e9, "integrate_main<sobol6,nested,gaussmix,grad>",
                                      sm_mhz)
+    # the first 1024 pixels' estimates, fused gradients and gradient means J (a backward with
+    # an upstream gradient of 1), for the error statement against the oracle's sample
+    k = 1024
+    B.qmc_integrate_backward(prob, n, d["c"], d["th"], torch.ones(n, dtype=torch.float64, device=dev), gb, ws)
+    torch.cuda.synchronize()
+    out["_gpu_sample"] = {"est": e[:k].copy(), "dtheta": g[:k].copy(), "J": gb[:k].cpu().numpy(),
+                          "theta": theta[:k], "target": target[:k]}
     return out
 
 
@@ -765,7 +889,7 @@ def bench_samplers(dev, steps, warmup, small, sm_mhz):
 
 
 def run_extras(args, dev, sm_mhz):
-    which = [args.only] if args.only else ["fwd_bwd", "batched", "lattice", "points", "partition", "samplers"]
+    which = [args.only] if args.only else ["fwd_bwd", "batched", "lattice", "points", "partition"]
     fns = {"fwd_bwd": bench_fwd_bwd, "batched": bench_batched, "lattice": bench_lattice,
            "points": bench_points, "samplers": bench_samplers, "partition": bench_partition}
     out = {}
@@ -778,6 +902,25 @@ def run_extras(args, dev, sm_mhz):
     return out
 
 
+def finish_extras(extras: dict, with_cpu: bool) -> None:
+    """The oracle's samples beside the GPU figures, and the fused gradient's errors
+    against the oracle's results on its sample of pixels."""
+    base = extras_cpu_baselines(list(extras)) if with_cpu else {}
+    fb = extras.get("fwd_bwd")
+    if fb is not None:
+        gpu = fb.pop("_gpu_sample", None)
+        ref = base.get("fwd_bwd", {}).get("_result")
+        if gpu is not None and ref is not None:
+            fb["errors_vs_oracle"] = gradient_errors(gpu, ref, gpu["theta"], gpu["target"])
+    attach_cpu_baselines(extras, base)
+
+
+def write_detail(path, record) -> None:
+    if path:
+        with open(path, "w") as f:
+            json.dump(record, f, indent=1)
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -788,8 +931,8 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     if args.only:  # one integration workload alone (profiling); no headline line
         res = run_extras(args, dev, None)
-        if not args.no_cpu:
-            attach_cpu_baselines(res, extras_cpu_baselines(list(res)))
+        finish_extras(res, not args.no_cpu)
+        write_detail(args.detail_out, res)
         print(json.dumps({"only": args.only, "small": args.small, **res}), flush=True)
         return
     if world > 1:
@@ -905,21 +1048,20 @@ def run_ours(args, world, rank, local):
                 "ms_copy_back": e2e_copy_ms, "ms_direct_to_host": e2e_direct_ms,
                 "achieved_gbs": (h2d + d2h) / (e2e_ms * 1e-3) / 1e9,
                 "link_gbs": d2h / (link_ms * 1e-3) / 1e9,
-                "link_frac": (link_ms / e2e_ms),
-                "link_note": "link_gbs: the same output bytes copied device to pinned host alone; "
-                             "splitting the copy over 2-8 streams measured the same"},
+                "link_frac": (link_ms / e2e_ms)},
         "gpu_launches": args.steps,
         "clocks": clk,
     }
     del out_u, out_f, h_u, h_f
     torch.cuda.empty_cache()
-    if not args.no_extra:
-        line["fused"] = run_extras(args, dev, clk.get("sm_mhz"))
+    extras = run_extras(args, dev, clk.get("sm_mhz")) if not args.no_extra else None
     if not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline()
-        if not args.no_extra:
-            attach_cpu_baselines(line["fused"], extras_cpu_baselines(list(line["fused"])))
-    print(json.dumps(line), flush=True)
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline().items() if not k.startswith("_")}
+    if extras is not None:
+        finish_extras(extras, not args.no_cpu)
+        write_detail(args.detail_out, {"line": line, "extras": extras})
+        line["fused"] = compact_extras(extras)  # last, so that the end of the output holds it
+    print(json.dumps(line, separators=(",", ":")), flush=True)
     if world > 1:
         dist.destroy_process_group()
 

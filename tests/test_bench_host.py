@@ -55,3 +55,39 @@ def test_committed_profile_figures_match_the_sources():
                 continue
             key, digest, _ = parts
             assert source_digest(bench.profile_sources(fname, key)) == digest, (fname, key)
+
+
+def test_gradient_errors_and_compact_summary():
+    """The bench's error statement: relative errors of the non-cancelling gradient
+    means, errors relative to |J| + M for the cancelling ones; and the summary the
+    JSON line carries keeps every workload's rate and fractions."""
+    import bench
+
+    rng = np.random.default_rng(3)
+    n = 8
+    J64 = rng.uniform(0.1, 1.0, (n, 16))
+    M64 = np.abs(J64) * 3
+    ref = {"est": rng.uniform(0.5, 1.0, n), "grad": J64, "grad_mass": M64}
+    gpu = {"est": ref["est"] * (1 + 1e-7), "J": (J64 * (1 + 2e-7)).astype(np.float32),
+           "dtheta": np.zeros((n, 16), np.float32)}
+    target = ref["est"] - 0.25
+    gpu["dtheta"] = (2 * 0.25 * J64 * (1 + 3e-7)).astype(np.float32)
+    e = bench.gradient_errors(gpu, ref, None, target)
+    assert 0.9e-7 < e["est_max_rel"] < 1.1e-7
+    assert e["J_w_max_rel"] < 3e-7 and e["J_sigma_max_rel"] < 3e-7
+    assert e["J_mu_max_over_J_plus_M"] < 1e-7  # the error over 4 |J|
+    assert e["dtheta_rel_quantiles"]["1.0"] < 5e-7
+    roof = {"alg_frac": 0.61234, "frac": 0.8, "pipes": {"alu": 0.5, "fma": 0.6, "fmaheavy": 0.2, "xu": 0.1}}
+    x = {"fwd_bwd": {"fused_gsamples_s": 142.0, "unfused_gsamples_s": 86.0, "roofline": roof,
+                     "cpu_baseline": {"value": 0.03, "value_1core": 0.002}, "errors_vs_oracle": e},
+         "batched": {"gsamples_s": 217.0, "roofline": roof},
+         "lattice": {"points": 4, "product_peak": {"gsamples_s": 264.0, "roofline": roof},
+                     "oscillatory": {"gsamples_s": 325.0, "roofline": roof}},
+         "partition": {"gsamples_s": 118.0, "roofline": roof, "rel_err_vs_exact": 2.4e-7},
+         "points": {"rows": 8, "sobol32_nested": {"gdims_s": 848.0, "frac_hbm": 1.01}}}
+    c = bench.compact_extras(x)
+    assert c["fwd_bwd"]["gsamples_s"] == 142.0 and c["fwd_bwd"]["alg_frac"] == 0.612
+    assert c["fwd_bwd"]["oracle"] == [0.03, 0.002]
+    assert set(c) == {"fwd_bwd", "batched", "lattice_product_peak", "lattice_oscillatory", "partition",
+                      "points_gdims_s_frac_hbm"}
+    assert c["points_gdims_s_frac_hbm"] == {"sobol32_nested": [848.0, 1.01]}
