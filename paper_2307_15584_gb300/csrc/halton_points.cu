@@ -19,7 +19,9 @@ using namespace pts;
 // partitioned by its base-2 dimension, Sec. 2.5.1) with b the (dim0 + j)-th
 // prime; digits permuted (Faure table or linear multiplier), i' = i mod 2^32
 // for b = 2 (the bit reversal of the low 32 bits), otherwise i mod b^K with b^K
-// the largest power below 2^32 (Alg. 1's domain limit).
+// the largest power below 2^32 (Alg. 1's domain limit).  Base 2 runs the same
+// tables with b^K = 2^32 (K = 32 digits; the scale 2^32 / b^K is then 1), so no
+// lane of a warp takes a path of its own.
 //
 // Multi-digit tables (Sec. 2.2): the K digits of i' are taken in G groups of L
 // digits (the most significant group holding the remaining L' digits), and a
@@ -33,7 +35,7 @@ constexpr uint32_t kHaltonPermWords = 8896;  // sum of the first 64 primes (8893
 constexpr uint32_t kHaltonGroupCap = 1024;   // largest table (b^L) for bases that allow L >= 2
 struct HaltonTables {
   uint32_t base[kHaltonMaxDims];
-  uint32_t max_power[kHaltonMaxDims];  // b^K: the largest power of the base below 2^32
+  uint32_t max_power[kHaltonMaxDims];  // b^K: the largest power of the base below 2^32; 0 for base 2 (2^32)
   uint32_t perm_off[kHaltonMaxDims];   // Faure table of dimension j at perm[perm_off[j]]
   uint32_t digits[kHaltonMaxDims];     // L, digits per full group
   uint32_t groups[kHaltonMaxDims];     // G
@@ -92,7 +94,6 @@ __global__ void __launch_bounds__(kThreads) halton_points_kernel(HaltonArgs p) {
   for (uint32_t jo = 0; jo < p.s; ++jo) {
     const uint32_t j = p.dim0 + jo;
     const uint32_t b = g_halton.base[j];
-    if (b == 2) continue;
     const uint32_t bL = g_halton.group_pow[j], bLp = g_halton.top_pow[j];
     const uint32_t poff = g_halton.perm_off[j];
     uint16_t* t = htab + p.table_off[jo];
@@ -147,27 +148,19 @@ __global__ void __launch_bounds__(kThreads) halton_points_kernel(HaltonArgs p) {
     const uint32_t dofs = k * s;
     uint32_t ofs = 0;
     const uint32_t j = p.dim0 + jo;
-    const uint32_t b = g_halton.base[j];
     const uint64_t i = ((p.index_begin + row) << p.q) | p.pconst;
-    // Base 2 (the bit reversal of the low 32 index bits, which advance by k 2^q mod 2^32)
-    // runs the same loop with a lowest group that never carries, so the warp does not
-    // split into two loops.
-    const bool two = b == 2;
-    uint32_t lo = (uint32_t)i;
-    const uint32_t dlo = (uint32_t)((uint64_t)k << p.q);
-    const uint32_t mp = two ? 1u : g_halton.max_power[j];
-    const uint32_t m0 = two ? 0u : g_halton.recip96[j][0], m1 = two ? 0u : g_halton.recip96[j][1];
-    const uint32_t m2 = two ? 0u : g_halton.recip96[j][2];
-    const uint32_t bL = two ? 0xFFFFFFFFu : g_halton.group_pow[j], bLp = two ? 1u : g_halton.top_pow[j];
-    const uint32_t G = two ? 2u : g_halton.groups[j];
-    const uint64_t mg = two ? 0ull : g_halton.magic_group[j];
+    const uint32_t mp = g_halton.max_power[j];  // 0: base 2, whose b^K is 2^32
+    const uint32_t m0 = g_halton.recip96[j][0], m1 = g_halton.recip96[j][1], m2 = g_halton.recip96[j][2];
+    const uint32_t bL = g_halton.group_pow[j], bLp = g_halton.top_pow[j];
+    const uint32_t G = g_halton.groups[j];
+    const uint64_t mg = g_halton.magic_group[j];
     const uint16_t* tab = htab + p.table_off[jo];
-    const uint32_t x = two ? 0u
-                           : (i >> 32) ? (uint32_t)(i % mp)
-                                       : (uint32_t)i - mp * (uint32_t)__umul64hi((uint32_t)i, g_halton.magic_max[j]);
+    const uint32_t x = mp == 0 ? (uint32_t)i
+                       : (i >> 32) ? (uint32_t)(i % mp)
+                                   : (uint32_t)i - mp * (uint32_t)__umul64hi((uint32_t)i, g_halton.magic_max[j]);
     uint32_t xg[kHaltonMaxGroups], dg[kHaltonMaxGroups], wg[kHaltonMaxGroups];
     halton_groups(x, G, bL, mg, xg);
-    const uint32_t D = two ? 0u : p.delta[jo];  // (k 2^q) mod b^K
+    const uint32_t D = p.delta[jo];  // (k 2^q) mod b^K
     halton_groups(D, G, bL, mg, dg);
     const bool d_hi = D >= bL;  // the step reaches beyond the lowest group
     // weights of the mirrored groups: N = sum_g T_g[x_g] wg[g], the lowest group the most significant
@@ -179,7 +172,7 @@ __global__ void __launch_bounds__(kThreads) halton_points_kernel(HaltonArgs p) {
       else if ((uint32_t)g + 1 < G) wacc *= bL;
     }
     auto entry = [&](int g) -> uint32_t {  // T_g[x_g]: the top group has its own table after the full one
-      return two ? 0u : (uint32_t)tab[(uint32_t)g + 1 == G ? bL + xg[g] : xg[g]];
+      return (uint32_t)tab[(uint32_t)g + 1 == G ? bL + xg[g] : xg[g]];
     };
     auto rest = [&]() {  // the groups above the lowest
       uint32_t r = 0;
@@ -206,12 +199,11 @@ __global__ void __launch_bounds__(kThreads) halton_points_kernel(HaltonArgs p) {
     uint32_t x0 = xg[0];
     const uint32_t d0 = dg[0], w0g = wg[0];
     auto emit = [&]() {  // the current row's coordinate
-      const uint32_t N = nrest + (two ? 0u : (uint32_t)tab[x0]) * w0g;
-      const uint32_t v = two ? __brev(lo) : halton_scale(N, m0, m1, m2);
+      const uint32_t N = nrest + (uint32_t)tab[x0] * w0g;
+      const uint32_t v = halton_scale(N, m0, m1, m2);
       if (p.out_u32) ou[ofs] = v;
       if (p.out_f32) of[ofs] = map_u32_to_unifloat(v);
       ofs += dofs;
-      lo += dlo;
       x0 += d0;
       const bool carry0 = x0 >= bL;
       if (carry0) x0 -= bL;
@@ -297,6 +289,7 @@ static const HaltonTables* halton_host_tables() {
       uint64_t mp = 1;
       uint32_t K = 0;
       while (mp * b <= 0xFFFFFFFFull) mp *= b, ++K;
+      if (b == 2) mp = 1ull << 32, K = 32;  // base 2 keeps all 32 index bits: its b^K is 2^32
       uint32_t L = 1;
       uint64_t bL = b;
       while (bL * b <= kHaltonGroupCap) bL *= b, ++L;
@@ -304,15 +297,16 @@ static const HaltonTables* halton_host_tables() {
       uint64_t bLp = 1;
       for (uint32_t t = 0; t < Lp; ++t) bLp *= b;
       h.base[j] = b;
-      h.max_power[j] = (uint32_t)mp;
+      h.max_power[j] = (uint32_t)mp;  // 0 for base 2
       h.digits[j] = L;
       h.groups[j] = G;
       h.top_digits[j] = Lp;
       h.group_pow[j] = (uint32_t)bL;
       h.top_pow[j] = (uint32_t)bLp;
       h.magic_group[j] = UINT64_MAX / bL + 1;
-      h.magic_max[j] = UINT64_MAX / mp + 1;
-      const unsigned __int128 r96 = ((((unsigned __int128)1) << 96) - 1) / mp + 1;  // mp odd: not a divisor of 2^96
+      h.magic_max[j] = b == 2 ? 0 : UINT64_MAX / mp + 1;  // base 2 takes i mod 2^32 directly
+      // ceil(2^96 / b^K): for odd b^K the quotient's floor plus one; for 2^32 exactly 2^64
+      const unsigned __int128 r96 = ((((unsigned __int128)1) << 96) - 1) / mp + 1;
       h.recip96[j][0] = (uint32_t)r96;
       h.recip96[j][1] = (uint32_t)(r96 >> 32);
       h.recip96[j][2] = (uint32_t)(r96 >> 64);
@@ -354,15 +348,12 @@ cudaError_t launch_halton_points(const HaltonArgs& args, cudaStream_t stream) {
   uint32_t table_words = 0;  // uint16 entries
   for (uint32_t jo = 0; jo < p.s; ++jo) {
     const uint32_t j = p.dim0 + jo;
-    p.table_off[jo] = 0;  // base 2 reads no table; its offset stays inside the buffer all the same
-    p.delta[jo] = 0;
-    if (h.base[j] == 2) continue;
     p.table_off[jo] = table_words;
     if (h.groups[j] < 2) return cudaErrorInvalidValue;  // the lowest group is a full one
     table_words += h.group_pow[j] + h.top_pow[j];
     // the index step of this dimension's lanes: k rows, k = floor(32 / w) for the chunk's width w
     const uint32_t chunk_w = jo < 32 ? (p.s < 32 ? p.s : 32) : p.s - 32;
-    const uint64_t k = 32 / chunk_w, mp = h.max_power[j];
+    const uint64_t k = 32 / chunk_w, mp = h.base[j] == 2 ? 1ull << 32 : h.max_power[j];
     const uint64_t pow2q = (p.q < 64 ? (1ull << p.q) : 0ull) % mp;
     p.delta[jo] = (uint32_t)((k % mp) * pow2q % mp);
   }
