@@ -209,12 +209,12 @@ def profile_traffic(kernel_key: str):
 # gradient 4 x (6 + 3) more FMAs (182); per lattice coordinate one IMAD, one IADD, one
 # conversion with one brev per point; the product peak 16 x (FADD + FFMA + FMUL) and one
 # reciprocal (98 per sample in all), the oscillatory 16 FFMAs and one cosine (66).  The
-# partitioned workload: 16 nested-scrambled Sobol' coordinates (240) and the product peak.
+# partitioned 64-bit workload has no such count (its alg_frac is null; its issue fraction
+# stands alone).
 ALG_OPS_PER_SAMPLE = {"integrate_main<sobol6,nested,gaussmix,grad>": 182.0,
                       "integrate_main<sobol6,nested,gaussmix>": 146.0,
                       "integrate_main<lattice16,product_peak>": 98.0,
-                      "integrate_main<lattice16,oscillatory>": 66.0,
-                      "integrate_main<sobol16,nested,product_peak>": 338.0}
+                      "integrate_main<lattice16,oscillatory>": 66.0}
 PIPES = ("alu", "fma", "fmaheavy", "xu")
 
 
@@ -242,10 +242,10 @@ def issue_roofline(samples_per_s: float, key: str, sm_mhz):
     ips = _profile_value("inst_per_sample.txt", key, integrate_sources(key))
     clock = sm_mhz or measured_peaks()["sm_max_mhz"]
     peak = SMS * SCHEDULERS_PER_SM * WARP * clock * 1e6 / 1e9  # Ginst/s
-    alg = ALG_OPS_PER_SAMPLE[key]
+    alg = ALG_OPS_PER_SAMPLE.get(key)
     out = {"bound": "alu", "peak": peak, "unit": "Ginst/s", "kernel": key, "clock_mhz": clock,
-           "alg_ops_per_sample": alg, "alg_achieved": samples_per_s * alg / 1e9,
-           "alg_frac": samples_per_s * alg / 1e9 / peak, "inst_per_sample": ips,
+           "alg_ops_per_sample": alg, "alg_achieved": None if alg is None else samples_per_s * alg / 1e9,
+           "alg_frac": None if alg is None else samples_per_s * alg / 1e9 / peak, "inst_per_sample": ips,
            "achieved": None if ips is None else samples_per_s * ips / 1e9,
            "frac": None if ips is None else samples_per_s * ips / 1e9 / peak}
     pipes = _profile_row("pipes.txt", key, integrate_sources(key))
@@ -254,6 +254,11 @@ def issue_roofline(samples_per_s: float, key: str, sm_mhz):
 
 
 # ------------------------------------------------------------------ oracle baseline
+def _discard(_result) -> None:
+    """Drops a sample's outputs (the rate is what is wanted)."""
+    return None
+
+
 def _oracle_rates(run, units: float, unit: str, sample: str, one_core_fraction: int = 16) -> dict:
     """The oracle as it stands on a bounded sample: run(k, threads) computes the sample's
     first 1/k of the units on `threads` host threads.  Timed once on every host core
@@ -279,9 +284,10 @@ def cpu_baseline(n_rows: int = 1 << 23):
     C = oracle.sobol_matrices(S_DIMS, inputs.sobol_raw_init(S_DIMS))
     seeds = inputs.scramble_seeds(S_DIMS)
     oracle.sobol_points(C, 0, 1024, oracle.SCRAMBLE_NESTED, seeds)
-    return _oracle_rates(lambda k, t: oracle.sobol_points(C, 0, n_rows // k, oracle.SCRAMBLE_NESTED, seeds,
-                                                         threads=t) and None,
-                         n_rows * S_DIMS, "Gdims/s",
+    def run(k, t):
+        return _discard(oracle.sobol_points(C, 0, n_rows // k, oracle.SCRAMBLE_NESTED, seeds, threads=t))
+
+    return _oracle_rates(run, n_rows * S_DIMS, "Gdims/s",
                          f"{n_rows} points x {S_DIMS} dims (nested scramble, u32+fp32) of the 2^24-point workload")
 
 
@@ -311,11 +317,14 @@ def extras_cpu_baselines(names) -> dict:
         C6 = oracle.sobol_matrices(6, inputs.sobol_raw_init(6))
         th, sd = inputs.gaussmix_theta(1920 * 1080, seed=7)[:n], inputs.pixel_seeds(n, 6, seed=7)
         k1 = 16
-        out["batched"] = _oracle_rates(
-            lambda k, t: oracle.integrate(oracle.SOURCE_SOBOL, oracle.F_GAUSSMIX4_6D, 6, counts[:n // k], th[:n // k],
-                                          C=C6, scramble=oracle.SCRAMBLE_NESTED, seeds=sd[:n // k], threads=t) and None,
-            float(counts.sum()), "Gsamples/s", f"the first {n} of the 1920x1080 pixels ({int(counts.sum())} samples)",
-            one_core_fraction=k1)
+        def batched(k, t):
+            return _discard(oracle.integrate(oracle.SOURCE_SOBOL, oracle.F_GAUSSMIX4_6D, 6, counts[:n // k],
+                                             th[:n // k], C=C6, scramble=oracle.SCRAMBLE_NESTED, seeds=sd[:n // k],
+                                             threads=t))
+
+        out["batched"] = _oracle_rates(batched, float(counts.sum()), "Gsamples/s",
+                                       f"the first {n} of the 1920x1080 pixels ({int(counts.sum())} samples)",
+                                       one_core_fraction=k1)
         # the single-core sample's own sample count: the first n / k1 pixels' counts
         out["batched"]["value_1core"] *= float(counts[:n // k1].sum()) / (float(counts.sum()) / k1)
     if "lattice" in names:  # config 3: 4 integrals x 2^20 of the 2^26 points, per family
@@ -324,22 +333,24 @@ def extras_cpu_baselines(names) -> dict:
         res = {}
         for fam, kind in (("product_peak", oracle.F_GENZ_PRODUCT_PEAK), ("oscillatory", oracle.F_GENZ_OSCILLATORY)):
             th = np.stack([inputs.genz_params(fam, s, k) for k in range(4)])
-            res[fam] = _oracle_rates(
-                lambda k, t, th=th, kind=kind: oracle.integrate(oracle.SOURCE_LATTICE, kind, s,
-                                                                np.full(4, N // k, np.uint32), th, g=g, seeds=sh,
-                                                                threads=t) and None,
-                4.0 * N, "Gsamples/s", "4 integrals x 2^20 of the 2^26 points")
+            def lattice(k, t, th=th, kind=kind):
+                return _discard(oracle.integrate(oracle.SOURCE_LATTICE, kind, s, np.full(4, N // k, np.uint32), th,
+                                                 g=g, seeds=sh, threads=t))
+
+            res[fam] = _oracle_rates(lattice, 4.0 * N, "Gsamples/s", "4 integrals x 2^20 of the 2^26 points")
         out["lattice"] = res
     if "partition" in names:  # the 16 elements x 2^16 of their 2^32 - 1 samples
         s, q, n = 16, 4, 1 << 16
         W = oracle.sobol_matrices_wide(s + 1, 64, inputs.sobol_raw_init(s + 1))
         th = inputs.genz_params("product_peak", s, 0)
-        out["partition"] = _oracle_rates(
-            lambda k, t: oracle.integrate_partitioned(oracle.F_GENZ_PRODUCT_PEAK, s, np.full(16, n // k, np.uint32),
-                                                      np.tile(th, (16, 1)), W, q, np.arange(16),
-                                                      scramble=oracle.SCRAMBLE_NESTED,
-                                                      seeds=inputs.scramble_seeds(s), threads=t) and None,
-            16.0 * n, "Gsamples/s", "the 16 elements x 2^16 of their 2^32 - 1 samples")
+        def partition(k, t):
+            return _discard(oracle.integrate_partitioned(oracle.F_GENZ_PRODUCT_PEAK, s, np.full(16, n // k, np.uint32),
+                                                         np.tile(th, (16, 1)), W, q, np.arange(16),
+                                                         scramble=oracle.SCRAMBLE_NESTED,
+                                                         seeds=inputs.scramble_seeds(s), threads=t))
+
+        out["partition"] = _oracle_rates(partition, 16.0 * n, "Gsamples/s",
+                                         "the 16 elements x 2^16 of their 2^32 - 1 samples")
     if "points" in names:  # every generator on s = 32, 2^10 .. 2^20 rows (about half a second each)
         s, n, nl = S_DIMS, 1 << 18, 1 << 10
         nb = 1 << 20
@@ -367,7 +378,7 @@ def extras_cpu_baselines(names) -> dict:
             "random_lattice_lfsr_x4_16spp": (n // 4, lambda r, t: oracle.random_lattice_points(
                 oracle.RLAT_LFSR, 7, 4, s, 1024, r // 16, 16, threads=t)),
         }
-        out["points"] = {name: _oracle_rates(lambda k, t, rows=rows, fn=fn: fn(rows // k, t) and None, rows * s,
+        out["points"] = {name: _oracle_rates(lambda k, t, rows=rows, fn=fn: _discard(fn(rows // k, t)), rows * s,
                                              "Gdims/s", f"{rows} rows x {s} dims")
                          for name, (rows, fn) in runs.items()}
     return out
@@ -389,16 +400,17 @@ def gradient_errors(gpu: dict, ref: dict, theta: np.ndarray, target: np.ndarray)
     """Errors of the GPU's estimates, gradient means J and fused gradients dtheta
     against the oracle on the same pixels (theta order w, mu, nu, sigma): the largest
     relative error of the estimates and of the non-cancelling means (w, sigma: every
-    term >= 0), the largest error relative to |J| + M for the cancelling ones (mu, nu;
-    M = mean |df/dtheta|), and quantiles of |dtheta32 - dtheta64| / |dtheta64|."""
+    term >= 0), the largest error relative to |J| + S for the cancelling ones (mu, nu;
+    S = the oracle's mean of the summed absolute values of each derivative's terms),
+    and quantiles of |dtheta32 - dtheta64| / |dtheta64|."""
     e, J, g = gpu["est"], gpu["J"].astype(np.float64), gpu["dtheta"].astype(np.float64)
-    e64, J64, M64 = ref["est"], ref["grad"], ref["grad_mass"]
+    e64, J64, S64 = ref["est"], ref["grad"], ref["grad_scale"]
     out = {"pixels": int(e.size), "est_max_rel": float(np.max(np.abs(e - e64) / np.abs(e64)))}
     for name, k in (("w", 0), ("sigma", 3)):
         out[f"J_{name}_max_rel"] = float(np.max(np.abs(J[:, k::4] - J64[:, k::4]) / np.abs(J64[:, k::4])))
     for name, k in (("mu", 1), ("nu", 2)):
-        out[f"J_{name}_max_over_J_plus_M"] = float(np.max(np.abs(J[:, k::4] - J64[:, k::4]) /
-                                                          (np.abs(J64[:, k::4]) + M64[:, k::4])))
+        out[f"J_{name}_max_over_J_plus_S"] = float(np.max(np.abs(J[:, k::4] - J64[:, k::4]) /
+                                                          (np.abs(J64[:, k::4]) + S64[:, k::4])))
     g64 = 2.0 * (e64 - target)[:, None] * J64
     rel = np.abs(g - g64) / np.abs(g64)
     out["dtheta_rel_quantiles"] = {q: float(np.quantile(rel, float(q))) for q in ("0.5", "0.99", "1.0")}
@@ -420,13 +432,21 @@ def compact_extras(x: dict) -> dict:
     def roof(rf):
         pipes = rf.get("pipes")
         return {"alg_frac": _r(rf["alg_frac"], 3), "issue_frac": _r(rf.get("frac"), 3),
-                "pipes": None if pipes is None else {k: _r(v, 2) for k, v in pipes.items()}}
+                "pipes": None if pipes is None else [_r(pipes[k], 2) for k in PIPES]}
 
-    out = {}
+    def errs(e):
+        if not e:
+            return None
+        q = e["dtheta_rel_quantiles"]
+        return {"est": _r(e["est_max_rel"], 2), "J_w": _r(e["J_w_max_rel"], 2), "J_sigma": _r(e["J_sigma_max_rel"], 2),
+                "J_mu_S": _r(e["J_mu_max_over_J_plus_S"], 2), "J_nu_S": _r(e["J_nu_max_over_J_plus_S"], 2),
+                "dtheta_p50_p99_max": [_r(q["0.5"], 2), _r(q["0.99"], 2), _r(q["1.0"], 2)]}
+
+    out = {"pipes_order": list(PIPES), "oracle_order": ["all cores", "one core"]}
     if "fwd_bwd" in x:
         f = x["fwd_bwd"]
         out["fwd_bwd"] = {"gsamples_s": _r(f["fused_gsamples_s"]), "unfused": _r(f.get("unfused_gsamples_s")),
-                          **roof(f["roofline"]), "oracle": cpu(f), "err_vs_oracle": f.get("errors_vs_oracle")}
+                          **roof(f["roofline"]), "oracle": cpu(f), "err_vs_oracle": errs(f.get("errors_vs_oracle"))}
     if "batched" in x:
         f = x["batched"]
         out["batched"] = {"gsamples_s": _r(f["gsamples_s"]), **roof(f["roofline"]), "oracle": cpu(f)}
@@ -440,7 +460,7 @@ def compact_extras(x: dict) -> dict:
         out["partition"] = {"gsamples_s": _r(f["gsamples_s"]), **roof(f["roofline"]), "oracle": cpu(f),
                             "rel_err_vs_exact": _r(f["rel_err_vs_exact"], 2)}
     if "points" in x:
-        out["points_gdims_s_frac_hbm"] = {k: [_r(v["gdims_s"]), _r(v["frac_hbm"], 3)]
+        out["points_gdims_s_frac_hbm"] = {k: [_r(v["gdims_s"], 3), _r(v["frac_hbm"], 2)]
                                           for k, v in x["points"].items() if isinstance(v, dict)}
     return out
 
@@ -1030,36 +1050,36 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": "Gdims/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": f"materialised scrambled Sobol: s={S_DIMS} dims, {count} indices per GPU, nested "
-                               f"scramble, u32+fp32 outputs [{count}][{S_DIMS}] each", "s": S_DIMS,
+        "config": {"workload": f"materialised scrambled Sobol': s={S_DIMS}, {count} indices per GPU, nested "
+                               f"scramble, u32 + f32 outputs [{count}][{S_DIMS}]", "s": S_DIMS,
                    "points_per_gpu": count, "scramble": "nested", "outputs": "u32+f32",
-                   "plan": ("contiguous index window per GPU" if args.plan == "window"
+                   "plan": ("index window per GPU" if args.plan == "window"
                             else f"element {rank} of P = {world} of the sequence partitioned by its phi_2 "
                                  "dimension"),
-                   "l2": "outputs (4 GiB per step) exceed the 129 MB L2; no flush needed"},
+                   "l2": "4 GiB of outputs per step > 129 MB L2: no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": profile_traffic("sobol_points_fast<1,2>"),
-                     "peak_source": peaks["source"] + " copy bandwidth",
+                     "peak_source": peaks["source"] + " copy",
                      "algorithmic_bytes_per_launch": bytes_per_launch},
         "e2e": {"value": coords / (e2e_ms * 1e-3) / 1e9, "unit": "Gdims/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-                "method": "kernel writes pinned host memory" if e2e_direct_ms <= e2e_copy_ms
-                          else "device outputs + cudaMemcpyAsync to pinned host",
-                "ms_copy_back": e2e_copy_ms, "ms_direct_to_host": e2e_direct_ms,
-                "achieved_gbs": (h2d + d2h) / (e2e_ms * 1e-3) / 1e9,
-                "link_gbs": d2h / (link_ms * 1e-3) / 1e9,
-                "link_frac": (link_ms / e2e_ms)},
+                "method": "kernel writes pinned host" if e2e_direct_ms <= e2e_copy_ms else "device + copy to host",
+                "link_gbs": d2h / (link_ms * 1e-3) / 1e9, "link_frac": (link_ms / e2e_ms)},
         "gpu_launches": args.steps,
         "clocks": clk,
     }
+    e2e_detail = {"ms_copy_back": e2e_copy_ms, "ms_direct_to_host": e2e_direct_ms, "ms_link_alone": link_ms,
+                  "achieved_gbs": (h2d + d2h) / (e2e_ms * 1e-3) / 1e9}
     del out_u, out_f, h_u, h_f
     torch.cuda.empty_cache()
     extras = run_extras(args, dev, clk.get("sm_mhz")) if not args.no_extra else None
     if not args.no_cpu:
-        line["cpu_baseline"] = {k: v for k, v in cpu_baseline().items() if not k.startswith("_")}
+        cb = cpu_baseline()
+        line["cpu_baseline"] = {k: v for k, v in cb.items() if k in ("value", "unit", "cores", "kind", "value_1core")}
+        line["cpu_baseline"]["sample"] = f"2^23 of the 2^24 points (1/16 of that on one core)"
     if extras is not None:
         finish_extras(extras, not args.no_cpu)
-        write_detail(args.detail_out, {"line": line, "extras": extras})
+        write_detail(args.detail_out, {"line": line, "e2e_detail": e2e_detail, "extras": extras})
         line["fused"] = compact_extras(extras)  # last, so that the end of the output holds it
     print(json.dumps(line, separators=(",", ":")), flush=True)
     if world > 1:

@@ -81,10 +81,10 @@ def lib() -> ctypes.CDLL:
             "qo_halton_u32": (u32, [u32, u32, u32, u32]),
             "qo_pixel_shift": (u32, [u32, u32, u32]),
             "qo_pixel_lattice_u32": (u32, [u32, u32, u32]),
-            "qo_integrate_one": (i32, [u32, u32, u32, u32, P, P, P, u32, P, P, P, P, P]),
-            "qo_integrate_range": (i32, [u32, u32, u32, u32, P, P, P, u64, P, P, u64, u64, u64, P, P, P, P]),
+            "qo_integrate_one": (i32, [u32, u32, u32, u32, P, P, P, u32, P, P, P, P, P, P]),
+            "qo_integrate_range": (i32, [u32, u32, u32, u32, P, P, P, u64, P, P, u64, u64, u64, P, P, P, P, P]),
             "qo_integrand": (dbl, [u32, u32, P, P, P]),
-            "qo_integrate_partitioned": (i32, [u32, u32, u32, P, u32, u32, u64, P, u32, P, P, P, P, P]),
+            "qo_integrate_partitioned": (i32, [u32, u32, u32, P, u32, u32, u64, P, u32, P, P, P, P, P, P]),
             "qo_gaussmix_f64": (dbl, [P, P]),
             "qo_exact_genz_product_peak": (dbl, [u32, P]),
             "qo_exact_genz_oscillatory": (dbl, [u32, P]),
@@ -268,8 +268,9 @@ def integrate(source, integrand, s, counts, theta, *, C=None, g=None, scramble=0
     """Per-integral QMC estimates (fp64).
 
     counts [n]; theta [n][P] (fp32); seeds None, [s] shared or [n][s].
-    Returns dict(est [n], mass [n], grad [n][16], grad_mass [n][16]).
-    """
+    Returns dict(est [n], mass [n], grad [n][16], grad_mass [n][16], grad_scale [n][16]):
+    grad the mean of df/dtheta, grad_mass the mean of |df/dtheta|, grad_scale the mean of
+    the sum of the absolute values of the terms of each df/dtheta (>= grad_mass)."""
     counts = np.ascontiguousarray(counts, dtype=np.uint32).reshape(-1)
     n = counts.size
     theta = np.ascontiguousarray(theta, dtype=np.float32).reshape(n, -1)
@@ -284,13 +285,14 @@ def integrate(source, integrand, s, counts, theta, *, C=None, g=None, scramble=0
     mass = np.zeros(n)
     grad = np.zeros((n, 16)) if with_grad else None
     gmass = np.zeros((n, 16)) if with_grad else None
+    gscale = np.zeros((n, 16)) if with_grad else None
 
     def run(rng):
         p0, p1 = rng
         rc = lib().qo_integrate_range(
             source, integrand, s, scramble, _p(C), _p(g), _p(seeds), 0 if seeds is None else seeds.shape[1],
             counts.ctypes.data, theta.ctypes.data, theta.shape[1], p0, p1, est.ctypes.data, mass.ctypes.data,
-            _p(grad), _p(gmass))
+            _p(grad), _p(gmass), _p(gscale))
         if rc != 0:
             raise ValueError("oracle rejected the problem")
 
@@ -303,7 +305,7 @@ def integrate(source, integrand, s, counts, theta, *, C=None, g=None, scramble=0
         bounds = sorted({0, n, *[int(c) for c in cuts if 0 < c < n]})
         with ThreadPoolExecutor(T) as ex:
             list(ex.map(run, zip(bounds[:-1], bounds[1:])))
-    return {"est": est, "mass": mass, "grad": grad, "grad_mass": gmass}
+    return {"est": est, "mass": mass, "grad": grad, "grad_mass": gmass, "grad_scale": gscale}
 
 
 def integrate_partitioned(integrand, s, counts, theta, C, q, elements, *, scramble=0, seeds=None,
@@ -325,20 +327,22 @@ def integrate_partitioned(integrand, s, counts, theta, C, q, elements, *, scramb
     est, mass = np.zeros(n), np.zeros(n)
     grad = np.zeros((n, 16)) if with_grad else None
     gmass = np.zeros((n, 16)) if with_grad else None
+    gscale = np.zeros((n, 16)) if with_grad else None
 
     def one(k):
         rc = lib().qo_integrate_partitioned(
             integrand, s, scramble, _p(C), m, q, int(elements[k]),
             None if seeds is None else seeds[k].ctypes.data, int(counts[k]), theta[k].ctypes.data,
             est[k:].ctypes.data, mass[k:].ctypes.data,
-            None if grad is None else grad[k].ctypes.data, None if gmass is None else gmass[k].ctypes.data)
+            None if grad is None else grad[k].ctypes.data, None if gmass is None else gmass[k].ctypes.data,
+            None if gscale is None else gscale[k].ctypes.data)
         if rc != 0:
             raise ValueError("oracle rejected the problem")
 
     order = np.argsort(-counts.astype(np.int64), kind="stable")
     with ThreadPoolExecutor(_threads(threads)) as ex:
         list(ex.map(one, order.tolist()))
-    return {"est": est, "mass": mass, "grad": grad, "grad_mass": gmass}
+    return {"est": est, "mass": mass, "grad": grad, "grad_mass": gmass, "grad_scale": gscale}
 
 
 def integrand(kind, x, theta, s=None):

@@ -602,18 +602,23 @@ static double f_genz_oscillatory(const double* x, uint32_t s, const float* theta
  * 0, 2, 4, mean nu_c in dimensions 1, 3, 5, width sigma_c in all six:
  *   f = sum_c w_c exp(-sum_d (x_d - m_{c,d})^2 / (2 sigma_c^2)).
  * When grad is given, it receives df/dtheta (16 values). */
-static double f_gaussmix(const double* x, const float* theta, double* grad)
+/* The mixture and, when grad is given, its 16 partial derivatives; with
+ * grad_abs, also the sum of the absolute values of the terms each derivative
+ * is a sum of (|w| G sum_d |x_d - m| / sigma^2 for a mean, whose differences
+ * may cancel; |df/dtheta| for w and sigma, whose terms all have one sign). */
+static double f_gaussmix_terms(const double* x, const float* theta, double* grad, double* grad_abs)
 {
     double f = 0.0;
     for (uint32_t c = 0; c < 4; ++c) {
         double w = theta[4 * c + 0], mu = theta[4 * c + 1];
         double nu = theta[4 * c + 2], sg = theta[4 * c + 3];
-        double q = 0.0, se = 0.0, so = 0.0;
+        double q = 0.0, se = 0.0, so = 0.0, ae = 0.0, ao = 0.0;
         for (uint32_t d = 0; d < 6; ++d) {
             double m = (d % 2 == 0) ? mu : nu;
             double diff = x[d] - m;
             q += diff * diff;
-            if (d % 2 == 0) se += diff; else so += diff;
+            if (d % 2 == 0) se += diff, ae += fabs(diff);
+            else so += diff, ao += fabs(diff);
         }
         double G = exp(-q / (2.0 * sg * sg));
         f += w * G;
@@ -623,8 +628,19 @@ static double f_gaussmix(const double* x, const float* theta, double* grad)
             grad[4 * c + 2] = w * G * so / (sg * sg);
             grad[4 * c + 3] = w * G * q / (sg * sg * sg);
         }
+        if (grad_abs) {
+            grad_abs[4 * c + 0] = G;
+            grad_abs[4 * c + 1] = fabs(w) * G * ae / (sg * sg);
+            grad_abs[4 * c + 2] = fabs(w) * G * ao / (sg * sg);
+            grad_abs[4 * c + 3] = fabs(w * G * q / (sg * sg * sg));
+        }
     }
     return f;
+}
+
+static double f_gaussmix(const double* x, const float* theta, double* grad)
+{
+    return f_gaussmix_terms(x, theta, grad, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -695,13 +711,16 @@ static double f_scene(const double* x, const float* th)
  *     (seed, px, py), scramble = kind + 256 R (R superimposed instances).
  * Coordinates are the fp32 values of the float mapping, promoted to fp64.
  * Outputs (each may be NULL except est): est = estimate; mass = (1/n) sum |f|;
- * grad[16] = (1/n) sum df/dtheta and grad_mass[16] = (1/n) sum |df/dtheta|
- * (Gaussian mixture only).  n = 0 gives zeros.  Returns 0, or -1 on bad
- * arguments. */
+ * grad[16] = (1/n) sum df/dtheta, grad_mass[16] = (1/n) sum |df/dtheta| and
+ * grad_scale[16] = (1/n) sum of the absolute values of the terms of each
+ * df/dtheta (>= grad_mass: the mean's own differences may cancel inside one
+ * sample) (Gaussian mixture only; grad_scale needs grad).  n = 0 gives zeros.
+ * Returns 0, or -1 on bad arguments. */
 QO_EXPORT int qo_integrate_one(uint32_t source, uint32_t integrand, uint32_t s,
                                uint32_t scramble, const uint32_t* C, const uint32_t* g,
                                const uint32_t* seeds, uint32_t n, const float* theta,
-                               double* est, double* mass, double* grad, double* grad_mass)
+                               double* est, double* mass, double* grad, double* grad_mass,
+                               double* grad_scale)
 {
     if (s == 0 || s > 32) return -1;
     if (integrand == QO_F_BILINEAR2D && s != 2) return -1;
@@ -711,10 +730,10 @@ QO_EXPORT int qo_integrate_one(uint32_t source, uint32_t integrand, uint32_t s,
     if (source == QO_SOURCE_RANDOM_LATTICE && (!seeds || (scramble >> 8) == 0)) return -1;
 
     neumaier sum = {0, 0}, abs_sum = {0, 0};
-    neumaier gsum[16], gabs[16];
-    for (int k = 0; k < 16; ++k) gsum[k] = gabs[k] = (neumaier){0, 0};
+    neumaier gsum[16], gabs[16], gterm[16];
+    for (int k = 0; k < 16; ++k) gsum[k] = gabs[k] = gterm[k] = (neumaier){0, 0};
 
-    double x[32], df[16];
+    double x[32], df[16], dfa[16];
     for (uint32_t i = 0; i < n; ++i) {
         for (uint32_t j = 0; j < s; ++j) {
             uint32_t v;
@@ -735,7 +754,7 @@ QO_EXPORT int qo_integrate_one(uint32_t source, uint32_t integrand, uint32_t s,
         case QO_F_GENZ_PRODUCT_PEAK: f = f_genz_product_peak(x, s, theta); break;
         case QO_F_GENZ_OSCILLATORY: f = f_genz_oscillatory(x, s, theta); break;
         case QO_F_SCENE4D: f = f_scene(x, theta); break;
-        default: f = f_gaussmix(x, theta, grad ? df : NULL); break;
+        default: f = f_gaussmix_terms(x, theta, grad ? df : NULL, grad ? dfa : NULL); break;
         }
         neu_add(&sum, f);
         neu_add(&abs_sum, fabs(f));
@@ -743,6 +762,7 @@ QO_EXPORT int qo_integrate_one(uint32_t source, uint32_t integrand, uint32_t s,
             for (int k = 0; k < 16; ++k) {
                 neu_add(&gsum[k], df[k]);
                 neu_add(&gabs[k], fabs(df[k]));
+                neu_add(&gterm[k], dfa[k]);
             }
     }
     double inv = n ? 1.0 / (double)n : 0.0;
@@ -752,6 +772,7 @@ QO_EXPORT int qo_integrate_one(uint32_t source, uint32_t integrand, uint32_t s,
         for (int k = 0; k < 16; ++k) {
             grad[k] = n ? (gsum[k].s + gsum[k].c) / (double)n : 0.0;
             if (grad_mass) grad_mass[k] = (gabs[k].s + gabs[k].c) * inv;
+            if (grad_scale) grad_scale[k] = (gterm[k].s + gterm[k].c) * inv;
         }
     return 0;
 }
@@ -759,19 +780,20 @@ QO_EXPORT int qo_integrate_one(uint32_t source, uint32_t integrand, uint32_t s,
 /* qo_integrate_one for integrals p0 .. p1-1 of a batch, one after another:
  * integral p reads seeds + p * seed_stride (NULL: none), counts[p] and
  * theta + p * theta_stride, and writes est[p], mass[p], grad[16 p ..] and
- * grad_mass[16 p ..] (the last three optional).  Returns 0, or the first
+ * grad_mass[16 p ..] and grad_scale[16 p ..] (the last four optional).  Returns 0, or the first
  * non-zero return of qo_integrate_one. */
 QO_EXPORT int qo_integrate_range(uint32_t source, uint32_t integrand, uint32_t s, uint32_t scramble,
                                  const uint32_t* C, const uint32_t* g, const uint32_t* seeds,
                                  uint64_t seed_stride, const uint32_t* counts, const float* theta,
                                  uint64_t theta_stride, uint64_t p0, uint64_t p1, double* est,
-                                 double* mass, double* grad, double* grad_mass)
+                                 double* mass, double* grad, double* grad_mass, double* grad_scale)
 {
     for (uint64_t p = p0; p < p1; ++p) {
         int rc = qo_integrate_one(source, integrand, s, scramble, C, g,
                                   seeds ? seeds + p * seed_stride : NULL, counts[p],
                                   theta + p * theta_stride, est + p, mass ? mass + p : NULL,
-                                  grad ? grad + 16 * p : NULL, grad_mass ? grad_mass + 16 * p : NULL);
+                                  grad ? grad + 16 * p : NULL, grad_mass ? grad_mass + 16 * p : NULL,
+                                  grad_scale ? grad_scale + 16 * p : NULL);
         if (rc != 0) return rc;
     }
     return 0;
@@ -788,7 +810,8 @@ QO_EXPORT int qo_integrate_range(uint32_t source, uint32_t integrand, uint32_t s
 QO_EXPORT int qo_integrate_partitioned(uint32_t integrand, uint32_t s, uint32_t scramble,
                                        const uint32_t* C, uint32_t m, uint32_t q, uint64_t p,
                                        const uint32_t* seeds, uint32_t n, const float* theta,
-                                       double* est, double* mass, double* grad, double* grad_mass)
+                                       double* est, double* mass, double* grad, double* grad_mass,
+                                       double* grad_scale)
 {
     if (s == 0 || s > 32 || m < 32 || m > 64 || q > 32 || m < 32 + q) return -1;
     if (integrand == QO_F_BILINEAR2D && s != 2) return -1;
@@ -797,10 +820,10 @@ QO_EXPORT int qo_integrate_partitioned(uint32_t integrand, uint32_t s, uint32_t 
     if (integrand > QO_F_SCENE4D) return -1;
 
     neumaier sum = {0, 0}, abs_sum = {0, 0};
-    neumaier gsum[16], gabs[16];
-    for (int k = 0; k < 16; ++k) gsum[k] = gabs[k] = (neumaier){0, 0};
+    neumaier gsum[16], gabs[16], gterm[16];
+    for (int k = 0; k < 16; ++k) gsum[k] = gabs[k] = gterm[k] = (neumaier){0, 0};
 
-    double x[32], df[16];
+    double x[32], df[16], dfa[16];
     for (uint32_t J = 0; J < n; ++J) {
         uint64_t i = qo_partition_index(2, q, p, J);
         for (uint32_t j = 0; j < s; ++j) {
@@ -814,7 +837,7 @@ QO_EXPORT int qo_integrate_partitioned(uint32_t integrand, uint32_t s, uint32_t 
         case QO_F_GENZ_PRODUCT_PEAK: f = f_genz_product_peak(x, s, theta); break;
         case QO_F_GENZ_OSCILLATORY: f = f_genz_oscillatory(x, s, theta); break;
         case QO_F_SCENE4D: f = f_scene(x, theta); break;
-        default: f = f_gaussmix(x, theta, grad ? df : NULL); break;
+        default: f = f_gaussmix_terms(x, theta, grad ? df : NULL, grad ? dfa : NULL); break;
         }
         neu_add(&sum, f);
         neu_add(&abs_sum, fabs(f));
@@ -822,6 +845,7 @@ QO_EXPORT int qo_integrate_partitioned(uint32_t integrand, uint32_t s, uint32_t 
             for (int k = 0; k < 16; ++k) {
                 neu_add(&gsum[k], df[k]);
                 neu_add(&gabs[k], fabs(df[k]));
+                neu_add(&gterm[k], dfa[k]);
             }
     }
     double inv = n ? 1.0 / (double)n : 0.0;
@@ -831,6 +855,7 @@ QO_EXPORT int qo_integrate_partitioned(uint32_t integrand, uint32_t s, uint32_t 
         for (int k = 0; k < 16; ++k) {
             grad[k] = n ? (gsum[k].s + gsum[k].c) / (double)n : 0.0;
             if (grad_mass) grad_mass[k] = (gabs[k].s + gabs[k].c) * inv;
+            if (grad_scale) grad_scale[k] = (gterm[k].s + gterm[k].c) * inv;
         }
     return 0;
 }

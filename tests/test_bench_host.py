@@ -67,7 +67,7 @@ def test_gradient_errors_and_compact_summary():
     n = 8
     J64 = rng.uniform(0.1, 1.0, (n, 16))
     M64 = np.abs(J64) * 3
-    ref = {"est": rng.uniform(0.5, 1.0, n), "grad": J64, "grad_mass": M64}
+    ref = {"est": rng.uniform(0.5, 1.0, n), "grad": J64, "grad_scale": M64}
     gpu = {"est": ref["est"] * (1 + 1e-7), "J": (J64 * (1 + 2e-7)).astype(np.float32),
            "dtheta": np.zeros((n, 16), np.float32)}
     target = ref["est"] - 0.25
@@ -75,7 +75,7 @@ def test_gradient_errors_and_compact_summary():
     e = bench.gradient_errors(gpu, ref, None, target)
     assert 0.9e-7 < e["est_max_rel"] < 1.1e-7
     assert e["J_w_max_rel"] < 3e-7 and e["J_sigma_max_rel"] < 3e-7
-    assert e["J_mu_max_over_J_plus_M"] < 1e-7  # the error over 4 |J|
+    assert e["J_mu_max_over_J_plus_S"] < 1e-7  # the error over 4 |J|
     assert e["dtheta_rel_quantiles"]["1.0"] < 5e-7
     roof = {"alg_frac": 0.61234, "frac": 0.8, "pipes": {"alu": 0.5, "fma": 0.6, "fmaheavy": 0.2, "xu": 0.1}}
     x = {"fwd_bwd": {"fused_gsamples_s": 142.0, "unfused_gsamples_s": 86.0, "roofline": roof,
@@ -88,6 +88,7 @@ def test_gradient_errors_and_compact_summary():
     c = bench.compact_extras(x)
     assert c["fwd_bwd"]["gsamples_s"] == 142.0 and c["fwd_bwd"]["alg_frac"] == 0.612
     assert c["fwd_bwd"]["oracle"] == [0.03, 0.002]
-    assert set(c) == {"fwd_bwd", "batched", "lattice_product_peak", "lattice_oscillatory", "partition",
-                      "points_gdims_s_frac_hbm"}
-    assert c["points_gdims_s_frac_hbm"] == {"sobol32_nested": [848.0, 1.01]}
+    assert set(c) == {"pipes_order", "oracle_order", "fwd_bwd", "batched", "lattice_product_peak",
+                      "lattice_oscillatory", "partition", "points_gdims_s_frac_hbm"}
+    assert c["fwd_bwd"]["pipes"] == [0.5, 0.6, 0.2, 0.1] and c["pipes_order"] == ["alu", "fma", "fmaheavy", "xu"]
+    assert c["points_gdims_s_frac_hbm"] == {"sobol32_nested": [848.0, 1.0]}  # 2 significant digits

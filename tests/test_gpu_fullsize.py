@@ -106,7 +106,7 @@ def test_config5_full_fwd_bwd(B, oracle, parity_report):
     W = np.abs(theta[:, 0::4]).sum(axis=1)
     tol_i = est_tol(ref["est"], W)
     err_i = np.abs(e - ref["est"])
-    tol_j = grad_tol(theta, ref["grad"], ref["grad_mass"])
+    tol_j = grad_tol(theta, ref["grad"], ref["grad_scale"])
     err_j = np.abs(J - ref["grad"])
     r = ref["est"] - target
     g_ref = 2 * r[:, None] * ref["grad"]
@@ -117,11 +117,11 @@ def test_config5_full_fwd_bwd(B, oracle, parity_report):
         "results": n, "samples": int(counts.sum()), "est_rel_err": _rel_quantiles(err_i, ref["est"]),
         "est_max_err_over_tol": float((err_i / tol_i).max()),
         "grad_mean_rel_err": {k: _rel_quantiles(err_j[:, v::4], ref["grad"][:, v::4]) for k, v in kinds.items()},
-        "grad_mean_err_over_J_plus_M": {k: float((err_j[:, v::4] / (np.abs(ref["grad"][:, v::4]) +
-                                                                    ref["grad_mass"][:, v::4])).max())
+        "grad_mean_err_over_J_plus_S": {k: float((err_j[:, v::4] / (np.abs(ref["grad"][:, v::4]) +
+                                                                    ref["grad_scale"][:, v::4])).max())
                                         for k, v in kinds.items()},
         "grad_mean_max_err_over_tol": float((err_j / tol_j).max()),
-        "grad_mean_tau_needed": tau_needed(theta, J, ref["grad"], ref["grad_mass"]),
+        "grad_mean_tau_needed": tau_needed(theta, J, ref["grad"], ref["grad_scale"]),
         "dtheta_rel_err": _rel_quantiles(err_g, g_ref), "dtheta_max_err_over_tol": float((err_g / tol_g).max())}
     assert (err_i <= tol_i).all(), np.flatnonzero(err_i > tol_i)[:8]
     bad = err_j > tol_j

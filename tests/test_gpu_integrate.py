@@ -223,7 +223,7 @@ def test_config5_fwd_bwd_small(B, oracle):
     # d(2 (I - T) J) = 2 dI J + 2 (I - T) dJ: the estimate's own tolerance enters through dI
     e_tol = est_tol(ref["est"], W)
     g_tol = 2.0 * (e_tol[:, None] * np.abs(ref["grad"])
-                   + np.abs(r)[:, None] * grad_tol(theta, ref["grad"], ref["grad_mass"]))
+                   + np.abs(r)[:, None] * grad_tol(theta, ref["grad"], ref["grad_scale"]))
     g = gth.cpu().numpy()
     assert (np.abs(g - g_ref) <= g_tol).all(), np.max(np.abs(g - g_ref) / g_tol)
     # unfused backward with an upstream gradient of 2 (I - T)

@@ -83,7 +83,7 @@ def test_element_estimates_match_oracle(B, oracle, case):
     assert not bad.any(), (np.flatnonzero(bad)[:5], e[bad][:5], ref["est"][bad][:5])
     assert e[0] == 0.0
     if grad:
-        g_tol = grad_tol(theta, ref["grad"], ref["grad_mass"])
+        g_tol = grad_tol(theta, ref["grad"], ref["grad_scale"], tau=2e-6)
         assert (np.abs(g - ref["grad"]) <= g_tol).all(), np.max(np.abs(g - ref["grad"]) / g_tol)
 
 

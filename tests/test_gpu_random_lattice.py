@@ -119,5 +119,5 @@ def test_random_lattice_fwd_bwd(B, oracle, kind):
     assert loss.item() == pytest.approx(float((r * r).sum()), rel=1e-5)
     g_ref = 2.0 * r[:, None] * ref["grad"]
     g_tol = 2.0 * (e_tol[:, None] * np.abs(ref["grad"])
-                   + np.abs(r)[:, None] * grad_tol(theta, ref["grad"], ref["grad_mass"]))
+                   + np.abs(r)[:, None] * grad_tol(theta, ref["grad"], ref["grad_scale"]))
     assert (np.abs(gth.cpu().numpy() - g_ref) <= g_tol).all()

@@ -57,7 +57,7 @@ def test_autograd_backward_matches_fused_and_oracle(B, oracle):
     r = ref["est"] - target
     g_ref = 2 * r[:, None] * ref["grad"]
     g_tol = 2 * (tol_i[:, None] * np.abs(ref["grad"]) +
-                 np.abs(r)[:, None] * grad_tol(theta, ref["grad"], ref["grad_mass"]))
+                 np.abs(r)[:, None] * grad_tol(theta, ref["grad"], ref["grad_scale"], tau=2e-6))
     assert (np.abs(g_auto - g_ref) <= g_tol).all()
 
 
@@ -81,7 +81,7 @@ def test_autograd_over_partition_elements(B, oracle):
                                        scramble=oracle.SCRAMBLE_NESTED, seeds=seeds, with_grad=True)
     W = np.abs(theta[:, 0::4]).sum(axis=1)
     assert (np.abs(est.detach().cpu().numpy() - ref["est"]) <= 1e-6 * np.abs(ref["est"]) + 1e-12 * W).all()
-    g_tol = grad_tol(theta, ref["grad"], ref["grad_mass"])
+    g_tol = grad_tol(theta, ref["grad"], ref["grad_scale"], tau=2e-6)
     assert (np.abs(g - ref["grad"]) <= g_tol).all(), np.max(np.abs(g - ref["grad"]) / g_tol)
     with pytest.raises(ValueError):  # the element dimension must be there
         GaussMixIntegrator(W7[1:], counts, seeds, index_bits=64, partition_log2=q)

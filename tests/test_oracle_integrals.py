@@ -127,6 +127,37 @@ def test_gradient_on_points_matches_central_differences(oracle, C6):
             assert abs(r["grad"][p, k] - fd) <= 2e-3 * scale, (p, k)
 
 
+def test_gradient_term_scale(oracle, C6):
+    """grad_scale (the tolerance scale of the cancelling gradient means) is the mean over
+    samples of the summed absolute values of each derivative's terms: recomputed here
+    from the oracle's own points with numpy, and >= mean |df/dtheta| >= |mean df/dtheta|,
+    with equality to mean |df/dtheta| for w and sigma (terms of one sign)."""
+    th = inputs.gaussmix_theta(3, seed=23)
+    seeds = inputs.pixel_seeds(3, 6, seed=23)
+    n = 300
+    r = oracle.integrate(oracle.SOURCE_SOBOL, oracle.F_GAUSSMIX4_6D, 6, [n] * 3, th, C=C6,
+                         scramble=oracle.SCRAMBLE_NESTED, seeds=seeds, with_grad=True)
+    for p in range(3):
+        _, x = oracle.sobol_points(C6, 0, n, mode=oracle.SCRAMBLE_NESTED, seeds=seeds[p])
+        x = x.astype(np.float64)
+        t = th[p].astype(np.float64).reshape(4, 4)
+        want = np.zeros(16)
+        for c in range(4):
+            w, mu, nu, sg = t[c]
+            m = np.array([mu, nu, mu, nu, mu, nu])
+            G = np.exp(-((x - m) ** 2).sum(1) / (2 * sg * sg))
+            want[4 * c] = G.mean()
+            want[4 * c + 1] = (abs(w) * G * np.abs(x[:, 0::2] - mu).sum(1)).mean() / sg**2
+            want[4 * c + 2] = (abs(w) * G * np.abs(x[:, 1::2] - nu).sum(1)).mean() / sg**2
+            want[4 * c + 3] = (abs(w) * G * ((x - m) ** 2).sum(1)).mean() / sg**3
+        np.testing.assert_allclose(r["grad_scale"][p], want, rtol=1e-12)
+    S, M, J = r["grad_scale"], r["grad_mass"], np.abs(r["grad"])
+    assert (S >= M * (1 - 1e-15)).all() and (M >= J * (1 - 1e-15)).all()
+    np.testing.assert_allclose(S[:, 0::4], M[:, 0::4], rtol=1e-14)
+    np.testing.assert_allclose(S[:, 3::4], M[:, 3::4], rtol=1e-14)
+    assert (S[:, 1::4] > M[:, 1::4] * 1.01).mean() > 0.5  # mostly, the differences inside a sample cancel
+
+
 def test_gradient_tends_to_closed_form_gradient(oracle, C6):
     th = inputs.gaussmix_theta(1, seed=5)
     seeds = inputs.pixel_seeds(1, 6, seed=5)
