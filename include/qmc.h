@@ -562,6 +562,22 @@ QMC_API qmc_status qmc_integrate_static(const qmc_problem* p, uint32_t n_integra
                                         const uint32_t* d_counts, const float* d_theta,
                                         double* d_estimate, qmc_stream_t stream);
 
+/*
+ * The checked build (libqmc_gb300_checked.so, compiled with QMC_CHECKED=1; the
+ * binding loads it when QMC_CHECKED=1 is set in the environment).  Every store of
+ * a point kernel and every per-item and per-integral store of the integration
+ * kernels tests its element offset against the extent the host validated; an
+ * offset outside it skips the store and sets a bit of a device error word:
+ *   1  a point kernel's store beyond count x s elements
+ *   2  an integration work item beyond the workspace's capacity
+ * qmc_checked_error synchronises the device, returns the word in *h_bits and,
+ * with reset = 1, clears it.  The normal build returns QMC_ERR_UNSUPPORTED (and
+ * *h_bits = 0).  Test hook: QMC_CHECK_SLACK=k makes the checked build treat every
+ * point output as k elements shorter, so the last stores of a launch are skipped
+ * and reported without any access outside the buffers.
+ */
+QMC_API qmc_status qmc_checked_error(uint32_t* h_bits, uint32_t reset);
+
 /* In-kernel error bits of the last integration that used this workspace
  * (0 = none; bit 0: more work items than the workspace holds).  Synchronises
  * `stream`. */

@@ -15,7 +15,8 @@ import numpy as np
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libqmc_gb300.so")
+CHECKED = os.environ.get("QMC_CHECKED") == "1"  # the checked build: bounds-tested stores (include/qmc.h)
+LIB_PATH = os.path.join(_PKG, "libqmc_gb300_checked.so" if CHECKED else "libqmc_gb300.so")
 if not os.path.exists(LIB_PATH):
     raise RuntimeError(
         f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`; "
@@ -42,7 +43,7 @@ EXPORTED = ["qmc_abi_version", "qmc_status_string", "qmc_sobol_matrices", "qmc_s
             "qmc_pixel_lattice_points", "qmc_halton_points", "qmc_sobol_matrices_wide",
             "qmc_sobol_points_wide", "qmc_sobol_points_partitioned", "qmc_halton_points_partitioned",
             "qmc_random_lattice_points", "qmc_last_cuda_error", "qmc_tune_save", "qmc_tune_load",
-            "qmc_tune_lookup"]
+            "qmc_tune_lookup", "qmc_checked_error"]
 HALTON_PLAIN, HALTON_FAURE, HALTON_LINEAR = 0, 1, 2
 
 
@@ -102,6 +103,7 @@ _sigs = {
     "qmc_tune_lookup": (ctypes.c_int, [ctypes.POINTER(qmc_problem), c_uint32, c_uint32,
                                        ctypes.POINTER(qmc_tuning)]),
     "qmc_last_cuda_error": (ctypes.c_int, []),
+    "qmc_checked_error": (ctypes.c_int, [ctypes.POINTER(c_uint32), c_uint32]),
     "qmc_graph_begin": (ctypes.c_int, [_P]),
     "qmc_graph_end": (ctypes.c_int, [_P, ctypes.POINTER(c_void_p)]),
     "qmc_graph_launch": (ctypes.c_int, [c_void_p, _P]),
@@ -325,6 +327,13 @@ def qmc_graph_launch(graph: int, stream=None) -> None:
 
 def qmc_graph_destroy(graph: int) -> None:
     _check(_lib.qmc_graph_destroy(graph), "qmc_graph_destroy")
+
+
+def qmc_checked_error(reset=False) -> int:
+    """The checked build's error bits (synchronises the device); QMCError(6) in the normal build."""
+    bits = c_uint32(0)
+    _check(_lib.qmc_checked_error(ctypes.byref(bits), int(bool(reset))), "qmc_checked_error")
+    return bits.value
 
 
 def qmc_read_device_error(workspace, stream=None) -> int:

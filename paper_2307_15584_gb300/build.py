@@ -1,5 +1,6 @@
-"""Build libqmc_gb300.so in-tree: one nvcc process per translation unit (in
-parallel), sm_103a only, then a shared link against the shared CUDA runtime."""
+"""Build libqmc_gb300.so (and its checked build libqmc_gb300_checked.so) in-tree: one
+nvcc process per translation unit (all in parallel), sm_103a only, then a shared link
+against the shared CUDA runtime."""
 from __future__ import annotations
 
 import glob
@@ -45,42 +46,60 @@ def source_digest(files: list[str] | None = None) -> str:
     return h.hexdigest()[:12]
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+LIB_CHECKED = os.path.join(PKG, "libqmc_gb300_checked.so")
+
+
+def _deps() -> list[str]:
+    return sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + [HEADER]
+
+
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + [HEADER]
-    return any(os.path.getmtime(d) > t for d in deps)
+    t = os.path.getmtime(lib)
+    return any(os.path.getmtime(d) > t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    """Compile every CUDA source of the package; returns the library path."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    nvcc = _nvcc()
-    flags = ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-             "-I", os.path.join(ROOT, "include"), *(extra_flags or [])]
+def _compile(build_dir: str, flags: list[str], verbose: bool):
+    """Starts one nvcc per translation unit; returns (objects, [(source, process)])."""
+    os.makedirs(build_dir, exist_ok=True)
     procs, objs = [], []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmd = [nvcc, *flags, "-c", src, "-o", obj]
+        cmd = [_nvcc(), *flags, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    return objs, procs
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
+          checked: bool = True) -> str:
+    """Compile every CUDA source of the package into libqmc_gb300.so and, with `checked`,
+    into the checked build libqmc_gb300_checked.so (-DQMC_CHECKED=1: bounds-tested stores),
+    all translation units of both in parallel; returns the normal library's path."""
+    flags = ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+             "-I", os.path.join(ROOT, "include"), *(extra_flags or [])]
+    jobs = []
+    if force or _stale(LIB):
+        jobs.append((LIB, *_compile(BUILD, flags, verbose)))
+    if checked and (force or _stale(LIB_CHECKED)):
+        jobs.append((LIB_CHECKED, *_compile(BUILD + "_checked", flags + ["-DQMC_CHECKED=1"], verbose)))
     failed = []
-    for src, p in procs:
-        out, _ = p.communicate()
-        if p.returncode != 0:
-            failed.append(f"{src}:\n{out.decode(errors='replace')}")
-        elif verbose and out:
-            print(out.decode(errors="replace"), file=sys.stderr)
+    for _, _, procs in jobs:
+        for src, p in procs:
+            out, _ = p.communicate()
+            if p.returncode != 0:
+                failed.append(f"{src}:\n{out.decode(errors='replace')}")
+            elif verbose and out:
+                print(out.decode(errors="replace"), file=sys.stderr)
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
-    tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
+    for lib, objs, _ in jobs:
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.check_call([_nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs])
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -39,14 +39,38 @@ const DeviceInfo& device_info() {
   return cache.back();
 }
 
+// The checked build's error word (qmc_checked_error); unused in the normal build.
+__device__ uint32_t g_check_word;
+
 namespace {
 thread_local int t_last_cuda_error = 0;
+
+// Device address of g_check_word on the current device (null on failure).
+uint32_t* check_word_address() {
+  static std::mutex mu;
+  static void* addr[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev] && cudaGetSymbolAddress(&addr[dev], g_check_word) != cudaSuccess) {
+    cudaGetLastError();
+    addr[dev] = nullptr;
+  }
+  return static_cast<uint32_t*>(addr[dev]);
+}
 
 nvtxDomainHandle_t nvtx_domain() {
   static const nvtxDomainHandle_t d = nvtxDomainCreateA("qmc");
   return d;
 }
 }  // namespace
+
+CheckCtx check_ctx(uint64_t limit) {
+  if (!kChecked) return CheckCtx{nullptr, limit};
+  const char* v = std::getenv("QMC_CHECK_SLACK");  // test hook: pretend the outputs end earlier
+  const uint64_t slack = v ? std::strtoull(v, nullptr, 10) : 0;
+  return CheckCtx{check_word_address(), limit > slack ? limit - slack : 0};
+}
 
 qmc_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return QMC_OK;
@@ -262,6 +286,7 @@ qmc_status qmc_sobol_points(const uint32_t* d_matrices, uint32_t s, uint64_t ind
   a.index_begin = index_begin;
   a.m = 32;
   a.scramble = scramble;
+  a.chk = check_ctx(count * s);
   return enqueue("qmc_sobol_points", [&] { return launch_sobol_points(a, (cudaStream_t)stream); });
 }
 
@@ -285,6 +310,7 @@ qmc_status qmc_sobol_points_wide(const uint32_t* d_matrices, uint32_t m, uint32_
   a.s = s;
   a.m = m;
   a.scramble = scramble;
+  a.chk = check_ctx(count * s);
   return enqueue("qmc_sobol_points_wide", [&] { return launch_sobol_points(a, (cudaStream_t)stream); });
 }
 
@@ -311,6 +337,7 @@ qmc_status qmc_sobol_points_partitioned(const uint32_t* d_matrices, uint32_t m, 
   a.m = m;
   a.col0 = q;
   a.scramble = scramble;
+  a.chk = check_ctx(count * s);
   return enqueue("qmc_sobol_points_partitioned",
                  [&] { return launch_sobol_points(a, (cudaStream_t)stream); });
 }
@@ -346,6 +373,7 @@ qmc_status qmc_halton_points(uint32_t s, uint32_t mode, const uint32_t* h_multip
   a.out_f32 = d_out_f32;
   a.count = count;
   a.index_begin = index_begin;
+  a.chk = check_ctx(count * s);
   return enqueue("qmc_halton_points", [&] { return launch_halton_points(a, (cudaStream_t)stream); });
 }
 
@@ -365,6 +393,7 @@ qmc_status qmc_halton_points_partitioned(uint32_t s, uint32_t mode, const uint32
   a.index_begin = j_begin;
   a.q = q;
   a.pconst = reverse_bits(p, q);
+  a.chk = check_ctx(count * s);
   return enqueue("qmc_halton_points_partitioned",
                  [&] { return launch_halton_points(a, (cudaStream_t)stream); });
 }
@@ -393,6 +422,7 @@ qmc_status qmc_pixel_lattice_points(const uint32_t* d_g, uint32_t s, uint32_t im
   const uint32_t side = image_width > image_height ? image_width : image_height;
   while (((uint64_t)1 << k) < side) ++k;
   a.grid_log2 = k;
+  a.chk = check_ctx(n_pixels * spp * s);
   return enqueue("qmc_pixel_lattice_points",
                  [&] { return launch_pixel_lattice_points(a, (cudaStream_t)stream); });
 }
@@ -412,6 +442,7 @@ qmc_status qmc_lattice_points(const uint32_t* d_g, const uint32_t* d_shift, uint
   a.s = s;
   a.index_begin = index_begin;
   a.scramble = flags;
+  a.chk = check_ctx(count * s);
   return enqueue("qmc_lattice_points", [&] { return launch_lattice_points(a, (cudaStream_t)stream); });
 }
 
@@ -557,6 +588,7 @@ qmc_status prepare(const qmc_problem* p, uint32_t n, const uint32_t* d_counts, c
   a.ws_loss_terms = reinterpret_cast<double*>(base + L.loss_terms);
   a.partials = reinterpret_cast<float*>(base + L.partials);
   a.capacity_items = capacity;
+  a.check_word = check_ctx(0).word;
   (void)L.row_off;
   out.block = block ? block : kDefaultBlock;
   return QMC_OK;
@@ -588,6 +620,7 @@ qmc_status qmc_random_lattice_points(uint32_t kind, uint32_t seed, uint32_t inst
   a.kind = kind;
   a.seed = seed;
   a.r_log2 = ilog2(instances);
+  a.chk = check_ctx(n_pixels * spp * s);
   return enqueue("qmc_random_lattice_points",
                  [&] { return launch_random_lattice_points(a, (cudaStream_t)stream); });
 }
@@ -671,6 +704,18 @@ qmc_status qmc_integrate_points(const qmc_problem* p, uint32_t n_integrals,
   pr.a.estimate = d_estimate;
   return enqueue("qmc_integrate_points",
                  [&] { return launch_integrate(pr.a, pr.block, false, (cudaStream_t)stream); });
+}
+
+qmc_status qmc_checked_error(uint32_t* h_bits, uint32_t reset) {
+  if (!h_bits || reset > 1) return QMC_ERR_INVALID_ARG;
+  *h_bits = 0;
+  if (!kChecked) return QMC_ERR_UNSUPPORTED;
+  uint32_t* word = check_word_address();
+  if (!word) return cuda_status(cudaErrorInvalidSymbol);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(h_bits, word, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && reset) e = cudaMemset(word, 0, sizeof(uint32_t));
+  return cuda_status(e);
 }
 
 qmc_status qmc_read_device_error(const void* d_workspace, uint32_t* h_error_bits,

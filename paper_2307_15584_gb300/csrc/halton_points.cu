@@ -201,8 +201,10 @@ __global__ void __launch_bounds__(kThreads) halton_points_kernel(HaltonArgs p) {
     auto emit = [&]() {  // the current row's coordinate
       const uint32_t N = nrest + (uint32_t)tab[x0] * w0g;
       const uint32_t v = halton_scale(N, m0, m1, m2);
-      if (p.out_u32) ou[ofs] = v;
-      if (p.out_f32) of[ofs] = map_u32_to_unifloat(v);
+      if (in_bounds(p.chk, off0 + ofs, 1, kCheckPoints)) {
+        if (p.out_u32) ou[ofs] = v;
+        if (p.out_f32) of[ofs] = map_u32_to_unifloat(v);
+      }
       ofs += dofs;
       x0 += d0;
       const bool carry0 = x0 >= bL;

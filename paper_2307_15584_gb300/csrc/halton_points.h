@@ -6,6 +6,8 @@
 
 #include <cstdint>
 
+#include "qmc_checked.cuh"
+
 namespace qmc {
 
 // Radical inversion in prime bases (Sec. 2.2).  The per-base constants (the
@@ -25,6 +27,7 @@ struct HaltonArgs {
   // set by the launcher
   uint32_t table_off[kHaltonMaxDims];  // output dimension jo's digit-group tables in shared memory
   uint32_t delta[kHaltonMaxDims];      // (k 2^q) mod b^K: the index step of the lanes of dimension jo
+  CheckCtx chk;                        // checked build: the output extent count * s and the error word
 };
 
 // Enqueues the Halton kernel; writes the device table first if this device has

@@ -176,7 +176,9 @@ __global__ void __launch_bounds__(256) reduce_forward(IntegrateArgs a) {
   }
   const uint32_t b = a.item_off[p], e = a.item_off[p + 1];
   Comp acc{0.0f, 0.0f};
-  for (uint32_t it = b + lane; it < e; it += 32) acc = comp_merge(acc, comp_load(a.partials + 2 * (size_t)it));
+  const bool items_ok = in_bounds(CheckCtx{a.check_word, a.capacity_items}, b, e - b, kCheckPartials);
+  if (items_ok)
+    for (uint32_t it = b + lane; it < e; it += 32) acc = comp_merge(acc, comp_load(a.partials + 2 * (size_t)it));
   acc = warp_comp_sum(acc);
   if (lane == 0) {
     const uint32_t n_p = a.counts[p];
@@ -203,7 +205,8 @@ __global__ void __launch_bounds__(256) reduce_grad(IntegrateArgs a) {
   }
   const uint32_t b = a.item_off[p], e = a.item_off[p + 1];
   Comp acc{0.0f, 0.0f};
-  if (lane < 17)
+  const bool items_ok = in_bounds(CheckCtx{a.check_word, a.capacity_items}, b, e - b, kCheckPartials);
+  if (items_ok && lane < 17)
     for (uint32_t it = b; it < e; ++it) acc = comp_merge(acc, comp_load(a.partials + (size_t)it * 34 + 2 * lane));
   const uint32_t n_p = a.counts[p];
   float scale = 0.0f;

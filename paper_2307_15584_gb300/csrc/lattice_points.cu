@@ -61,13 +61,13 @@ __global__ void __launch_bounds__(kThreads) lattice_points_fast(PointsArgs a) {
         if (TMA)
           stager.put(lane, c, v);
         else
-          store4(a.out_u32, a.out_f32, o, v);
+          store4(a.out_u32, a.out_f32, o, v, a.chk);
       } else {  // ragged last group: per-element row test
         const uint64_t rows_left = a.count - (g << a.q_log2);
         const uint32_t e0 = 4u * (lane + 32u * c);
 #pragma unroll
         for (int t = 0; t < 4; ++t)
-          if ((uint64_t)((e0 + t) / s) < rows_left) store1(a.out_u32, a.out_f32, o + t, v[t]);
+          if ((uint64_t)((e0 + t) / s) < rows_left) store1(a.out_u32, a.out_f32, o + t, v[t], a.chk);
       }
     }
     if (TMA && g < full_groups)
@@ -110,11 +110,11 @@ __global__ void __launch_bounds__(kThreads) lattice_points_flat(PointsArgs a) {
         v[t] = BACKWARD ? sh - g - phi * g : phi * g + sh;  // phi_2(~k) = ~phi_2(k)
       }
       if (e + 4u <= total) {
-        store4(a.out_u32, a.out_f32, off0 + e, v);
+        store4(a.out_u32, a.out_f32, off0 + e, v, a.chk);
       } else {
 #pragma unroll
         for (int t = 0; t < 4; ++t)
-          if (e + t < total) store1(a.out_u32, a.out_f32, off0 + e + t, v[t]);
+          if (e + t < total) store1(a.out_u32, a.out_f32, off0 + e + t, v[t], a.chk);
       }
     }
   }
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kThreads) lattice_points_generic(PointsArgs a)
     const uint32_t phi = __brev(BACKWARD ? ~k : k);
     const uint32_t g = __ldg(a.matrices + j) | 1u;
     const uint32_t sh = a.seeds ? __ldg(a.seeds + j) : 0u;
-    store1(a.out_u32, a.out_f32, f, phi * g + sh);
+    store1(a.out_u32, a.out_f32, f, phi * g + sh, a.chk);
   }
 }
 
@@ -211,11 +211,11 @@ __global__ void __launch_bounds__(kThreads) pixel_lattice_points_fast(PixelPoint
       }
       if (c < chunks) {
         if (e + 4u <= total) {
-          store4(a.out_u32, a.out_f32, off0 + e, v);
+          store4(a.out_u32, a.out_f32, off0 + e, v, a.chk);
         } else {  // the batch's ragged end (s % 4 != 0)
 #pragma unroll
           for (int t = 0; t < 4; ++t)
-            if (e + t < total) store1(a.out_u32, a.out_f32, off0 + e + t, v[t]);
+            if (e + t < total) store1(a.out_u32, a.out_f32, off0 + e + t, v[t], a.chk);
         }
       }
     }
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(kThreads) pixel_lattice_points_kernel(PixelPoi
     const uint32_t i = (uint32_t)(r % a.spp);
     const uint32_t shift = pixel_shift((uint32_t)(p % a.width), (uint32_t)(p / a.width), a.grid_log2);
     const uint32_t base = __brev(i) + shift;
-    for (uint32_t j = 0; j < a.s; ++j) store1(a.out_u32, a.out_f32, r * a.s + j, base * (__ldg(a.g + j) | 1u));
+    for (uint32_t j = 0; j < a.s; ++j) store1(a.out_u32, a.out_f32, r * a.s + j, base * (__ldg(a.g + j) | 1u), a.chk);
   }
 }
 
@@ -378,11 +378,11 @@ __global__ void __launch_bounds__(kThreads) random_lattice_points_fast(RandomPoi
         }
       }
       if (e + 4u <= total) {
-        store4(a.out_u32, a.out_f32, off0 + e, v);
+        store4(a.out_u32, a.out_f32, off0 + e, v, a.chk);
       } else {  // the batch's ragged end (s % 4 != 0)
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-          if (e + q < total) store1(a.out_u32, a.out_f32, off0 + e + q, v[q]);
+          if (e + q < total) store1(a.out_u32, a.out_f32, off0 + e + q, v[q], a.chk);
       }
     }
   }
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(kThreads) random_lattice_points_generic(Random
     uint32_t g[1];
     rlat_generators<KIND, 1>(a.seed, t & ((1u << a.r_log2) - 1u), j, (uint32_t)(p % a.width),
                              (uint32_t)(p / a.width), jump, g);
-    store1(a.out_u32, a.out_f32, f, __brev(~(t >> a.r_log2)) * g[0]);
+    store1(a.out_u32, a.out_f32, f, __brev(~(t >> a.r_log2)) * g[0], a.chk);
   }
 }
 

@@ -15,7 +15,8 @@ namespace pts {
 constexpr int kThreads = 256;
 
 __device__ __forceinline__ void store4(uint32_t* out_u32, float* out_f32, uint64_t off,
-                                       const uint32_t (&v)[4]) {
+                                       const uint32_t (&v)[4], const CheckCtx& chk) {
+  if (!in_bounds(chk, off, 4, kCheckPoints)) return;
   if (out_u32) __stcs(reinterpret_cast<uint4*>(out_u32 + off), make_uint4(v[0], v[1], v[2], v[3]));
   if (out_f32)
     __stcs(reinterpret_cast<float4*>(out_f32 + off),
@@ -24,7 +25,8 @@ __device__ __forceinline__ void store4(uint32_t* out_u32, float* out_f32, uint64
 }
 
 __device__ __forceinline__ void store1(uint32_t* out_u32, float* out_f32, uint64_t off,
-                                       uint32_t v) {
+                                       uint32_t v, const CheckCtx& chk) {
+  if (!in_bounds(chk, off, 1, kCheckPoints)) return;
   if (out_u32) out_u32[off] = v;
   if (out_f32) out_f32[off] = map_u32_to_unifloat(v);
 }
@@ -51,7 +53,7 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 // tile 0.726 / 0.728 / 0.653 / 0.866 ms (4 groups: 2 KiB bulk stores, 2 CTAs per
 // SM; 8 groups: 1 CTA per SM).
 #ifndef QMC_POINTS_TMA
-#define QMC_POINTS_TMA 1
+#define QMC_POINTS_TMA (QMC_CHECKED ? 0 : 1)  // the checked build tests every 16-byte store
 #endif
 #ifndef QMC_POINTS_STAGE_GROUPS
 #define QMC_POINTS_STAGE_GROUPS 4

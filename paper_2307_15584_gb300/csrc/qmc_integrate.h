@@ -54,6 +54,7 @@ struct IntegrateArgs {
   // placing these before the hot fields measured 1.5 % slower)
   uint32_t sobol_m;      // columns per dimension of matrices (32 .. 64)
   uint32_t part_log2;    // integral p enumerates element p mod 2^part_log2 (0: the sequence)
+  uint32_t* check_word;  // checked build: where out-of-range stores report themselves
 };
 
 // Offsets of the workspace regions (bytes from the 256-byte aligned base).

@@ -8,6 +8,7 @@
 #include <cstdint>
 
 #include "../../include/qmc.h"
+#include "qmc_checked.cuh"
 
 namespace qmc {
 
@@ -40,6 +41,7 @@ struct PointsArgs {
   uint32_t scramble;         // Sobol': 0 none, 1 XOR, 2 nested; lattice: bit 0 = backward
   uint32_t q_log2;           // set by the launcher
   uint32_t u_log2;           // set by the launcher
+  CheckCtx chk;              // checked build: the output extent count * s and the error word
 };
 
 // Arguments of the pixel-shifted lattice points (Sec. 3).
@@ -49,6 +51,7 @@ struct PixelPointsArgs {
   float* out_f32;     // [n_pixels * spp][s] or null
   uint64_t pixel_begin, n_pixels;
   uint32_t spp, s, width, grid_log2;
+  CheckCtx chk;  // checked build: the output extent n_pixels * spp * s and the error word
 };
 
 cudaError_t launch_pixel_lattice_points(const PixelPointsArgs& a, cudaStream_t stream);
@@ -61,12 +64,18 @@ struct RandomPointsArgs {
   uint32_t spp, s, width;
   uint32_t kind, seed, r_log2;  // qmc_rlat_kind, hash seed, log2 of the instance count
   uint32_t batch_pixels;        // set by the launcher: pixels per shared-memory batch
+  CheckCtx chk;                 // checked build: the output extent n_pixels * spp * s and the error word
 };
 
 cudaError_t launch_random_lattice_points(const RandomPointsArgs& a, cudaStream_t stream);
 
 cudaError_t launch_sobol_points(PointsArgs a, cudaStream_t stream);
 cudaError_t launch_lattice_points(PointsArgs a, cudaStream_t stream);
+
+// The checked build's error word of the current device and the extent `limit`
+// (less QMC_CHECK_SLACK elements, a test hook that makes the last stores of a
+// launch report themselves); {nullptr, limit} in the normal build.
+CheckCtx check_ctx(uint64_t limit);
 
 // Work split recorded by qmc_tune_integrate for this problem class, if any.
 bool tuned_lookup(const qmc_problem* p, uint32_t n, bool grad, uint32_t* chunk, uint32_t* block);

@@ -145,13 +145,13 @@ __global__ void __launch_bounds__(kThreads) sobol_points_fast(PointsArgs a) {
         if (TMA)
           stager.put(lane, c, v);
         else
-          store4(a.out_u32, a.out_f32, o, v);
+          store4(a.out_u32, a.out_f32, o, v, a.chk);
       } else {  // ragged last group: per-element row test
         const uint64_t rows_left = a.count - (g << a.q_log2);
         const uint32_t e0 = 4u * (lane + 32u * c);
 #pragma unroll
         for (int t = 0; t < 4; ++t)
-          if ((uint64_t)((e0 + t) / s) < rows_left) store1(a.out_u32, a.out_f32, o + t, v[t]);
+          if ((uint64_t)((e0 + t) / s) < rows_left) store1(a.out_u32, a.out_f32, o + t, v[t], a.chk);
       }
     }
     if (TMA && g < full_groups)
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kThreads) sobol_points_generic(PointsArgs a) {
     for (; i != 0; i &= i - 1u) y ^= __ldg(Cj + (__ffsll((long long)i) - 1));
     if (MODE == 1 || (MODE == 2 && a.scramble == QMC_SCRAMBLE_NESTED_XOR)) y ^= __ldg(a.seeds + j);
     if (MODE == 2) y = __brev(nested_mix(__brev(y), nested_key(__ldg(a.seeds + j))));
-    store1(a.out_u32, a.out_f32, f, y);
+    store1(a.out_u32, a.out_f32, f, y, a.chk);
   }
 }
 

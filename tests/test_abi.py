@@ -35,6 +35,9 @@ def test_header_symbols_exported(B):
     for name in declared:
         assert hasattr(lib, name), name
     assert sorted(B.EXPORTED) == sorted(declared)
+    checked = ctypes.CDLL(os.path.join(os.path.dirname(B.LIB_PATH), "libqmc_gb300_checked.so"))
+    for name in declared:  # the checked build exports the same interface
+        assert hasattr(checked, name), name
     assert B.qmc_abi_version() == 5
     assert ctypes.sizeof(B.qmc_problem) == 72  # 4 + 3 pointers + 8 words, as in include/qmc.h
     assert "INVALID" in B.qmc_status_string(1)
@@ -315,3 +318,12 @@ def test_autotune_cache_file(B, tmp_path):
     with pytest.raises(B.QMCError) as e:
         B.qmc_tune_save(str(tmp_path / "no_such_dir" / "x.json"))
     assert e.value.status == 8
+
+
+def test_checked_error_word_only_in_the_checked_build(B):
+    """The normal build has no error word: qmc_checked_error answers QMC_ERR_UNSUPPORTED
+    (with no CUDA call, so this runs on the CPU) and reports 0 bits."""
+    bits = ctypes.c_uint32(123)
+    assert B._lib.qmc_checked_error(ctypes.byref(bits), 0) == 6
+    assert bits.value == 0
+    assert B._lib.qmc_checked_error(None, 0) == 1
