@@ -174,7 +174,7 @@ def profile_sources(fname: str, key: str) -> list[str]:
     """The sources whose digest keys a committed profile figure."""
     if fname == "traffic.txt":
         return KERNEL_SOURCES[key]
-    if fname == "inst_per_sample.txt":
+    if fname in ("inst_per_sample.txt", "pipes.txt"):
         return integrate_sources(key)
     for k, src in POINTS_KERNELS.values():
         if k == key:
@@ -227,7 +227,7 @@ def _profile_row(fname: str, key: str, files):
 
     digest = source_digest(files)
     for line in open(path):
-        parts = line.split()
+        parts = line.split("#", 1)[0].split()  # a trailing comment is not a figure
         if len(parts) >= 3 and parts[0] == key and parts[1] == digest:
             return [float(v) for v in parts[2:]]
     return None

@@ -13,6 +13,7 @@
 #include <cstdint>
 
 #include "../../include/qmc.h"
+#include "qmc_checked.cuh"
 #include "qmc_device.cuh"
 #include "qmc_integrate.h"
 #include "qmc_internal.h"
@@ -323,16 +324,18 @@ constexpr float kU32 = 5.9604645e-8f;
 // sums: their error against the fp64 oracle is set by the fp32 evaluation of
 // each term (about 8u ln2 |t| relative, see the mixture), which a compensated
 // sum was measured not to reduce, at 16 more registers and 10 % of the fused
-// kernel's rate.  Whole blocks run unrolled (by kBlock, by two with the
-// gradient, whose 17 sums leave fewer registers); the item's last, partial
-// block runs sample by sample.
+// kernel's rate.  Whole blocks of full rows (all 32 samples of each row in the
+// item) run unrolled -- by kBlock, by two with the gradient, whose 17 sums leave
+// fewer registers -- with no per-sample test of the sample's existence; the
+// remaining rows (fewer than kBlock full ones and the ragged last) run sample by
+// sample with it.
 constexpr uint32_t kBlock = 4;
 
-template <bool EXACT, bool GRAD, int NV, class Src, class F>
+template <bool EXACT, bool GRAD, bool FULL, int NV, class Src, class F>
 __device__ __forceinline__ void run_sample(const Src& src, const F& f, uint32_t r, uint32_t len, float (&blk)[NV],
                                            Kahan (&acc)[NV], float& e2) {
   const uint32_t il = (r << 5) + (threadIdx.x & 31u);
-  const bool valid = il < len;
+  const bool valid = FULL || il < len;
   float x[F::S];
   src.point(r, il, valid, x);
   float err;
@@ -379,20 +382,23 @@ __device__ __forceinline__ void run_item(const Src& src, const F& f, uint32_t le
     }
   };
   uint32_t r0 = 0;
-  for (; r0 + kBlock <= R; r0 += kBlock) {
+  const uint32_t Rfull = len >> 5;  // rows whose 32 samples all exist
+  for (; r0 + kBlock <= Rfull; r0 += kBlock) {
     float blk[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) blk[v] = 0.0f;
 #pragma unroll (GRAD ? 2 : kBlock)
-    for (uint32_t k = 0; k < kBlock; ++k) run_sample<EXACT, GRAD>(src, f, r0 + k, len, blk, acc, e2);
+    for (uint32_t k = 0; k < kBlock; ++k) run_sample<EXACT, GRAD, true>(src, f, r0 + k, len, blk, acc, e2);
     fold(blk);
   }
-  if (r0 < R) {
+  while (r0 < R) {  // the rest: at most kBlock - 1 full rows and the ragged last row, in blocks
     float blk[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) blk[v] = 0.0f;
-    for (uint32_t r = r0; r < R; ++r) run_sample<EXACT, GRAD>(src, f, r, len, blk, acc, e2);
+    const uint32_t r1 = min(R, r0 + kBlock);
+    for (uint32_t r = r0; r < r1; ++r) run_sample<EXACT, GRAD, false>(src, f, r, len, blk, acc, e2);
     fold(blk);
+    r0 = r1;
   }
 }
 
@@ -442,6 +448,7 @@ __global__ void __launch_bounds__(256, Integrand<FN>::kMinBlocks) integrate_main
       }
     }
     float* out = a.partials + (size_t)item * (2 * NV);
+    const bool store_ok = in_bounds(CheckCtx{a.check_word, a.capacity_items}, item, 1, kCheckPartials);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const Comp c = warp_comp_sum(acc[v].comp());
@@ -449,7 +456,7 @@ __global__ void __launch_bounds__(256, Integrand<FN>::kMinBlocks) integrate_main
       if constexpr (GRAD) {
         if (v > 0) k = f.grad_scale(v);
       }
-      if (lane == (uint32_t)(v & 31)) {
+      if (store_ok && lane == (uint32_t)(v & 31)) {
         out[2 * v] = __fmul_rn(c.sum, k);
         out[2 * v + 1] = __fmul_rn(c.err, k);
       }

@@ -47,13 +47,13 @@ def test_committed_profile_figures_match_the_sources():
     import bench
     from paper_2307_15584_gb300.build import source_digest
 
-    for fname in ("traffic.txt", "inst_per_coord.txt", "inst_per_sample.txt"):
+    for fname in ("traffic.txt", "inst_per_coord.txt", "inst_per_sample.txt", "pipes.txt"):
         path = os.path.join(bench.ROOT, "profiles", fname)
         for line in open(path):
-            parts = line.split()
-            if len(parts) != 3 or line.startswith("#"):
+            parts = line.split("#", 1)[0].split()
+            if len(parts) < 3:
                 continue
-            key, digest, _ = parts
+            key, digest = parts[:2]
             assert source_digest(bench.profile_sources(fname, key)) == digest, (fname, key)
 
 
