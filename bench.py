@@ -161,7 +161,8 @@ KERNEL_SOURCES = {"sobol_points_fast<1,2>": POINTS_SOURCES}
 POINTS_COMMON = ["points_common.cuh", "qmc_device.cuh", "qmc_internal.h"]
 # the points workloads' kernels: (profile key, the kernel's own sources besides POINTS_COMMON)
 POINTS_KERNELS = {"sobol32_nested": ("sobol_points_fast<1,2>", ["sobol_points.cu"]),
-                  "sobol32_nested_from_index_1": ("sobol_points_walk<2>", ["sobol_points.cu"]),
+                  "sobol32_nested_from_index_1": ("sobol_points_fast<1,2>@1", ["sobol_points.cu"]),
+                  "sobol40_nested": ("sobol_points_walk<2>", ["sobol_points.cu"]),
                   "lattice_shifted": ("lattice_points_fast<1,0,1>", ["lattice_points.cu"]),
                   "lattice_shifted_from_index_1": ("lattice_points_flat<0>", ["lattice_points.cu"]),
                   "halton_faure": ("halton_points_kernel<faure>", ["halton_points.cu", "halton_points.h"]),
@@ -357,11 +358,14 @@ def extras_cpu_baselines(names) -> dict:
         C = oracle.sobol_matrices(s, inputs.sobol_raw_init(s))
         W = oracle.sobol_matrices_wide(s + 1, 64, inputs.sobol_raw_init(s + 1))
         sd = inputs.scramble_seeds(s)
+        C37 = oracle.sobol_matrices(37, inputs.sobol_raw_init(37))
+        C40, sd40 = np.concatenate([C37, C37[:3]]), inputs.scramble_seeds(40)
         g, sh = inputs.lattice_generator(s), inputs.lattice_shift(s)
         nested = oracle.SCRAMBLE_NESTED
         runs = {
             "sobol32_nested": (n, lambda r, t: oracle.sobol_points(C, 0, r, nested, sd, threads=t)),
             "sobol32_nested_from_index_1": (n, lambda r, t: oracle.sobol_points(C, 1, r, nested, sd, threads=t)),
+            "sobol40_nested": (n, lambda r, t: oracle.sobol_points(C40, 0, r, nested, sd40, threads=t)),
             "sobol64_nested_at_2^40": (n, lambda r, t: oracle.sobol_points_wide(W[:s], 1 << 40, r, nested, sd,
                                                                                 threads=t)),
             "sobol64_partition_p5_of_8": (n, lambda r, t: oracle.sobol_points_partitioned(W, 3, 5, 1 << 37, r, nested,
@@ -378,8 +382,10 @@ def extras_cpu_baselines(names) -> dict:
             "random_lattice_lfsr_x4_16spp": (n // 4, lambda r, t: oracle.random_lattice_points(
                 oracle.RLAT_LFSR, 7, 4, s, 1024, r // 16, 16, threads=t)),
         }
-        out["points"] = {name: _oracle_rates(lambda k, t, rows=rows, fn=fn: _discard(fn(rows // k, t)), rows * s,
-                                             "Gdims/s", f"{rows} rows x {s} dims")
+        dims = {"sobol40_nested": 40}
+        out["points"] = {name: _oracle_rates(lambda k, t, rows=rows, fn=fn: _discard(fn(rows // k, t)),
+                                             rows * dims.get(name, s), "Gdims/s",
+                                             f"{rows} rows x {dims.get(name, s)} dims")
                          for name, (rows, fn) in runs.items()}
     return out
 
@@ -695,8 +701,9 @@ def bench_lattice(dev, steps, warmup, small, sm_mhz):
 def bench_points(dev, steps, warmup, small, sm_mhz):
     """Every materialising generator on the headline's shape (s = 32, 2^24 rows,
     u32 + fp32, 8 B written per coordinate; 2^20 rows when small): the 32-bit
-    Sobol' headline kernel again, the same from index 1 (off the fast path's
-    group grid: the walking kernel), Sobol' with 64-bit indices at 2^40 (Alg. 3),
+    Sobol' headline kernel again, the same from index 1 (its first group cut by
+    the range), Sobol' at s = 40 (16-byte groups of 5 chunks per lane do not fit
+    the fast path: the walking kernel), Sobol' with 64-bit indices at 2^40 (Alg. 3),
     the shifted rank-1 lattice from index 1 (the flat-chunk kernel),
     one element of a partitioned Sobol' sequence (Sec. 2.5.1), the shifted
     rank-1 lattice, Halton (Faure; whole, and one element of the sequence
@@ -717,9 +724,16 @@ def bench_points(dev, steps, warmup, small, sm_mhz):
     W = B.u32_tensor(B.qmc_sobol_matrices_wide(s + 1, 64, inputs.sobol_raw_init(s + 1)), dev)
     sd = B.u32_tensor(inputs.scramble_seeds(s), dev)
     g, sh = B.u32_tensor(inputs.lattice_generator(s), dev), B.u32_tensor(inputs.lattice_shift(s), dev)
+    s40 = 40  # the walking kernel's workload: 40 = 8 x 5, five 16-byte chunks per lane in a group
+    C40 = B.u32_tensor(B.qmc_sobol_matrices(37, inputs.sobol_raw_init(37)), dev)
+    C40 = torch.cat([C40, C40[:s40 - 37]])  # dimensions 37-39 reuse columns: any matrices are valid input
+    sd40 = B.u32_tensor(inputs.scramble_seeds(s40), dev)
+    u40 = torch.empty((n, s40), dtype=torch.int32, device=dev)
+    f40 = torch.empty((n, s40), dtype=torch.float32, device=dev)
     runs = {
         "sobol32_nested": lambda: B.qmc_sobol_points(C, s, 0, n, B.SCRAMBLE_NESTED, sd, u, f),
         "sobol32_nested_from_index_1": lambda: B.qmc_sobol_points(C, s, 1, n, B.SCRAMBLE_NESTED, sd, u, f),
+        "sobol40_nested": (lambda: B.qmc_sobol_points(C40, s40, 0, n, B.SCRAMBLE_NESTED, sd40, u40, f40), s40),
         "sobol64_nested_at_2^40": lambda: B.qmc_sobol_points_wide(W, 64, s, 1 << 40, n, B.SCRAMBLE_NESTED, sd, u, f),
         "sobol64_partition_p5_of_8": lambda: B.qmc_sobol_points_partitioned(W, 64, s, 3, 5, 1 << 37, n,
                                                                             B.SCRAMBLE_NESTED, sd, u, f),
@@ -743,18 +757,21 @@ def bench_points(dev, steps, warmup, small, sm_mhz):
     res = {"rows": n, "s": s, "bytes_per_launch": n * s * 8,
            "issue_peak_ginst_s": issue_peak / 1e9, "clock_mhz": clock}
     for name, fn in runs.items():
+        fn, si = fn if isinstance(fn, tuple) else (fn, s)
         ms = statistics.median(timed(fn, steps, warmup, stream))
-        gbs = n * s * 8 / (ms * 1e-3) / 1e9
-        entry = {"ms": ms, "gdims_s": n * s / (ms * 1e-3) / 1e9, "gb_s": gbs, "frac_hbm": gbs / peak}
+        gbs = n * si * 8 / (ms * 1e-3) / 1e9
+        entry = {"ms": ms, "gdims_s": n * si / (ms * 1e-3) / 1e9, "gb_s": gbs, "frac_hbm": gbs / peak}
+        if si != s:
+            entry["s"] = si
         if name in POINTS_KERNELS:
             key = POINTS_KERNELS[name][0]
             ipc = _profile_value("inst_per_coord.txt", key, profile_sources("inst_per_coord.txt", key))
             if ipc is not None:
                 entry["inst_per_coord"] = ipc
-                entry["frac_issue"] = ipc * n * s / (ms * 1e-3) / issue_peak
+                entry["frac_issue"] = ipc * n * si / (ms * 1e-3) / issue_peak
                 entry["bound"] = "hbm" if entry["frac_hbm"] >= entry["frac_issue"] else "alu"
         res[name] = entry
-    del u, f
+    del u, f, u40, f40
     return res
 
 

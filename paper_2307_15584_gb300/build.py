@@ -28,9 +28,36 @@ def sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+def code_only(text: str) -> str:
+    """C/C++ source without its comments and blank lines, each line stripped of
+    trailing blanks: what a comment-only edit leaves unchanged."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":  # a string or character literal, copied whole
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    lines = (line.rstrip() for line in "".join(out).split("\n"))
+    return "\n".join(line for line in lines if line)
+
+
 def source_digest(files: list[str] | None = None) -> str:
-    """Short hash of the given csrc files (default: every CUDA source and header);
-    ties a profile figure to the sources of the kernel it was taken from."""
+    """Short hash of the code of the given csrc files (default: every CUDA source
+    and header), comments left out; ties a profile figure to the code of the
+    kernel it was taken from."""
     import hashlib
 
     h = hashlib.sha256()
@@ -41,8 +68,8 @@ def source_digest(files: list[str] | None = None) -> str:
         deps.append(HEADER)
     for d in deps:
         h.update(os.path.basename(d).encode())
-        with open(d, "rb") as f:
-            h.update(f.read())
+        with open(d, encoding="utf-8") as f:
+            h.update(code_only(f.read()).encode())
     return h.hexdigest()[:12]
 
 

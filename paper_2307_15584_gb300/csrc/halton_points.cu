@@ -53,13 +53,17 @@ __device__ HaltonTables g_halton;
 // Work layout.  The output is [count][s] row-major.  Lanes own dimensions: a
 // warp takes a chunk of up to 32 consecutive output dimensions (w of them) and
 // k = floor(32 / w) consecutive rows per step, lane l holding dimension l mod w
-// of row l / w, so each step writes k whole rows of the chunk -- coalesced,
-// with no staging.  A unit is kHaltonSteps steps of one chunk; each lane walks
-// its dimension down the rows, advancing the digit groups of i mod b^K by the
-// index step k 2^q instead of recomputing them: one table lookup and one
-// multiply-add per row, the higher groups touched only on a carry (or every
-// row when the step has higher digits, as in a partitioned sequence).
+// of row l / w, so each step writes k whole rows of the chunk, coalesced.  A
+// unit is kHaltonSteps steps of one chunk; each lane walks its dimension down
+// the rows, advancing the digit groups of i mod b^K by the index step k 2^q
+// instead of recomputing them: one table lookup and one multiply-add per row,
+// the higher groups touched only on a carry (or every row when the step has
+// higher digits, as in a partitioned sequence).  A 32-wide chunk with 16-byte
+// aligned rows passes each group of four rows through a per-warp 4 x 32
+// shared-memory tile, so each lane stores four consecutive dimensions of one
+// row as one 16-byte chunk.
 constexpr uint32_t kHaltonSteps = 256;
+constexpr uint32_t kHaltonStageWords = 128;  // per warp: 4 rows x 32 dimensions
 constexpr int kHaltonMaxGroups = 6;  // G <= 6 for every base up to the 64th prime (base 37: L = 1, K = 6)
 
 // floor(N 2^32 / b^K) for N < b^K < 2^32, exactly: with M = ceil(2^96 / b^K) = M2 2^64 + M1 2^32 + M0,
@@ -88,9 +92,11 @@ __device__ __forceinline__ void halton_groups(uint32_t x, uint32_t G, uint32_t b
   }
 }
 
-__global__ void __launch_bounds__(kThreads) halton_points_kernel(HaltonArgs p) {
+__global__ void __launch_bounds__(kThreads, 2) halton_points_kernel(HaltonArgs p) {
   extern __shared__ __align__(16) uint32_t hsmem[];
   uint16_t* htab = reinterpret_cast<uint16_t*>(hsmem);  // digit-group tables
+  // this warp's 4 x 32 tile for the transposed stores, after the tables (16-byte aligned)
+  uint32_t* stage = hsmem + p.stage_word + (threadIdx.x >> 5) * kHaltonStageWords;
   for (uint32_t jo = 0; jo < p.s; ++jo) {
     const uint32_t j = p.dim0 + jo;
     const uint32_t b = g_halton.base[j];
@@ -198,36 +204,80 @@ __global__ void __launch_bounds__(kThreads) halton_points_kernel(HaltonArgs p) {
     const uint32_t lim1 = G == 2 ? bLp : bL, w1g = wg[1];
     uint32_t x0 = xg[0];
     const uint32_t d0 = dg[0], w0g = wg[0];
-    auto emit = [&]() {  // the current row's coordinate
-      const uint32_t N = nrest + (uint32_t)tab[x0] * w0g;
-      const uint32_t v = halton_scale(N, m0, m1, m2);
-      if (in_bounds(p.chk, off0 + ofs, 1, kCheckPoints)) {
-        if (p.out_u32) ou[ofs] = v;
-        if (p.out_f32) of[ofs] = map_u32_to_unifloat(v);
+    auto put = [&](uint32_t o, uint32_t v) {  // one coordinate, element o of the unit's outputs
+      if (in_bounds(p.chk, off0 + o, 1, kCheckPoints)) {
+        if (p.out_u32) ou[o] = v;
+        if (p.out_f32) of[o] = map_u32_to_unifloat(v);
       }
+    };
+    auto emit = [&]() {  // the current row's coordinate
+      put(ofs, halton_scale(nrest + (uint32_t)tab[x0] * w0g, m0, m1, m2));
       ofs += dofs;
       x0 += d0;
       const bool carry0 = x0 >= bL;
       if (carry0) x0 -= bL;
       return carry0;
     };
-    if (!d_hi) {  // the step lies in the lowest group: the higher groups move only on its carry
-      for (uint32_t t = 0; t < steps; ++t) {
-        if (emit()) {
-          if (xg[1] + 1 < lim1) {  // the common carry: group 1 moves by one
-            ++xg[1];
-            const uint32_t t1n = entry(1);
-            nrest += (t1n - t1) * w1g;  // exact modulo 2^32, and the result is below b^K
-            t1 = t1n;
-          } else {
-            add_high(1u);
-            nrest = rest();
-            t1 = entry(1);
-          }
-        }
+    auto carry1 = [&]() {  // a carry out of the lowest group
+      if (xg[1] + 1 < lim1) {  // the common carry: group 1 moves by one
+        ++xg[1];
+        const uint32_t t1n = entry(1);
+        nrest += (t1n - t1) * w1g;  // exact modulo 2^32, and the result is below b^K
+        t1 = t1n;
+      } else {
+        add_high(1u);
+        nrest = rest();
+        t1 = entry(1);
       }
+    };
+    uint32_t t = 0;
+    // Four steps at a time while the step lies in the lowest group and four of them wrap it at
+    // most once: the four table reads go out together, and the rows past the wrap take the
+    // carried higher part.  A 32-wide chunk (all lanes on the same rows, so the choice is made
+    // for the whole warp) with 16-byte aligned rows transposes its four rows through the warp's
+    // tile and stores 16-byte chunks of four consecutive dimensions.
+    bool grouped = !d_hi && 4u * d0 <= bL;
+    if (w == 32u) grouped = __all_sync(0xffffffffu, grouped);
+    if (grouped) {
+      const bool rows16 = w == 32u && (s & 3u) == 0 &&
+                          (((uintptr_t)p.out_u32 | (uintptr_t)p.out_f32) & 15u) == 0;
+      uint64_t vo = (row + (lane >> 3)) * s + (c1 ? 32u : 0u) + 4u * (lane & 7u);  // after the transpose
+      for (; t + 4u <= steps; t += 4u) {
+        uint32_t e[4];
+        bool wr[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t v = x0 + (uint32_t)q * d0;  // below 2 b^L
+          wr[q] = v >= bL;
+          e[q] = tab[wr[q] ? v - bL : v];
+        }
+        const uint32_t xn = x0 + 4u * d0, nlow = nrest;
+        if (xn >= bL) carry1();  // at one of the four rows or at the next group's first
+        x0 = xn >= bL ? xn - bL : xn;
+        uint32_t y4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) y4[q] = halton_scale((wr[q] ? nrest : nlow) + e[q] * w0g, m0, m1, m2);
+        if (rows16) {
+          __syncwarp();
+#pragma unroll
+          for (int q = 0; q < 4; ++q) stage[q * 32u + lane] = y4[q];
+          __syncwarp();
+          const uint4 v = *reinterpret_cast<const uint4*>(stage + (lane >> 3) * 32u + 4u * (lane & 7u));
+          const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+          store4(p.out_u32, p.out_f32, vo, vv, p.chk);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) put(ofs + (uint32_t)q * dofs, y4[q]);
+        }
+        ofs += 4u * dofs;
+        vo += 4u * s;
+      }
+    }
+    if (!d_hi) {  // the step lies in the lowest group: the higher groups move only on its carry
+      for (; t < steps; ++t)
+        if (emit()) carry1();
     } else {  // every step moves the higher groups (a partitioned sequence)
-      for (uint32_t t = 0; t < steps; ++t) {
+      for (; t < steps; ++t) {
         add_high(emit() ? 1u : 0u);
         nrest = rest();
       }
@@ -359,7 +409,8 @@ cudaError_t launch_halton_points(const HaltonArgs& args, cudaStream_t stream) {
     const uint64_t pow2q = (p.q < 64 ? (1ull << p.q) : 0ull) % mp;
     p.delta[jo] = (uint32_t)((k % mp) * pow2q % mp);
   }
-  const size_t smem = ((size_t)(table_words ? table_words : 1) * sizeof(uint16_t) + 15) & ~(size_t)15;
+  p.stage_word = (uint32_t)((((size_t)table_words * sizeof(uint16_t) + 15) & ~(size_t)15) / sizeof(uint32_t));
+  const size_t smem = ((size_t)p.stage_word + (size_t)(kThreads / 32) * kHaltonStageWords) * sizeof(uint32_t);
   const DeviceInfo& dev = device_info();
   if (smem > dev.smem_per_block_optin) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {

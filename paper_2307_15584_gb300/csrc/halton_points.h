@@ -27,6 +27,7 @@ struct HaltonArgs {
   // set by the launcher
   uint32_t table_off[kHaltonMaxDims];  // output dimension jo's digit-group tables in shared memory
   uint32_t delta[kHaltonMaxDims];      // (k 2^q) mod b^K: the index step of the lanes of dimension jo
+  uint32_t stage_word;                 // first 32-bit word of the warps' store tiles, after the tables
   CheckCtx chk;                        // checked build: the output extent count * s and the error word
 };
 

@@ -92,3 +92,15 @@ def test_gradient_errors_and_compact_summary():
                       "lattice_oscillatory", "partition", "points_gdims_s_frac_hbm"}
     assert c["fwd_bwd"]["pipes"] == [0.5, 0.6, 0.2, 0.1] and c["pipes_order"] == ["alu", "fma", "fmaheavy", "xu"]
     assert c["points_gdims_s_frac_hbm"] == {"sobol32_nested": [848.0, 1.0]}  # 2 significant digits
+
+
+def test_digest_ignores_comments_only():
+    """Profile figures are keyed by the code without its comments: a comment-only edit keeps the
+    key, a code edit (even inside a line that also holds a comment) changes it; string literals
+    that look like comments are code."""
+    from paper_2307_15584_gb300.build import code_only
+
+    base = 'int a = 1;  // one\n/* block\n comment */ const char* p = "x//y";\n\nint b;\n'
+    assert code_only(base) == code_only(base.replace("// one", "// another").replace("block", "other"))
+    assert code_only(base) != code_only(base.replace("int a = 1;", "int a = 2;"))
+    assert '"x//y"' in code_only(base) and "one" not in code_only(base)

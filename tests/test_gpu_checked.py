@@ -38,10 +38,16 @@ def same(u, f, ou, of, what):
 s, n = 32, 4096 + 37
 C = B.qmc_sobol_matrices(s, inputs.sobol_raw_init(s)); Cd = B.u32_tensor(C)
 sd = inputs.scramble_seeds(s); sdd = B.u32_tensor(sd)
-for begin, mode in ((0, 2), (1, 3), (4096, 1)):  # the 16-byte path, the walking path
+for begin, mode in ((0, 2), (1, 3), (4096, 1)):  # the 16-byte path, on and off its group grid
     u, f = fresh(n, s)
     B.qmc_sobol_points(Cd, s, begin, n, mode, sdd, u, f)
     same(u, f, *oracle.sobol_points(C, begin, n, mode, sd), f"sobol {begin} {mode}")
+C37 = B.qmc_sobol_matrices(37, inputs.sobol_raw_init(37))
+for s2, begin, mode in ((40, 3, 2), (7, 1, 1)):  # the walking path: 32- and 8-wide chunks; 7-wide chunks
+    C2, sd2 = np.ascontiguousarray(np.concatenate([C37, C37])[:s2]), inputs.scramble_seeds(s2)
+    u, f = fresh(n, s2)
+    B.qmc_sobol_points(B.u32_tensor(C2), s2, begin, n, mode, B.u32_tensor(sd2), u, f)
+    same(u, f, *oracle.sobol_points(C2, begin, n, mode, sd2), f"sobol walk {s2}")
 W = oracle.sobol_matrices_wide(s + 1, 64, inputs.sobol_raw_init(s + 1)); Wd = B.u32_tensor(W)
 u, f = fresh(n, s); B.qmc_sobol_points_wide(B.u32_tensor(np.ascontiguousarray(W[:s])), 64, s, 1 << 40, n, 2, sdd, u, f)
 same(u, f, *oracle.sobol_points_wide(W[:s], 1 << 40, n, 2, sd), "wide")
@@ -88,7 +94,14 @@ B.qmc_halton_points(s, 0, None, 0, 512, u, f)
 assert B.qmc_checked_error(reset=True) == 1
 gh = B.as_u32(u).reshape(-1)
 assert (gh[512 * s - 5:] == np.uint32(SENT & 0xFFFFFFFF)).all()
-assert (gh[:512 * s - 5] == oracle.halton_points(s, 0, 512).reshape(-1)[:512 * s - 5]).all()
+# a 16-byte store that reaches past the shortened extent is skipped whole
+assert (gh[:512 * s - 9] == oracle.halton_points(s, 0, 512).reshape(-1)[:512 * s - 9]).all()
+C2, sd2 = np.ascontiguousarray(np.concatenate([C37, C37])[:40]), inputs.scramble_seeds(40)
+u, f = fresh(n, 40)
+B.qmc_sobol_points(B.u32_tensor(C2), 40, 0, n, 2, B.u32_tensor(sd2), u, f)  # the walking path
+assert B.qmc_checked_error(reset=True) == 1
+gw, ow = B.as_u32(u).reshape(-1), oracle.sobol_points(C2, 0, n, 2, sd2)[0].reshape(-1)
+assert (gw[n * 40 - 5:] == np.uint32(SENT & 0xFFFFFFFF)).all() and (gw[:n * 40 - 9] == ow[:n * 40 - 9]).all()
 del os.environ["QMC_CHECK_SLACK"]
 u, f = fresh(n, s)
 B.qmc_sobol_points(Cd, s, 0, n, 2, sdd, u, f)

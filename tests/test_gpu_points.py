@@ -1,5 +1,7 @@
 """GPU parity of the materialised points (K1 Sobol', K2 lattice) against the
 oracle: bit-exact u32 and fp32 bit patterns, through the C-ABI."""
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -47,6 +49,58 @@ def test_sobol_points_bit_exact(B, oracle, s, mode):
 def test_sobol_points_offsets(B, oracle, begin):
     for s, mode in ((32, 2), (2, 0), (6, 1), (5, 3), (32, 3)):
         _sobol_case(B, oracle, s, begin, min(2999, (1 << 32) - begin), mode)
+
+
+@pytest.mark.parametrize("s", [4, 6, 8, 12, 20, 32, 64, 96, 128, 256])
+def test_sobol_fast_path_any_start(B, oracle, s):
+    """The 16-byte group path from starts off its group grid of Q = 128 / gcd(s, 128) rows: the
+    first group cut at the start, ranges inside one group, and last groups cut at the end
+    (index_begin * s a multiple of 4, so every group's chunks stay 16-byte aligned)."""
+    Q = 128 // math.gcd(s, 128)
+    step = 1 if s % 4 == 0 else 4 // math.gcd(s, 4)  # the smallest start spacing with begin * s % 4 == 0
+    begins = sorted({step, Q - step, Q + step, 3 * Q + 2 * step, (1 << 31) + step})
+    for i, begin in enumerate(begins):
+        for count in (1, max(1, Q // 2 - 1), 5 * Q + 3, 4096 + 37):
+            _sobol_case(B, oracle, s, begin, count, (i + count) % 4)
+
+
+@pytest.mark.parametrize("s,begin,count,mode", [
+    (32, 1, 4099, 2),      # a start off the group grid: a one-element-per-thread head, then the 16-byte path
+    (100, 0, 1027, 3),     # 25 quads per row, one row per warp step (4-byte path: three 32-wide chunks, one 4-wide)
+    (36, 6, 1030, 2),      # 9 quads, 3 rows per step, 5 lanes idle (32- and 4-wide chunks)
+    (40, 9, 3001, 2),      # 10 quads, 3 rows per step (the bench's s = 40; 32- and 8-wide chunks)
+    (44, 5, 2100, 2),      # 11 quads, 2 rows per step (32- and 12-wide chunks)
+    (52, 0, 1500, 3),      # 13 quads (32- and 20-wide chunks)
+    (60, 2, 999, 1),       # 15 quads (32- and 28-wide chunks)
+    (644, 3, 700, 2),      # five 128-wide chunks and a 4-wide one with a 2^5-row table (shared memory is
+                           # tight): its 32-row steps go one at a time
+    (7, 3, 2053, 1),       # 7-wide chunks, four rows per warp step
+    (2, 1, 777, 0),        # 2-wide chunks: 16 rows per warp step
+])
+def test_sobol_walk_outputs(B, oracle, s, begin, count, mode):
+    """The walking path with each output alone (quads of four dimensions per lane, 16-byte
+    stores), and with outputs that start 4 and 8 bytes past a 16-byte boundary (one dimension
+    per lane, 4-byte stores); counts that leave rows of a unit outside a whole pair or group of
+    steps."""
+    raw = inputs.sobol_raw_init(s, seed=5)
+    C = B.qmc_sobol_matrices(min(s, 37), raw[: min(s, 37)])
+    if s > 37:
+        C = np.concatenate([C] * (s // 37 + 1))[:s]
+    seeds = inputs.scramble_seeds(s, seed=5)
+    Cd, sd = B.u32_tensor(C), B.u32_tensor(seeds)
+    sk = sd if mode else None
+    ou, of = oracle.sobol_points(C, begin, count, mode, seeds if mode else None)
+    u, _ = B.sobol_points(Cd, count, index_begin=begin, scramble=mode, seeds=sk, want_f32=False)
+    _, f = B.sobol_points(Cd, count, index_begin=begin, scramble=mode, seeds=sk, want_u32=False)
+    np.testing.assert_array_equal(B.as_u32(u), ou)
+    np.testing.assert_array_equal(_f32_bits(f), of.view(np.uint32))
+    ub = torch.zeros(count * s + 1, dtype=torch.int32, device="cuda")
+    fb = torch.zeros(count * s + 2, dtype=torch.float32, device="cuda")
+    u2, f2 = ub[1:].view(count, s), fb[2:].view(count, s)
+    B.qmc_sobol_points(Cd, s, begin, count, mode, sk, u2, f2)
+    np.testing.assert_array_equal(B.as_u32(u2), ou)
+    np.testing.assert_array_equal(_f32_bits(f2), of.view(np.uint32))
+    assert ub[0].item() == 0 and fb[:2].eq(0).all().item()
 
 
 def test_sobol_single_outputs_and_empty(B, oracle):
