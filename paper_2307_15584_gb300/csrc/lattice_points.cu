@@ -466,12 +466,10 @@ cudaError_t launch_pixel_lattice_points(const PixelPointsArgs& a, cudaStream_t s
     const auto kernel = (a.s & 3u) == 0 ? pixel_lattice_points_fast<1>
                         : a.s <= 2       ? pixel_lattice_points_fast<2>
                                          : pixel_lattice_points_fast<0>;
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0);
-    if (e != cudaSuccess) return e;
-    uint64_t blocks = (uint64_t)dev.sm_count * (per_sm < 1 ? 1 : per_sm);
-    const uint64_t need = (((a.n_pixels + 31) >> 5) + kThreads / 32 - 1) / (kThreads / 32);
-    if (need < blocks) blocks = need;
+    // one 32-pixel batch per warp: the kernel has no per-block set-up, and a persistent grid's
+    // warps would end unevenly when they hold only a few batches each
+    uint64_t blocks = (((a.n_pixels + 31) >> 5) + kThreads / 32 - 1) / (kThreads / 32);
+    if (blocks > 0x7FFFFFFFull) blocks = 0x7FFFFFFFull;  // warp_range spreads the batches over the grid
     if (blocks < 1) blocks = 1;
     kernel<<<(unsigned)blocks, kThreads, 0, stream>>>(a);
     return cudaGetLastError();
