@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kThreads) sobol_points_walk(PointsArgs a) {
 
   const uint32_t lane = threadIdx.x & 31u;
   const bool rows16 = (s & 3u) == 0 && (((uintptr_t)a.out_u32 | (uintptr_t)a.out_f32) & 15u) == 0;
-  // chunks of CW dimensions, 32 lanes per row of a whole chunk: 32 quads (128 dimensions) with
+  // chunks of cw dimensions, 32 lanes per row of a whole chunk: 32 quads (128 dimensions) with
   // 16-byte rows, else 32 dimensions; the last chunk is wl wide, kl rows per warp step
   const uint32_t cw = rows16 ? 128u : 32u;
   const uint32_t nch = (s + cw - 1u) / cw, wl = s - cw * (nch - 1u), kl = 32u / (rows16 ? wl >> 2 : wl);
