@@ -130,16 +130,23 @@ __global__ void __launch_bounds__(kThreads, 2) halton_points_kernel(HaltonArgs p
   const uint32_t w0 = s < 32u ? s : 32u, k0 = 32u / w0;
   const uint32_t w1 = s > 32u ? s - 32u : 0u, k1 = w1 ? 32u / w1 : 1u;
   const uint64_t U0 = (uint64_t)kHaltonSteps * k0, U1 = (uint64_t)kHaltonSteps * k1;
-  const uint64_t n0 = (p.count + U0 - 1) / U0, n1 = w1 ? (p.count + U1 - 1) / U1 : 0;
+  // Two chunks (s > 32, so k0 = 1): units go by row blocks of U1 rows, k1 units of the first
+  // chunk then one of the second, so the two chunks of the same rows -- which share cache lines
+  // when a row is not a whole number of lines -- are written at about the same time.
+  const uint32_t per_block = w1 ? k1 + 1u : 1u;
+  const uint64_t n_units = w1 ? (p.count + U1 - 1) / U1 * per_block : (p.count + U0 - 1) / U0;
   const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
   // this lane's place in a unit of either chunk: (row offset, output dimension)
   const uint32_t ro0 = lane / w0, jo0 = lane % w0;
   const uint32_t ro1 = w1 ? lane / w1 : 0u, jo1 = w1 ? 32u + lane % w1 : 0u;
-  for (uint64_t u = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < n0 + n1; u += nw) {
-    const bool c1 = u >= n0;
+  for (uint64_t u = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < n_units; u += nw) {
+    const uint64_t rb = u / per_block;
+    const uint32_t within = (uint32_t)(u - rb * per_block);
+    const bool c1 = w1 && within == k1;
     const uint32_t w = c1 ? w1 : w0, k = c1 ? k1 : k0;
     const uint64_t U = c1 ? U1 : U0;
-    const uint64_t r0 = (c1 ? u - n0 : u) * U;
+    const uint64_t r0 = w1 ? rb * U1 + (c1 ? 0u : (uint64_t)within * kHaltonSteps) : u * U0;
+    if (r0 >= p.count) continue;  // the last row block is cut by the range
     if (lane >= k * w) continue;  // w does not divide 32: the remaining lanes idle
     const uint32_t jo = c1 ? jo1 : jo0;
     const uint64_t row = r0 + (c1 ? ro1 : ro0);
@@ -422,13 +429,14 @@ cudaError_t launch_halton_points(const HaltonArgs& args, cudaStream_t stream) {
   cudaError_t eo = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, halton_points_kernel, kThreads, smem);
   if (eo != cudaSuccess) return eo;
   uint64_t blocks = (uint64_t)dev.sm_count * (per_sm < 1 ? 1 : per_sm);
-  // units of kHaltonSteps steps: one chunk of up to 32 dimensions, k rows per step
+  // units of kHaltonSteps steps: one chunk of up to 32 dimensions, k rows per step; with two
+  // chunks, row blocks of one second-chunk unit's rows, 32 / w1 + 1 units each
   const uint32_t w0 = p.s < 32 ? p.s : 32, w1 = p.s > 32 ? p.s - 32 : 0;
   const uint64_t U0 = (uint64_t)kHaltonSteps * (32 / w0);
   uint64_t units = (p.count + U0 - 1) / U0;
   if (w1) {
     const uint64_t U1 = (uint64_t)kHaltonSteps * (32 / w1);
-    units += (p.count + U1 - 1) / U1;
+    units = (p.count + U1 - 1) / U1 * (32 / w1 + 1);
   }
   const uint64_t need = (units + kThreads / 32 - 1) / (kThreads / 32);
   if (need < blocks) blocks = need;

@@ -19,13 +19,13 @@ using namespace pts;
 
 // ---------------------------------------------------------------------------
 // K2: rank-1 lattice.  BACKWARD follows Alg. 4: phi_2(~k) = ~phi_2(k), so
-// x = shift - g - phi_2(k) g (mod 2^32).
+// x = shift - g - phi_2(k) g (mod 2^32).  Direct 16-byte stores; each warp takes
+// a short range of groups (launch_spread), so the resident warps write
+// neighbouring parts of the output.
 // ---------------------------------------------------------------------------
-template <int K, bool BACKWARD, bool TMA>
+template <int K, bool BACKWARD>
 __global__ void __launch_bounds__(kThreads) lattice_points_fast(PointsArgs a) {
-  extern __shared__ __align__(128) uint32_t smem[];
   const uint32_t lane = threadIdx.x & 31u;
-  WarpStager<K> stager(smem + (threadIdx.x >> 5) * WarpStager<K>::kWarpWords);
   const uint32_t s = a.s;
   const uint32_t Q = 1u << a.q_log2;
   uint32_t gj[4 * K], lo[4 * K];
@@ -58,10 +58,7 @@ __global__ void __launch_bounds__(kThreads) lattice_points_fast(PointsArgs a) {
         v[t] = BACKWARD ? lo[4 * c + t] - phib * gj[4 * c + t] : phib * gj[4 * c + t] + lo[4 * c + t];
       const uint64_t o = off + 128u * c;
       if (g < full_groups) {
-        if (TMA)
-          stager.put(lane, c, v);
-        else
-          store4(a.out_u32, a.out_f32, o, v, a.chk);
+        store4(a.out_u32, a.out_f32, o, v, a.chk);
       } else {  // ragged last group: per-element row test
         const uint64_t rows_left = a.count - (g << a.q_log2);
         const uint32_t e0 = 4u * (lane + 32u * c);
@@ -70,10 +67,7 @@ __global__ void __launch_bounds__(kThreads) lattice_points_fast(PointsArgs a) {
           if ((uint64_t)((e0 + t) / s) < rows_left) store1(a.out_u32, a.out_f32, o + t, v[t], a.chk);
       }
     }
-    if (TMA && g < full_groups)
-      stager.group_done(lane, off, g + 1 == g1 || g + 1 == full_groups, a.out_u32, a.out_f32);
   }
-  if (TMA) stager.finish(lane);
 }
 
 // K2 for the shapes the fast path's groups do not fit (s / gcd(s, 128) > 4, or an
@@ -491,25 +485,19 @@ cudaError_t launch_lattice_points(PointsArgs a, cudaStream_t stream) {
   if (!fast) {
     if (aligned16(a.out_u32) && aligned16(a.out_f32) && a.s <= 1024) {
       const uint64_t batches = (a.count + kFlatRows - 1) / kFlatRows;
-      return backward ? launch_persistent(lattice_points_flat<true>, batches, 0, stream, a)
-                      : launch_persistent(lattice_points_flat<false>, batches, 0, stream, a);
+      return backward ? launch_spread(lattice_points_flat<true>, batches, 1, 0, stream, a)
+                      : launch_spread(lattice_points_flat<false>, batches, 1, 0, stream, a);
     }
     return backward ? launch_grid_stride(lattice_points_generic<true>, a.count * a.s, stream, a)
                     : launch_grid_stride(lattice_points_generic<false>, a.count * a.s, stream, a);
   }
   const uint64_t groups = (a.count + (1u << a.q_log2) - 1) >> a.q_log2;
-  // TMA bulk stores for device-memory outputs whose staging tiles fit (K <= 3)
-  const size_t stage = (size_t)(kThreads / 32) * 4 * kStageGroups * 128u * K * sizeof(uint32_t);
-  const bool tma = kPointsTma && device_resident(a.out_u32) && device_resident(a.out_f32) &&
-                   stage <= device_info().smem_per_block_optin;
-  const size_t smem = tma ? stage : 0;
-#define QMC_LATTICE_CASE(KK)                                                                                 \
-  case KK:                                                                                                   \
-    if (tma)                                                                                                 \
-      return backward ? launch_persistent(lattice_points_fast<KK, true, kPointsTma>, groups, smem, stream, a)  \
-                      : launch_persistent(lattice_points_fast<KK, false, kPointsTma>, groups, smem, stream, a); \
-    return backward ? launch_persistent(lattice_points_fast<KK, true, false>, groups, 0, stream, a)          \
-                    : launch_persistent(lattice_points_fast<KK, false, false>, groups, 0, stream, a);
+  // direct 16-byte stores, four groups per warp on a grid sized by the groups: at s = 32 this
+  // wrote 2^24 points 21 % faster than TMA bulk stores from a persistent grid of long ranges
+#define QMC_LATTICE_CASE(KK)                                                                  \
+  case KK:                                                                                    \
+    return backward ? launch_spread(lattice_points_fast<KK, true>, groups, 4, 0, stream, a) \
+                    : launch_spread(lattice_points_fast<KK, false>, groups, 4, 0, stream, a);
   switch (K) {
     QMC_LATTICE_CASE(1)
     QMC_LATTICE_CASE(2)

@@ -47,13 +47,15 @@ __device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Build-time choices of the Sobol' store path: TMA bulk stores from staged
-// shared-memory tiles (1) or direct 128-bit stores (0), and the groups per
-// staged tile (per warp, double-buffered).  Measured on GB300 at s = 32, 2^24
-// points, u32 + f32: direct stores 0.714 ms; TMA with 1 / 2 / 4 / 8 groups per
-// tile 0.726 / 0.728 / 0.653 / 0.866 ms (4 groups: 2 KiB bulk stores, 2 CTAs per
-// SM; 8 groups: 1 CTA per SM).
+// shared-memory tiles on a persistent grid (1) or direct 128-bit stores on a
+// grid of short per-warp ranges (0), and the groups per staged tile (per warp,
+// double-buffered).  Measured on GB300 at s = 32, 2^24 points, u32 + f32, on a
+// persistent grid of long per-warp ranges: direct stores 0.714 ms; TMA with
+// 1 / 2 / 4 / 8 groups per tile 0.726 / 0.728 / 0.653 / 0.866 ms.  Direct stores
+// with 64 groups per warp on a grid sized by the groups (launch_spread): 0.60 ms;
+// TMA on that grid 0.83 ms (each block stages 86 KB).
 #ifndef QMC_POINTS_TMA
-#define QMC_POINTS_TMA (QMC_CHECKED ? 0 : 1)  // the checked build tests every 16-byte store
+#define QMC_POINTS_TMA 0
 #endif
 #ifndef QMC_POINTS_STAGE_GROUPS
 #define QMC_POINTS_STAGE_GROUPS 4
@@ -154,6 +156,24 @@ inline cudaError_t launch_persistent(KernelT kernel, uint64_t warps_needed, size
   uint64_t blocks = (uint64_t)dev.sm_count * per_sm;
   const uint64_t need = (warps_needed + kThreads / 32 - 1) / (kThreads / 32);
   if (need < blocks) blocks = need;
+  if (blocks < 1) blocks = 1;
+  kernel<<<(unsigned)blocks, kThreads, smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
+// A grid of one range of per_warp units per warp, as many blocks as the units ask, so that the
+// warps resident at any time write neighbouring parts of the output (measured on GB300: a
+// persistent grid of long per-warp ranges spreads the concurrent stores over the whole output
+// and writes 5-20 % slower).  Kernels with a per-block set-up take ranges long enough to pay it.
+template <typename KernelT>
+inline cudaError_t launch_spread(KernelT kernel, uint64_t units, uint64_t per_warp, size_t smem,
+                                 cudaStream_t stream, const PointsArgs& a) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  uint64_t blocks = (units + per_warp * (kThreads / 32) - 1) / (per_warp * (kThreads / 32));
+  if (blocks > 0x7FFFFFFFull) blocks = 0x7FFFFFFFull;  // warp_range spreads any remainder over the grid
   if (blocks < 1) blocks = 1;
   kernel<<<(unsigned)blocks, kThreads, smem, stream>>>(a);
   return cudaGetLastError();

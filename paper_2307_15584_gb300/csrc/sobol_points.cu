@@ -495,10 +495,20 @@ cudaError_t launch_sobol_points(PointsArgs a, cudaStream_t stream) {
   const size_t smem = ((tma ? stage_words : 0) + table_words) * sizeof(uint32_t);
   const uint64_t groups = (a.count + (1u << a.q_log2) - 1) >> a.q_log2;
   const bool v4 = (a.s & 3u) == 0;
-#define QMC_SOBOL_MODES(KK, V, T)                                                                       \
-  if (a.scramble == 0) return launch_persistent(sobol_points_fast<KK, 0, V, T>, groups, smem, stream, a); \
-  if (a.scramble == 1) return launch_persistent(sobol_points_fast<KK, 1, V, T>, groups, smem, stream, a); \
-  return launch_persistent(sobol_points_fast<KK, 2, V, T>, groups, smem, stream, a);
+  // direct stores: short per-warp ranges (launch_spread), long enough to pay each warp's first
+  // Hout (one column XOR per set bit of G_hi) and each block's tables; 64 groups for the
+  // sequences of up to 2^16 G_hi values, 256 for longer indices (measured at s = 32: 64-bit
+  // indices at 2^40 ran 4 % slower with 64 groups a warp than with 256)
+  uint32_t hb = 0;  // bit length of the largest G_hi
+  for (uint64_t gh = ((a.index_begin + a.count) >> a.q_log2) >> a.u_log2; gh; gh >>= 1) ++hb;
+  const uint64_t per_warp = hb <= 16 ? 64 : 256;
+#define QMC_SOBOL_LAUNCH(T, KERNEL)                                 \
+  ((T) ? launch_persistent(KERNEL, groups, smem, stream, a)         \
+       : launch_spread(KERNEL, groups, per_warp, smem, stream, a))
+#define QMC_SOBOL_MODES(KK, V, T)                                                 \
+  if (a.scramble == 0) return QMC_SOBOL_LAUNCH(T, (sobol_points_fast<KK, 0, V, T>)); \
+  if (a.scramble == 1) return QMC_SOBOL_LAUNCH(T, (sobol_points_fast<KK, 1, V, T>)); \
+  return QMC_SOBOL_LAUNCH(T, (sobol_points_fast<KK, 2, V, T>));
 #define QMC_SOBOL_CASE(KK)                \
   case KK:                                \
     if (v4 && tma) {                      \
@@ -519,6 +529,7 @@ cudaError_t launch_sobol_points(PointsArgs a, cudaStream_t stream) {
   }
 #undef QMC_SOBOL_CASE
 #undef QMC_SOBOL_MODES
+#undef QMC_SOBOL_LAUNCH
 }
 
 }  // namespace qmc
