@@ -467,7 +467,9 @@ def compact_extras(x: dict) -> dict:
                             "rel_err_vs_exact": _r(f["rel_err_vs_exact"], 2)}
     if "points" in x:
         out["points_gdims_s_frac_hbm"] = {k: [_r(v["gdims_s"], 3), _r(v["frac_hbm"], 2)]
-                                          for k, v in x["points"].items() if isinstance(v, dict)}
+                                          for k, v in x["points"].items() if isinstance(v, dict) and "gdims_s" in v}
+        if "fill_reference" in x["points"]:
+            out["points_fill_reference_frac_hbm"] = _r(x["points"]["fill_reference"]["frac_hbm"], 3)
     return out
 
 
@@ -771,6 +773,11 @@ def bench_points(dev, steps, warmup, small, sm_mhz):
                 entry["frac_issue"] = ipc * n * si / (ms * 1e-3) / issue_peak
                 entry["bound"] = "hbm" if entry["frac_hbm"] >= entry["frac_issue"] else "alu"
         res[name] = entry
+    # context for fractions above 1: the copy peak moves every byte twice (a read and a write);
+    # a write-only stream of the same two outputs by the library's fill kernels, timed the same way
+    ms = statistics.median(timed(lambda: (u.fill_(0), f.fill_(0.0)), steps, warmup, stream))
+    gbs = n * s * 8 / (ms * 1e-3) / 1e9
+    res["fill_reference"] = {"ms": ms, "gb_s": gbs, "frac_hbm": gbs / peak, "kind": "library fill (write-only)"}
     del u, f, u40, f40
     return res
 
