@@ -131,16 +131,17 @@ __global__ void __launch_bounds__(kThreads) lattice_points_generic(PointsArgs a)
 }
 
 // Pixel-shifted lattice, coalesced path (16-byte aligned outputs, 32 spp s <= 2^31).
-// A warp takes batches of 32 consecutive pixels: lane l computes the shift of pixel
-// l of the batch once (Hilbert position, then phi_3), and the batch's 32 spp rows
+// A warp takes batches of 2^BLOG2 <= 32 consecutive pixels: lane l computes the shift
+// of pixel l of the batch once (Hilbert position, then phi_3), and the batch's rows
 // are written as consecutive 16-byte chunks, each element's pixel shift fetched from
 // its lane with a shuffle.  LAYOUT 1 (s % 4 == 0): a chunk holds four dimensions of
 // one row; LAYOUT 2 (s = 1, 2): a chunk holds 4 / s whole rows; LAYOUT 0: each of its
 // four elements finds its own row, dimension and pixel.
-template <int LAYOUT>
+template <int LAYOUT, int BLOG2>
 __global__ void __launch_bounds__(kThreads) pixel_lattice_points_fast(PixelPointsArgs a) {
+  constexpr uint32_t kBatch = 1u << BLOG2;
   const uint32_t lane = threadIdx.x & 31u;
-  const uint64_t n_batches = (a.n_pixels + 31) >> 5;
+  const uint64_t n_batches = (a.n_pixels + kBatch - 1) >> BLOG2;
   uint64_t b0, b1;
   warp_range(n_batches, b0, b1);
   // x / d = umulhi(x, floor(2^64 / d) + 1) exactly for x < 2^32 and d > 1
@@ -148,9 +149,9 @@ __global__ void __launch_bounds__(kThreads) pixel_lattice_points_fast(PixelPoint
   const uint64_t mag_spp = a.spp > 1 ? ~0ull / a.spp + 1 : 0;
   const uint32_t per_pixel = a.spp * a.s;  // elements
   for (uint64_t b = b0; b < b1; ++b) {
-    const uint64_t first = b << 5;  // batch's first pixel, relative to pixel_begin
+    const uint64_t first = b << BLOG2;  // batch's first pixel, relative to pixel_begin
     const uint64_t left = a.n_pixels - first;
-    const uint32_t npx = left < 32 ? (uint32_t)left : 32u;
+    const uint32_t npx = left < kBatch ? (uint32_t)left : kBatch;
     uint32_t sh = 0;
     if (lane < npx) {
       const uint64_t p = a.pixel_begin + first + lane;
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(kThreads) pixel_lattice_points_fast(PixelPoint
     }
     const uint32_t total = npx * per_pixel;  // the batch's elements
     const uint32_t chunks = (total + 3u) >> 2;
-    const uint64_t off0 = first * per_pixel;  // element offset of the batch: a multiple of 32
+    const uint64_t off0 = first * per_pixel;  // element offset of the batch: a multiple of 8
     for (uint32_t c0 = 0; c0 < chunks; c0 += 32) {  // same trip count in every lane
       const uint32_t c = c0 + lane;
       const uint32_t e = 4u * c;  // element within the batch, < 2^32
@@ -465,12 +466,17 @@ cudaError_t launch_random_lattice_points(const RandomPointsArgs& args, cudaStrea
 cudaError_t launch_pixel_lattice_points(const PixelPointsArgs& a, cudaStream_t stream) {
   const DeviceInfo& dev = device_info();
   if ((uint64_t)32 * a.spp * a.s <= (1ull << 31) && aligned16(a.out_u32) && aligned16(a.out_f32)) {
-    const auto kernel = (a.s & 3u) == 0 ? pixel_lattice_points_fast<1>
-                        : a.s <= 2       ? pixel_lattice_points_fast<2>
-                                         : pixel_lattice_points_fast<0>;
-    // one 32-pixel batch per warp: the kernel has no per-block set-up, and a persistent grid's
-    // warps would end unevenly when they hold only a few batches each
-    uint64_t blocks = (((a.n_pixels + 31) >> 5) + kThreads / 32 - 1) / (kThreads / 32);
+    // one batch per warp: the kernel has no per-block set-up, and a persistent grid's warps would
+    // end unevenly when they hold only a few batches each.  Batches of 8 pixels when a pixel has
+    // 256 or more elements (short ranges keep the resident warps' stores together: s = 32 at 16
+    // spp 920 Gdims/s against 880 with 32-pixel batches), else 32 (at s = 2, 16 spp, a warp
+    // computing 8 shifts for 256 elements ran at a third of the speed)
+    const bool small = a.spp * a.s >= 256u;
+    const auto kernel = (a.s & 3u) == 0 ? (small ? pixel_lattice_points_fast<1, 3> : pixel_lattice_points_fast<1, 5>)
+                        : a.s <= 2       ? (small ? pixel_lattice_points_fast<2, 3> : pixel_lattice_points_fast<2, 5>)
+                                         : (small ? pixel_lattice_points_fast<0, 3> : pixel_lattice_points_fast<0, 5>);
+    const uint32_t blog2 = small ? 3u : 5u;
+    uint64_t blocks = (((a.n_pixels + (1u << blog2) - 1) >> blog2) + kThreads / 32 - 1) / (kThreads / 32);
     if (blocks > 0x7FFFFFFFull) blocks = 0x7FFFFFFFull;  // warp_range spreads the batches over the grid
     if (blocks < 1) blocks = 1;
     kernel<<<(unsigned)blocks, kThreads, 0, stream>>>(a);
