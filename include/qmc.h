@@ -227,9 +227,13 @@ QMC_API qmc_status qmc_sobol_matrices_wide(uint32_t s, uint32_t m, const uint32_
  *   d_out_u32    [count][s] integer points (units of 2^-32), or NULL
  *   d_out_f32    [count][s] map_u32_to_unifloat of the same values (every
  *                component in [0,1)), or NULL; at least one output required
- * Outputs must be 4-byte aligned (QMC_ERR_ALIGN); the 128-bit store path runs
- * when both are 16-byte aligned and index_begin is a multiple of the warp's
- * row group, a scalar path otherwise.  count = 0 is a no-op.
+ * Outputs must be 4-byte aligned (QMC_ERR_ALIGN); with 16-byte aligned outputs
+ * and index_begin * s a multiple of 4 the points are written with 128-bit
+ * stores (a start off the row-group grid first writes the rows up to the next
+ * group in a separate small launch on the same stream), otherwise the walking
+ * kernel writes them (128-bit stores when s % 4 == 0 and both outputs are
+ * 16-byte aligned, else 4-byte stores).
+ * count = 0 is a no-op.
  */
 QMC_API qmc_status qmc_sobol_points(const uint32_t* d_matrices, uint32_t s, uint64_t index_begin,
                             uint64_t count, uint32_t scramble, const uint32_t* d_seeds,
