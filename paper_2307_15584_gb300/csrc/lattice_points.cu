@@ -137,8 +137,8 @@ __global__ void __launch_bounds__(kThreads) lattice_points_generic(PointsArgs a)
 // its lane with a shuffle.  LAYOUT 1 (s % 4 == 0): a chunk holds four dimensions of
 // one row; LAYOUT 2 (s = 1, 2): a chunk holds 4 / s whole rows; LAYOUT 0: each of its
 // four elements finds its own row, dimension and pixel.
-template <int LAYOUT, int BLOG2>
-__global__ void __launch_bounds__(kThreads) pixel_lattice_points_fast(PixelPointsArgs a) {
+template <int LAYOUT, int BLOG2, int NB>  // NB: batches whose shifts a warp computes together
+__global__ void __launch_bounds__(kThreads, 4) pixel_lattice_points_fast(PixelPointsArgs a) {
   constexpr uint32_t kBatch = 1u << BLOG2;
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t n_batches = (a.n_pixels + kBatch - 1) >> BLOG2;
@@ -148,15 +148,20 @@ __global__ void __launch_bounds__(kThreads) pixel_lattice_points_fast(PixelPoint
   const uint64_t mag_s = a.s > 1 ? ~0ull / a.s + 1 : 0;
   const uint64_t mag_spp = a.spp > 1 ? ~0ull / a.spp + 1 : 0;
   const uint32_t per_pixel = a.spp * a.s;  // elements
-  for (uint64_t b = b0; b < b1; ++b) {
+  // the shift of pixel `lane` of batch b (0 past the batch's pixels)
+  auto shift_of = [&](uint64_t b) -> uint32_t {
+    const uint64_t first = b << BLOG2;
+    const uint64_t left = a.n_pixels - first;
+    const uint32_t npx = left < kBatch ? (uint32_t)left : kBatch;
+    if (lane >= npx) return 0u;
+    const uint64_t p = a.pixel_begin + first + lane;
+    return pixel_shift((uint32_t)(p % a.width), (uint32_t)(p / a.width), a.grid_log2);
+  };
+  // the rows of batch b, its pixels' shifts in lanes 0 .. npx - 1 of sh
+  auto write_batch = [&](uint64_t b, uint32_t sh) {
     const uint64_t first = b << BLOG2;  // batch's first pixel, relative to pixel_begin
     const uint64_t left = a.n_pixels - first;
     const uint32_t npx = left < kBatch ? (uint32_t)left : kBatch;
-    uint32_t sh = 0;
-    if (lane < npx) {
-      const uint64_t p = a.pixel_begin + first + lane;
-      sh = pixel_shift((uint32_t)(p % a.width), (uint32_t)(p / a.width), a.grid_log2);
-    }
     const uint32_t total = npx * per_pixel;  // the batch's elements
     const uint32_t chunks = (total + 3u) >> 2;
     const uint64_t off0 = first * per_pixel;  // element offset of the batch: a multiple of 8
@@ -214,6 +219,15 @@ __global__ void __launch_bounds__(kThreads) pixel_lattice_points_fast(PixelPoint
         }
       }
     }
+  };
+  // NB batches at a time: their shifts are independent dependency chains, computed together
+  for (uint64_t b = b0; b < b1; b += NB) {
+    uint32_t shv[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) shv[k] = b + k < b1 ? shift_of(b + k) : 0u;
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+      if (b + k < b1) write_batch(b + k, shv[k]);
   }
 }
 
@@ -471,12 +485,16 @@ cudaError_t launch_pixel_lattice_points(const PixelPointsArgs& a, cudaStream_t s
     // 256 or more elements (short ranges keep the resident warps' stores together: s = 32 at 16
     // spp 920 Gdims/s against 880 with 32-pixel batches), else 32 (at s = 2, 16 spp, a warp
     // computing 8 shifts for 256 elements ran at a third of the speed)
+    // With 32-pixel batches a warp takes four of them and computes their shifts together: one
+    // shift is a long dependent chain, and a warp with a single batch spent most of its life on it
+    // (s = 2, 16 spp: 0.79 of the copy bandwidth at any image size).
     const bool small = a.spp * a.s >= 256u;
-    const auto kernel = (a.s & 3u) == 0 ? (small ? pixel_lattice_points_fast<1, 3> : pixel_lattice_points_fast<1, 5>)
-                        : a.s <= 2       ? (small ? pixel_lattice_points_fast<2, 3> : pixel_lattice_points_fast<2, 5>)
-                                         : (small ? pixel_lattice_points_fast<0, 3> : pixel_lattice_points_fast<0, 5>);
-    const uint32_t blog2 = small ? 3u : 5u;
-    uint64_t blocks = (((a.n_pixels + (1u << blog2) - 1) >> blog2) + kThreads / 32 - 1) / (kThreads / 32);
+    const auto kernel = (a.s & 3u) == 0 ? (small ? pixel_lattice_points_fast<1, 3, 1> : pixel_lattice_points_fast<1, 5, 4>)
+                        : a.s <= 2       ? (small ? pixel_lattice_points_fast<2, 3, 1> : pixel_lattice_points_fast<2, 5, 4>)
+                                         : (small ? pixel_lattice_points_fast<0, 3, 1> : pixel_lattice_points_fast<0, 5, 4>);
+    const uint32_t blog2 = small ? 3u : 5u, per_warp = small ? 1u : 4u;
+    uint64_t blocks = (((a.n_pixels + (1u << blog2) - 1) >> blog2) + per_warp * (kThreads / 32) - 1) /
+                      (per_warp * (kThreads / 32));
     if (blocks > 0x7FFFFFFFull) blocks = 0x7FFFFFFFull;  // warp_range spreads the batches over the grid
     if (blocks < 1) blocks = 1;
     kernel<<<(unsigned)blocks, kThreads, 0, stream>>>(a);
